@@ -1,0 +1,300 @@
+/*
+ * crystal.h -- C ABI of the B300 CrystalGPU hashing library (libcrystal.so).
+ *
+ * The library runs a stream of host data units through MD5 direct hashing
+ * and MD5 sliding-window hashing on one GPU, behind the job abstraction of
+ * the CrystalGPU paper (Gharaibeh, Al-Kiswany, Ripeanu):
+ *   - Section 3, Figure 2: a job carries host and device input/output
+ *     buffers, their sizes, the kernel to run and a completion callback;
+ *   - Section 3, Figure 3: init / finalize / job_get / job_put / job_submit /
+ *     job_synch / job_query;
+ *   - Section 4.2: one host master thread per GPU, idle / outstanding /
+ *     running job queues, jobs interleaved over a copy-in / kernel /
+ *     copy-out pipeline (Figure 4), completion found by polling because the
+ *     GPU runtime has no completion interrupt (Section 4.1).
+ * Every call below names the paper passage it follows.  All sizes are bytes.
+ * Every function returns a status (CRYSTAL_OK or a negative error) unless it
+ * says otherwise; no function throws, aborts or prints.
+ *
+ * Two layers:
+ *   1. the job runtime (crystal_init ... crystal_shutdown), which owns a
+ *      device pool, a pinned host pool, the streams and the master thread;
+ *   2. the stateless batch launchers (crystal_launch_*), which run the
+ *      kernels of one batch on caller-owned device memory and a caller
+ *      stream.  The runtime is built on them.
+ */
+#ifndef CRYSTAL_H
+#define CRYSTAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+enum {
+    CRYSTAL_OK = 0,
+    CRYSTAL_PENDING = 1,      /* job submitted and not finished (job_query false) */
+    CRYSTAL_EINVAL = -1,      /* bad argument, or a call not allowed in this state */
+    CRYSTAL_EAGAIN = -2,      /* pool has no room now; retry after a release */
+    CRYSTAL_ENOMEM = -3,      /* allocation failed at init / unpooled create */
+    CRYSTAL_ETIMEDOUT = -4,   /* bounded wait ran out */
+    CRYSTAL_EOVERFLOW = -5,   /* sliding output buffer too small for the chunk records */
+    CRYSTAL_ESHUTDOWN = -6,   /* context is shutting down */
+    CRYSTAL_EDEVICE = -7      /* CUDA error, or a device-side status word was set */
+};
+
+/* ---- job kinds (the kernel_func of Figure 2, chosen by id) -------------- */
+enum {
+    CRYSTAL_KIND_NOP = 0,         /* dummy kernel of Section 5.1: copy in, no work, copy out */
+    CRYSTAL_KIND_MD5_DIRECT = 1,  /* direct hashing (Section 5.2, Figure 6) */
+    CRYSTAL_KIND_MD5_SLIDING = 2  /* sliding-window hashing (Section 2.2, content-addressable storage) */
+};
+
+/* ---- context flags ------------------------------------------------------ */
+enum {
+    /* Allocate each job's device and pinned host buffers at crystal_task_create
+     * (cudaMalloc / cudaHostAlloc) and free them at release: the per-job
+     * allocation the paper's buffer pool removes (Section 3, Section 5.2). */
+    CRYSTAL_FLAG_NO_POOL = 1u,
+    /* One stream, one job at a time, the master waits for each job to finish
+     * before issuing the next: no copy/compute overlap (Section 4.1). */
+    CRYSTAL_FLAG_NO_OVERLAP = 2u,
+    /* One job per kernel launch (no grouping of outstanding jobs). */
+    CRYSTAL_FLAG_NO_BATCH = 4u,
+    /* Replay each batch's descriptor upload and kernel chain as a captured
+     * CUDA graph instead of individual launches. */
+    CRYSTAL_FLAG_GRAPHS = 8u
+};
+
+/* crystal_init's argument.  Zero fields take the defaults listed. */
+typedef struct crystal_config {
+    uint64_t max_in_bytes;      /* largest job input (init's max_input_size, Figure 3); default 64 MiB */
+    uint64_t max_out_bytes;     /* largest job output (init's max_output_size); default 16 MiB */
+    uint64_t device_pool_bytes; /* device arena for job buffers and scratch; default 4 GiB */
+    uint64_t host_pool_bytes;   /* pinned host arena for job buffers; default 1 GiB */
+    void* device_arena;         /* optional caller-owned device memory of device_pool_bytes
+                                   (must stay valid until shutdown); NULL: the library
+                                   allocates it with one cudaMalloc */
+    int32_t n_streams;          /* streams the master interleaves jobs over; default 4 */
+    int32_t device;             /* CUDA device ordinal; default 0 */
+    uint32_t flags;             /* CRYSTAL_FLAG_* */
+    uint32_t max_batch_jobs;    /* outstanding jobs grouped into one launch; default 64 */
+    uint64_t max_batch_bytes;   /* input bytes grouped into one launch; default 32 MiB */
+} crystal_config;
+
+/* Hash parameters of one job.  A NULL params pointer means all defaults
+ * (crystal_params_default).  A zero size field takes its default; mask and
+ * target are always taken as given (mask = 0, target = 0 marks every window). */
+typedef struct crystal_hash_params {
+    uint32_t segment_bytes;       /* direct: segment size S; default 4096; >= 1 */
+    uint32_t window_bytes;        /* sliding: window w; default 20; 1..55 (one MD5 block) */
+    uint32_t mask;                /* sliding: boundary mask; default 0x1FFF */
+    uint32_t target;              /* sliding: boundary target; default 0x1FFF */
+    uint32_t chunk_segment_bytes; /* sliding: S of each chunk's direct hash; default 4096 */
+    uint32_t reserved;            /* must be 0 */
+} crystal_hash_params;
+
+typedef struct crystal_ctx crystal_ctx;   /* opaque: pools, streams, master thread */
+typedef struct crystal_task crystal_task; /* opaque: one job (Figure 2's job_t) */
+
+/* Completion callback (Figure 2's callback_func).  Runs on the master thread
+ * (Section 4.2) once the job's output is in host memory.  It may read the
+ * output and call crystal_task_release on this job; it must not block, and
+ * crystal_task_wait called from it returns CRYSTAL_EINVAL. */
+typedef void (*crystal_callback)(crystal_task* task, int status, void* user);
+
+/* Fill *cfg / *p with the defaults above. */
+void crystal_config_default(crystal_config* cfg);
+void crystal_params_default(crystal_hash_params* p);
+
+/* init(max_input_size, max_output_size), Figure 3 / Section 3: creates the
+ * buffer pool (one device arena, one pinned host arena), the streams and the
+ * master thread.  *out receives the context.  Errors: EINVAL (bad field),
+ * ENOMEM (an allocation failed; nothing is left allocated), EDEVICE. */
+int crystal_init(const crystal_config* cfg, crystal_ctx** out);
+
+/* finalize(), Figure 3: stops accepting jobs, lets in-flight jobs finish,
+ * cancels outstanding ones (their status becomes ESHUTDOWN and their
+ * callbacks run), frees every pool and stream.  Jobs not yet released are
+ * freed too; their handles become invalid. */
+int crystal_shutdown(crystal_ctx* ctx);
+
+/* job_get(), Figure 3: takes a job from the pool with a pinned host input of
+ * in_size bytes, a pinned host output of out_size bytes and device buffers of
+ * the same sizes.  in_size <= max_in_bytes, out_size <= max_out_bytes.
+ * Errors: EINVAL, EAGAIN (pool full now), ENOMEM (unpooled mode), ESHUTDOWN. */
+int crystal_task_create(crystal_ctx* ctx, uint64_t in_size, uint64_t out_size, crystal_task** out);
+
+/* h_input / h_output of Figure 2.  The application writes the input before
+ * submit and reads the output after completion until release; it must not
+ * touch either while the job runs.  NULL for a NULL task. */
+void* crystal_task_host_in(crystal_task* task);
+void* crystal_task_host_out(crystal_task* task);
+
+/* Device addresses of d_input / d_output (Figure 2), for inspection. */
+uint64_t crystal_task_device_in(crystal_task* task);
+uint64_t crystal_task_device_out(crystal_task* task);
+
+/* Shrink the sizes the next submit uses (input_size / output_size of
+ * Figure 2) without giving the buffers back: in_size and out_size must not
+ * exceed the sizes the job was created with.  Not while the job runs. */
+int crystal_task_resize(crystal_task* task, uint64_t in_size, uint64_t out_size);
+
+/* job_submit(), Figure 3: queues the job on the shared outstanding queue
+ * (Section 4.2).  kind is a CRYSTAL_KIND_*, params may be NULL (defaults).
+ * cb (may be NULL) runs on completion with user.  Errors: EINVAL (bad kind,
+ * params or out_size below what the kind needs: 16 for direct, the fixed
+ * sliding header + bitmap for sliding), EAGAIN (no device room for the job's
+ * scratch now), ESHUTDOWN.  A job may be submitted again after it finished. */
+int crystal_task_submit(crystal_task* task, int kind, const crystal_hash_params* params,
+                        crystal_callback cb, void* user);
+
+/* job_query(), Figure 3: CRYSTAL_PENDING while queued or running, otherwise
+ * the job's final status (CRYSTAL_OK, CRYSTAL_EOVERFLOW, CRYSTAL_EDEVICE,
+ * CRYSTAL_ESHUTDOWN).  EINVAL for a job never submitted. */
+int crystal_task_poll(crystal_task* task);
+
+/* job_synch(), Figure 3, bounded: blocks until the job finished or
+ * timeout_ns elapsed (timeout_ns < 0: no bound).  Returns the job's final
+ * status, CRYSTAL_ETIMEDOUT, or CRYSTAL_EINVAL (never submitted, or called
+ * from a completion callback). */
+int crystal_task_wait(crystal_task* task, int64_t timeout_ns);
+
+/* job_put(), Figure 3: returns the job's buffers to the pool.  EINVAL while
+ * the job is queued or running. */
+int crystal_task_release(crystal_task* task);
+
+/* Host clock stamps (nanoseconds, CLOCK_MONOTONIC) of the job's last run:
+ * submit, dispatch by the master thread, completion seen by the master.
+ * Any pointer may be NULL. */
+int crystal_task_timing(crystal_task* task, uint64_t* submit_ns, uint64_t* dispatch_ns,
+                        uint64_t* done_ns);
+
+/* Counters of a context. */
+typedef struct crystal_stats {
+    uint64_t jobs_completed;
+    uint64_t batches_launched;
+    uint64_t device_pool_bytes, device_pool_used;
+    uint64_t host_pool_bytes, host_pool_used;
+    uint64_t jobs_outstanding, jobs_running;
+} crystal_stats;
+int crystal_get_stats(crystal_ctx* ctx, crystal_stats* out);
+
+/* Worst-case output size of a job: 16 for direct; for sliding the header,
+ * the bitmap and one record per possible chunk (n - w + 2 of them, the
+ * case mask = 0).  in_size for NOP.  0 on a bad kind. */
+uint64_t crystal_out_bytes(int kind, uint64_t in_size, const crystal_hash_params* params);
+
+/* Output size of a sliding job with room for max_chunks chunk records. */
+uint64_t crystal_sliding_out_bytes(uint64_t in_size, uint64_t max_chunks);
+
+/* Static text for a status code. */
+const char* crystal_strerror(int status);
+
+/* Kernel launches this process made through the library (all contexts and
+ * launchers; a graph replay counts each kernel node). */
+uint64_t crystal_kernel_launches(void);
+
+/* ---- output layouts (what the kernels write) ----------------------------
+ * direct  : 16-byte digest Direct(u, S) = MD5(MD5(seg_0) || ... || MD5(seg_{m-1})),
+ *           m = max(1, ceil(n / S)); the last segment may be short.
+ * sliding : u32 n_chunks | u32 flags | u32 bitmap[ceil(n/32)] |
+ *           u32 chunk_end[n_chunks] | u8 digest[n_chunks][16]
+ *           bit i of the bitmap (word i/32, bit i%32) is set iff
+ *           i <= n - w and (LE32(MD5(u[i, i+w))[0..3]) & mask) == target;
+ *           chunk ends are the sorted set {i + w : bit i} U {n};
+ *           digest[k] = Direct(u[end_{k-1}, end_k), chunk_segment_bytes),
+ *           end_{-1} = 0.  If the records do not fit in out_size, flags bit 0
+ *           is set, n_chunks holds the count needed and no record is written.
+ * nop     : nothing is written; out_size bytes are copied back.
+ */
+
+/* ---- stateless batch launchers ------------------------------------------
+ * One batch = a device-resident crystal_batch header followed by n_units
+ * crystal_unit records (direct units first, then sliding units).  Build it on
+ * the host with crystal_batch_plan, copy it to the device, then launch.
+ * Every pointer inside is a device address.  Kernels read the header from
+ * device memory, so one launch sequence (or one captured graph) serves any
+ * batch that fits the launch's grid-independent limits.
+ */
+typedef struct crystal_unit {
+    uint64_t in;         /* device address of the unit's bytes (any alignment) */
+    uint64_t n;          /* unit length */
+    uint64_t out;        /* device address of the unit's output (4-byte aligned) */
+    uint64_t scratch;    /* device address of the unit's scratch (16-byte aligned) */
+    uint64_t work_begin; /* filled by crystal_batch_plan: first global work item */
+    uint32_t out_cap;    /* output bytes available */
+    uint32_t seg_bytes;  /* direct: S; sliding: chunk S */
+    uint32_t window, mask, target;
+    uint32_t kind;       /* CRYSTAL_KIND_MD5_DIRECT or CRYSTAL_KIND_MD5_SLIDING */
+} crystal_unit;
+
+typedef struct crystal_batch {
+    uint32_t n_direct;        /* units [0, n_direct) are direct */
+    uint32_t n_sliding;       /* units [n_direct, n_direct + n_sliding) are sliding */
+    uint64_t direct_segments; /* total segments over the direct units */
+    uint64_t sliding_tiles;   /* total window tiles over the sliding units */
+    uint32_t window_max;      /* largest window among the sliding units */
+    uint32_t status;          /* device status word: 0, or a bit set by a kernel that met
+                                 an inconsistent record (the record is skipped) */
+    uint64_t reserved[4];     /* header is 64 bytes */
+    /* crystal_unit units[n_direct + n_sliding] follow */
+} crystal_batch;
+
+/* Offsets processed by one window tile of the sliding kernel. */
+#define CRYSTAL_SLIDING_TILE 1024u
+
+/* Scratch bytes one unit needs: 16 * ceil(n/S) for direct; for sliding the
+ * per-chunk segment table and digests for as many chunks as out_size holds.
+ * 0 for NOP or on a bad argument. */
+uint64_t crystal_scratch_bytes(int kind, uint64_t n, uint64_t out_size, const crystal_hash_params* params);
+
+/* Host-side planning of a batch in host memory (the header followed by the
+ * unit records, units filled by the caller except work_begin): checks every
+ * unit (kinds in order, sizes, windows 1..55, out_cap large enough, 16-byte
+ * aligned scratch), fills work_begin and the header's totals.  The buffer is
+ * then copied to the device as is.  Returns CRYSTAL_OK or CRYSTAL_EINVAL. */
+int crystal_batch_plan(crystal_batch* batch_host, uint32_t n_direct, uint32_t n_sliding);
+
+/* Bytes of a batch buffer holding n_units records. */
+uint64_t crystal_batch_bytes(uint32_t n_units);
+
+/* Launch the kernels of a device-resident batch on a CUDA stream
+ * (cudaStream_t passed as void*; NULL = legacy default stream).  Asynchronous;
+ * errors are launch errors only (CRYSTAL_EDEVICE).  The kernels may read up
+ * to 15 bytes before a unit's first byte and after its last byte inside the
+ * same 16-byte-aligned block; those bytes never affect a result.
+ *   crystal_launch_direct          segment MD5s then the digest of digests
+ *   crystal_launch_direct_segments segment MD5s into scratch only
+ *   crystal_launch_direct_outer    digest of digests from scratch only
+ *   crystal_launch_sliding         window bitmap, chunk ends, chunk digests
+ *   crystal_launch_sliding_windows window MD5s and the boundary bitmap only
+ *   crystal_launch_sliding_chunks  chunk ends and chunk segment tables only
+ *   crystal_launch_sliding_digests chunk segment MD5s and chunk digests only
+ *   crystal_launch_batch           everything the batch holds */
+int crystal_launch_direct(const crystal_batch* batch_dev, void* stream);
+int crystal_launch_direct_segments(const crystal_batch* batch_dev, void* stream);
+int crystal_launch_direct_outer(const crystal_batch* batch_dev, void* stream);
+int crystal_launch_sliding(const crystal_batch* batch_dev, void* stream);
+int crystal_launch_sliding_windows(const crystal_batch* batch_dev, void* stream);
+int crystal_launch_sliding_chunks(const crystal_batch* batch_dev, void* stream);
+int crystal_launch_sliding_digests(const crystal_batch* batch_dev, void* stream);
+int crystal_launch_batch(const crystal_batch* batch_dev, void* stream);
+
+/* Host-side arena allocator the pools use (exposed for tests; no GPU
+ * needed).  Offsets are relative to 0; alignment is a power of two. */
+typedef struct crystal_arena crystal_arena;
+int crystal_arena_create(uint64_t bytes, uint64_t alignment, crystal_arena** out);
+int crystal_arena_alloc(crystal_arena* a, uint64_t bytes, uint64_t* offset);
+int crystal_arena_free(crystal_arena* a, uint64_t offset);
+uint64_t crystal_arena_used(crystal_arena* a);
+uint64_t crystal_arena_largest_free(crystal_arena* a);
+void crystal_arena_destroy(crystal_arena* a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRYSTAL_H */

@@ -1,0 +1,394 @@
+"""ctypes binding of ``libcrystal.so`` (the C ABI in ``include/crystal.h``).
+
+Argument marshalling only: every step of the hashing path runs in the
+library's CUDA kernels and its C++ runtime.  The function names are the C
+names.  PyTorch is used for device memory and stream handles only (see
+:class:`DeviceBatch`).
+
+Loading fails loudly if the library cannot be found or built; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+CRYSTAL_OK = 0
+CRYSTAL_PENDING = 1
+CRYSTAL_EINVAL = -1
+CRYSTAL_EAGAIN = -2
+CRYSTAL_ENOMEM = -3
+CRYSTAL_ETIMEDOUT = -4
+CRYSTAL_EOVERFLOW = -5
+CRYSTAL_ESHUTDOWN = -6
+CRYSTAL_EDEVICE = -7
+
+CRYSTAL_KIND_NOP = 0
+CRYSTAL_KIND_MD5_DIRECT = 1
+CRYSTAL_KIND_MD5_SLIDING = 2
+
+CRYSTAL_FLAG_NO_POOL = 1
+CRYSTAL_FLAG_NO_OVERLAP = 2
+CRYSTAL_FLAG_NO_BATCH = 4
+CRYSTAL_FLAG_GRAPHS = 8
+
+CRYSTAL_SLIDING_TILE = 1024
+
+
+class crystal_config(ctypes.Structure):
+    _fields_ = [
+        ("max_in_bytes", ctypes.c_uint64),
+        ("max_out_bytes", ctypes.c_uint64),
+        ("device_pool_bytes", ctypes.c_uint64),
+        ("host_pool_bytes", ctypes.c_uint64),
+        ("device_arena", ctypes.c_void_p),
+        ("n_streams", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("max_batch_jobs", ctypes.c_uint32),
+        ("max_batch_bytes", ctypes.c_uint64),
+    ]
+
+
+class crystal_hash_params(ctypes.Structure):
+    _fields_ = [
+        ("segment_bytes", ctypes.c_uint32),
+        ("window_bytes", ctypes.c_uint32),
+        ("mask", ctypes.c_uint32),
+        ("target", ctypes.c_uint32),
+        ("chunk_segment_bytes", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+
+class crystal_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "jobs_completed", "batches_launched", "device_pool_bytes", "device_pool_used",
+        "host_pool_bytes", "host_pool_used", "jobs_outstanding", "jobs_running")]
+
+
+UNIT_DTYPE = np.dtype([
+    ("in", "<u8"), ("n", "<u8"), ("out", "<u8"), ("scratch", "<u8"), ("work_begin", "<u8"),
+    ("out_cap", "<u4"), ("seg_bytes", "<u4"), ("window", "<u4"), ("mask", "<u4"), ("target", "<u4"),
+    ("kind", "<u4"),
+])
+assert UNIT_DTYPE.itemsize == 64
+BATCH_HEADER_BYTES = 64
+
+crystal_callback = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
+
+_lib = None
+_u64 = ctypes.c_uint64
+_vp = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load (building first if the sources are newer) ``libcrystal.so``."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libcrystal.so is missing and could not be built")
+    L = ctypes.CDLL(path)
+    sig = {
+        "crystal_config_default": (None, [ctypes.POINTER(crystal_config)]),
+        "crystal_params_default": (None, [ctypes.POINTER(crystal_hash_params)]),
+        "crystal_init": (ctypes.c_int, [ctypes.POINTER(crystal_config), ctypes.POINTER(_vp)]),
+        "crystal_shutdown": (ctypes.c_int, [_vp]),
+        "crystal_task_create": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(_vp)]),
+        "crystal_task_host_in": (_vp, [_vp]),
+        "crystal_task_host_out": (_vp, [_vp]),
+        "crystal_task_device_in": (_u64, [_vp]),
+        "crystal_task_device_out": (_u64, [_vp]),
+        "crystal_task_resize": (ctypes.c_int, [_vp, _u64, _u64]),
+        "crystal_task_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(crystal_hash_params),
+                                               crystal_callback, _vp]),
+        "crystal_task_poll": (ctypes.c_int, [_vp]),
+        "crystal_task_wait": (ctypes.c_int, [_vp, ctypes.c_int64]),
+        "crystal_task_release": (ctypes.c_int, [_vp]),
+        "crystal_task_timing": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                                               ctypes.POINTER(_u64)]),
+        "crystal_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(crystal_stats)]),
+        "crystal_out_bytes": (_u64, [ctypes.c_int, _u64, ctypes.POINTER(crystal_hash_params)]),
+        "crystal_sliding_out_bytes": (_u64, [_u64, _u64]),
+        "crystal_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "crystal_kernel_launches": (_u64, []),
+        "crystal_scratch_bytes": (_u64, [ctypes.c_int, _u64, _u64, ctypes.POINTER(crystal_hash_params)]),
+        "crystal_batch_plan": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
+        "crystal_batch_bytes": (_u64, [ctypes.c_uint32]),
+        "crystal_arena_create": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(_vp)]),
+        "crystal_arena_alloc": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(_u64)]),
+        "crystal_arena_free": (ctypes.c_int, [_vp, _u64]),
+        "crystal_arena_used": (_u64, [_vp]),
+        "crystal_arena_largest_free": (_u64, [_vp]),
+        "crystal_arena_destroy": (None, [_vp]),
+    }
+    for name in ("crystal_launch_direct", "crystal_launch_direct_segments", "crystal_launch_direct_outer",
+                 "crystal_launch_sliding", "crystal_launch_sliding_windows", "crystal_launch_sliding_chunks",
+                 "crystal_launch_sliding_digests", "crystal_launch_batch"):
+        sig[name] = (ctypes.c_int, [_vp, _vp])
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status: int, what: str = "") -> int:
+    if status < 0:
+        msg = load().crystal_strerror(status).decode()
+        raise RuntimeError(f"{what}: {msg} ({status})")
+    return status
+
+
+def params(segment_bytes=4096, window_bytes=20, mask=0x1FFF, target=0x1FFF, chunk_segment_bytes=4096):
+    return crystal_hash_params(segment_bytes, window_bytes, mask, target, chunk_segment_bytes, 0)
+
+
+def out_bytes(kind: int, in_size: int, p: Optional[crystal_hash_params] = None) -> int:
+    return int(load().crystal_out_bytes(kind, in_size, ctypes.byref(p) if p is not None else None))
+
+
+def sliding_out_bytes(in_size: int, max_chunks: int) -> int:
+    return int(load().crystal_sliding_out_bytes(in_size, max_chunks))
+
+
+def scratch_bytes(kind: int, n: int, out_size: int, p: Optional[crystal_hash_params] = None) -> int:
+    return int(load().crystal_scratch_bytes(kind, n, out_size, ctypes.byref(p) if p is not None else None))
+
+
+def kernel_launches() -> int:
+    return int(load().crystal_kernel_launches())
+
+
+# ---- job runtime ---------------------------------------------------------------
+
+class Task:
+    """One job (Figure 2's job_t): numpy views of the pinned host buffers."""
+
+    def __init__(self, ctx: "Context", handle: int, in_size: int, out_size: int):
+        self.ctx, self.handle = ctx, handle
+        self.in_size, self.out_size = in_size, out_size
+        L = load()
+        hin, hout = L.crystal_task_host_in(handle), L.crystal_task_host_out(handle)
+        self.h_in = np.ctypeslib.as_array((ctypes.c_uint8 * max(in_size, 1)).from_address(hin))[:in_size] \
+            if hin else np.zeros(0, np.uint8)
+        self.h_out = np.ctypeslib.as_array((ctypes.c_uint8 * max(out_size, 1)).from_address(hout))[:out_size] \
+            if hout else np.zeros(0, np.uint8)
+
+    def resize(self, in_size: int, out_size: int):
+        check(load().crystal_task_resize(self.handle, in_size, out_size), "crystal_task_resize")
+        self.in_size, self.out_size = in_size, out_size
+
+    def submit(self, kind: int, p: Optional[crystal_hash_params] = None, callback=None, user=None) -> int:
+        cb = callback if callback is not None else crystal_callback()
+        self._cb_keepalive = cb
+        return load().crystal_task_submit(self.handle, kind, ctypes.byref(p) if p is not None else None, cb, user)
+
+    def poll(self) -> int:
+        return load().crystal_task_poll(self.handle)
+
+    def wait(self, timeout_ns: int = -1) -> int:
+        return load().crystal_task_wait(self.handle, timeout_ns)
+
+    def release(self) -> int:
+        st = load().crystal_task_release(self.handle)
+        if st == CRYSTAL_OK:
+            self.ctx._tasks.discard(self)
+        return st
+
+    def timing(self):
+        a, b, c = _u64(), _u64(), _u64()
+        check(load().crystal_task_timing(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def output(self, n: Optional[int] = None) -> bytes:
+        return self.h_out[: self.out_size if n is None else n].tobytes()
+
+
+class Context:
+    """init(...) / finalize() of Figure 3 as a Python object."""
+
+    def __init__(self, max_in_bytes=64 << 20, max_out_bytes=16 << 20, device_pool_bytes=1 << 30,
+                 host_pool_bytes=512 << 20, n_streams=4, device=0, flags=0, max_batch_jobs=64,
+                 max_batch_bytes=32 << 20, device_arena=None):
+        L = load()
+        cfg = crystal_config()
+        L.crystal_config_default(ctypes.byref(cfg))
+        cfg.max_in_bytes, cfg.max_out_bytes = max_in_bytes, max_out_bytes
+        cfg.device_pool_bytes, cfg.host_pool_bytes = device_pool_bytes, host_pool_bytes
+        cfg.n_streams, cfg.device, cfg.flags = n_streams, device, flags
+        cfg.max_batch_jobs, cfg.max_batch_bytes = max_batch_jobs, max_batch_bytes
+        self._arena_ref = device_arena
+        if device_arena is not None:
+            cfg.device_arena = device_arena.data_ptr()
+            cfg.device_pool_bytes = device_arena.numel() * device_arena.element_size()
+        h = _vp()
+        check(L.crystal_init(ctypes.byref(cfg), ctypes.byref(h)), "crystal_init")
+        self.handle = h.value
+        self._tasks = set()
+
+    def task_create(self, in_size: int, out_size: int) -> Task:
+        h = _vp()
+        st = load().crystal_task_create(self.handle, in_size, out_size, ctypes.byref(h))
+        if st != CRYSTAL_OK:
+            raise CrystalError(st, "crystal_task_create")
+        t = Task(self, h.value, in_size, out_size)
+        self._tasks.add(t)
+        return t
+
+    def stats(self) -> crystal_stats:
+        s = crystal_stats()
+        check(load().crystal_get_stats(self.handle, ctypes.byref(s)), "crystal_get_stats")
+        return s
+
+    def shutdown(self) -> int:
+        if self.handle is None:
+            return CRYSTAL_OK
+        st = load().crystal_shutdown(self.handle)
+        self.handle = None
+        self._tasks.clear()
+        return st
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.shutdown()
+
+
+class CrystalError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {load().crystal_strerror(status).decode()} ({status})")
+
+
+# ---- stateless batch launchers on torch-owned device memory ---------------------
+
+def _align(x: int, a: int) -> int:
+    return (x + a - 1) // a * a
+
+
+class DeviceBatch:
+    """A batch of units living in one device input buffer (a torch uint8
+    tensor), with outputs, scratch and the descriptor in torch-owned device
+    memory.  ``offsets``/``sizes`` locate each unit in ``d_input``; units are
+    reordered direct-first as the descriptor requires, and results come back
+    in the caller's order."""
+
+    def __init__(self, d_input, offsets: Sequence[int], sizes: Sequence[int], kinds: Sequence[int],
+                 p: Optional[crystal_hash_params] = None, out_sizes: Optional[Sequence[int]] = None,
+                 per_unit_params: Optional[Sequence[crystal_hash_params]] = None):
+        import torch
+
+        L = load()
+        if not d_input.is_cuda or d_input.dtype != torch.uint8:
+            raise ValueError("d_input must be a CUDA uint8 tensor")
+        n_units = len(sizes)
+        self.device = d_input.device
+        self.kinds = list(kinds)
+        self.sizes = [int(s) for s in sizes]
+        order = [i for i in range(n_units) if kinds[i] == CRYSTAL_KIND_MD5_DIRECT] + \
+                [i for i in range(n_units) if kinds[i] == CRYSTAL_KIND_MD5_SLIDING]
+        if len(order) != n_units:
+            raise ValueError("kinds must be direct or sliding")
+        self.order = order
+        self.n_direct = sum(1 for k in kinds if k == CRYSTAL_KIND_MD5_DIRECT)
+        self.n_sliding = n_units - self.n_direct
+        plist = per_unit_params or [p if p is not None else params()] * n_units
+        self.params = plist
+        # output and scratch layout, 256-byte aligned per unit
+        self.out_off, self.out_size, self.scr_off = [0] * n_units, [0] * n_units, [0] * n_units
+        o = s = 0
+        for i in range(n_units):
+            pi = plist[i]
+            if out_sizes is not None:
+                osz = int(out_sizes[i])
+            elif kinds[i] == CRYSTAL_KIND_MD5_DIRECT:
+                osz = 16
+            else:
+                osz = L.crystal_out_bytes(kinds[i], self.sizes[i], ctypes.byref(pi))
+            self.out_off[i], self.out_size[i] = o, osz
+            o = _align(o + osz, 256)
+            sb = L.crystal_scratch_bytes(kinds[i], self.sizes[i], osz, ctypes.byref(pi))
+            self.scr_off[i] = s
+            s = _align(s + max(sb, 16), 256)
+        self.d_out = torch.zeros(max(o, 256), dtype=torch.uint8, device=self.device)
+        self.d_scratch = torch.zeros(max(s, 256), dtype=torch.uint8, device=self.device)
+        self.d_input = d_input
+        nbytes = int(L.crystal_batch_bytes(n_units))
+        host = np.zeros(nbytes, dtype=np.uint8)
+        units = host[BATCH_HEADER_BYTES:].view(UNIT_DTYPE)
+        base_in, base_out, base_scr = d_input.data_ptr(), self.d_out.data_ptr(), self.d_scratch.data_ptr()
+        for k, i in enumerate(order):
+            pi = plist[i]
+            u = units[k]
+            u["in"] = base_in + int(offsets[i])
+            u["n"] = self.sizes[i]
+            u["out"] = base_out + self.out_off[i]
+            u["scratch"] = base_scr + self.scr_off[i]
+            u["out_cap"] = self.out_size[i]
+            direct = kinds[i] == CRYSTAL_KIND_MD5_DIRECT
+            u["seg_bytes"] = (pi.segment_bytes if direct else pi.chunk_segment_bytes) or 4096
+            u["window"] = pi.window_bytes or 20
+            u["mask"], u["target"], u["kind"] = pi.mask, pi.target, kinds[i]
+        st = L.crystal_batch_plan(host.ctypes.data, self.n_direct, self.n_sliding)
+        check(st, "crystal_batch_plan")
+        self.host_desc = host
+        self.d_desc = torch.from_numpy(host).to(self.device)
+        self.total_segments = int(host[8:16].view("<u8")[0])
+        self.total_tiles = int(host[16:24].view("<u8")[0])
+
+    @staticmethod
+    def _stream(stream) -> int:
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return s.cuda_stream
+
+    def _launch(self, fn: str, stream=None) -> None:
+        st = getattr(load(), fn)(self.d_desc.data_ptr(), self._stream(stream))
+        check(st, fn)
+
+    def launch(self, stream=None):
+        self._launch("crystal_launch_batch", stream)
+
+    def launch_direct(self, stream=None):
+        self._launch("crystal_launch_direct", stream)
+
+    def launch_direct_segments(self, stream=None):
+        self._launch("crystal_launch_direct_segments", stream)
+
+    def launch_direct_outer(self, stream=None):
+        self._launch("crystal_launch_direct_outer", stream)
+
+    def launch_sliding(self, stream=None):
+        self._launch("crystal_launch_sliding", stream)
+
+    def launch_sliding_windows(self, stream=None):
+        self._launch("crystal_launch_sliding_windows", stream)
+
+    def launch_sliding_chunks(self, stream=None):
+        self._launch("crystal_launch_sliding_chunks", stream)
+
+    def launch_sliding_digests(self, stream=None):
+        self._launch("crystal_launch_sliding_digests", stream)
+
+    def device_status(self) -> int:
+        return int(self.d_desc[:64].cpu().numpy()[28:32].view("<u4")[0])
+
+    def outputs(self) -> List[bytes]:
+        """Each unit's output bytes, in the caller's order."""
+        host = self.d_out.cpu().numpy()
+        return [host[self.out_off[i]:self.out_off[i] + self.out_size[i]].tobytes() for i in range(len(self.sizes))]

@@ -1,0 +1,36 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "crystal.h"
+
+namespace crystal {
+
+extern std::atomic<uint64_t> g_kernel_launches;
+
+// Kernel launchers on a device-resident batch (kernels.cu).
+int launch_direct_segments(crystal_batch* b, cudaStream_t s);
+int launch_direct_outer(crystal_batch* b, cudaStream_t s);
+int launch_sliding_windows(crystal_batch* b, cudaStream_t s);
+int launch_sliding_chunks(crystal_batch* b, cudaStream_t s);
+int launch_sliding_digests(crystal_batch* b, cudaStream_t s);  // two kernels
+
+inline crystal_unit* batch_units(crystal_batch* b) {
+    return reinterpret_cast<crystal_unit*>(reinterpret_cast<uint8_t*>(b) + sizeof(crystal_batch));
+}
+
+constexpr uint32_t kMaxWindow = 55;  // a window message fits one MD5 block
+
+inline uint64_t segments_of(uint64_t n, uint64_t S) { return n == 0 ? 1 : (n + S - 1) / S; }
+inline uint64_t bitmap_words(uint64_t n) { return (n + 31) / 32; }
+inline uint64_t sliding_fixed_bytes(uint64_t n) { return 8 + 4 * bitmap_words(n); }
+inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) & ~(a - 1); }
+
+}  // namespace crystal
+
+static_assert(sizeof(crystal_unit) == 64, "unit record is 64 bytes");
+static_assert(sizeof(crystal_batch) == 64, "batch header is 64 bytes");

@@ -1,0 +1,518 @@
+// Hashing kernels of one batch (sm_103a) and their stateless launchers.
+//
+//   k_direct_segments  K1  one MD5 per segment of every direct unit
+//   k_direct_outer     K2  MD5 over each unit's concatenated segment digests
+//   k_sliding_windows  K3  MD5 of every w-byte window, boundary bitmap
+//   k_sliding_chunks   K4  chunk ends from the bitmap, per-chunk segment table
+//   k_chunk_segments   K5a one MD5 per segment of every chunk
+//   k_chunk_outer      K5b MD5 over each chunk's segment digests
+//
+// Direct hashing is StoreGPU's direct hashing (Section 5.2, Figure 6 of the
+// CrystalGPU paper; the paper's CPU post-processing step, the hash of the
+// digests, runs on the GPU here as K2).  Sliding-window hashing is the
+// content-defined chunking of content-addressable storage (Section 2.2).
+//
+// Every kernel is persistent: a fixed grid sized to the device walks the work
+// of whatever batch the device-resident header describes, so one launch
+// sequence (or one captured graph) serves every batch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "crystal.h"
+#include "crystal_internal.h"
+#include "md5_device.cuh"
+
+namespace crystal {
+
+std::atomic<uint64_t> g_kernel_launches{0};
+
+namespace {
+
+constexpr int kTile = CRYSTAL_SLIDING_TILE;  // window offsets per tile
+constexpr int kWinThreads = 256;             // 8 warps x 4 windows x 32 lanes = 1024
+constexpr int kWinPerThread = kTile / kWinThreads;
+static_assert(kWinPerThread == 4, "window tile layout assumes 4 windows per thread");
+// Staged bytes per tile: 1024 offsets + up to 54 halo bytes + 15 alignment bytes,
+// rounded to whole 16-byte vectors, plus room for the last window's word reads.
+constexpr int kStageWords = 284;
+
+constexpr int kSegThreads = 128;
+constexpr int kChunkThreads = 512;
+constexpr int kDigestThreads = 256;
+
+constexpr uint32_t kDevBadRecord = 1u;
+
+__device__ __forceinline__ crystal_unit* units_of(crystal_batch* b) {
+    return reinterpret_cast<crystal_unit*>(reinterpret_cast<uint8_t*>(b) + sizeof(crystal_batch));
+}
+
+// Last unit in [lo, lo + cnt) whose work_begin <= g (units with no work share
+// their successor's begin, so the last one is the owner).
+__device__ __forceinline__ uint32_t owner_of(const crystal_unit* U, uint32_t cnt, uint64_t g) {
+    uint32_t lo = 0, hi = cnt;  // answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (U[mid].work_begin <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void store_digest(uint8_t* dst, const uint32_t (&st)[4]) {
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);  // 4-byte aligned by contract
+    d[0] = st[0];
+    d[1] = st[1];
+    d[2] = st[2];
+    d[3] = st[3];
+}
+
+__device__ __forceinline__ void store_digest16(uint8_t* dst, const uint32_t (&st)[4]) {
+    *reinterpret_cast<uint4*>(dst) = make_uint4(st[0], st[1], st[2], st[3]);
+}
+
+__device__ __forceinline__ uint64_t num_segments(uint64_t n, uint32_t S) {
+    return n == 0 ? 1 : (n + S - 1) / S;
+}
+
+// ---- K1: segment digests of direct units ------------------------------------
+
+__global__ void __launch_bounds__(kSegThreads) k_direct_segments(crystal_batch* B) {
+    const uint32_t nd = B->n_direct;
+    const uint64_t total = B->direct_segments;
+    const crystal_unit* U = units_of(B);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const uint32_t u = owner_of(U, nd, g);
+        const crystal_unit X = U[u];
+        const uint64_t j = g - X.work_begin;
+        const uint64_t off = j * X.seg_bytes;
+        const uint64_t len = X.n > off ? (X.n - off < X.seg_bytes ? X.n - off : X.seg_bytes) : 0;
+        uint32_t st[4];
+        md5::digest_global(reinterpret_cast<const uint8_t*>(X.in) + off, len, st);
+        store_digest16(reinterpret_cast<uint8_t*>(X.scratch) + 16 * j, st);
+    }
+}
+
+// ---- K2: digest of digests -------------------------------------------------
+
+__global__ void __launch_bounds__(kDigestThreads) k_direct_outer(crystal_batch* B) {
+    const uint32_t nd = B->n_direct;
+    const crystal_unit* U = units_of(B);
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nd; u += gridDim.x * blockDim.x) {
+        const crystal_unit X = U[u];
+        const uint64_t m = num_segments(X.n, X.seg_bytes);
+        uint32_t st[4];
+        md5::digest_global(reinterpret_cast<const uint8_t*>(X.scratch), 16 * m, st);
+        store_digest(reinterpret_cast<uint8_t*>(X.out), st);
+    }
+}
+
+// ---- K3: window digests and boundary bitmap ---------------------------------
+
+// Message block of the window starting at staged byte p.  W > 0: the window
+// length is the compile-time constant W (constant padding words fold away);
+// W == 0: the length w is taken at run time.
+template <int W>
+__device__ __forceinline__ void window_block(const uint32_t* sw, uint32_t p, uint32_t w,
+                                             uint32_t (&X)[16]) {
+    const uint32_t q = p >> 2;
+    const uint32_t sh = (p & 3) * 8;
+    if constexpr (W > 0) {
+        constexpr int full = W / 4;
+        constexpr int part = W % 4;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) X[k] = 0;
+#pragma unroll
+        for (int k = 0; k < full; ++k) X[k] = __funnelshift_r(sw[q + k], sw[q + k + 1], sh);
+        if constexpr (part > 0) {
+            const uint32_t v = __funnelshift_r(sw[q + full], sw[q + full + 1], sh);
+            X[full] = (v & ((1u << (8 * part)) - 1u)) | (0x80u << (8 * part));
+        } else {
+            X[full] = 0x80u;
+        }
+        X[14] = 8u * W;
+        X[15] = 0;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            const int have = (int)w - 4 * k;
+            uint32_t v = 0;
+            if (have > 0) {
+                v = __funnelshift_r(sw[q + k], sw[q + k + 1], sh);
+                if (have < 4) v &= (1u << (8 * have)) - 1u;
+            }
+            if (have >= 0 && have < 4) v |= 0x80u << (8 * have);
+            X[k] = v;
+        }
+        X[14] = 8u * w;
+        X[15] = 0;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t delta, uint64_t base,
+                                                 uint64_t n, uint32_t w, uint32_t mask,
+                                                 uint32_t target) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t A[kWinPerThread];
+#pragma unroll
+    for (int r = 0; r < kWinPerThread; ++r) {
+        const uint32_t rel = warp * 128 + r * 32 + lane;
+        uint32_t X[16];
+        window_block<W>(sw, rel + delta, w, X);
+        A[r] = md5::first_word_one_block(X);
+    }
+    uint32_t mine = 0;
+#pragma unroll
+    for (int r = 0; r < kWinPerThread; ++r) {
+        const uint64_t i = base + warp * 128 + r * 32 + lane;
+        const bool hit = (i + w <= n) && ((A[r] & mask) == target);
+        const uint32_t word = __ballot_sync(0xffffffffu, hit);
+        if (lane == (uint32_t)r) mine = word;
+    }
+    return mine;
+}
+
+__global__ void __launch_bounds__(kWinThreads) k_sliding_windows(crystal_batch* B) {
+    __shared__ __align__(16) uint32_t sw[kStageWords];
+    const uint32_t ns = B->n_sliding;
+    const uint64_t total = B->sliding_tiles;
+    const crystal_unit* U = units_of(B) + B->n_direct;
+    for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const uint32_t u = owner_of(U, ns, t);
+        const crystal_unit X = U[u];
+        const uint64_t base = (t - X.work_begin) * (uint64_t)kTile;
+        const uint32_t w = X.window;
+        // Stage bytes [base, min(n, base + kTile + w - 1)) from their 16-byte
+        // aligned block on; vectors past the unit's end are not loaded.
+        const uint64_t a = X.in + base;
+        const uint32_t delta = (uint32_t)(a & 15);
+        const uint64_t a0 = a - delta;
+        const uint64_t want = X.n - base < (uint64_t)(kTile + w - 1) ? X.n - base : (uint64_t)(kTile + w - 1);
+        const uint32_t nvec = (uint32_t)((delta + want + 15) >> 4);
+        uint4* sv = reinterpret_cast<uint4*>(sw);
+        for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
+            sv[v] = md5::ldg_stream16(reinterpret_cast<const void*>(a0 + 16ull * v));
+        }
+        __syncthreads();
+        uint32_t mine;
+        if (w == 20) {
+            mine = tile_windows<20>(sw, delta, base, X.n, w, X.mask, X.target);
+        } else {
+            mine = tile_windows<0>(sw, delta, base, X.n, w, X.mask, X.target);
+        }
+        const uint32_t lane = threadIdx.x & 31;
+        if (lane < (uint32_t)kWinPerThread) {
+            const uint64_t word = (base >> 5) + (threadIdx.x >> 5) * 4 + lane;
+            if (word < ((X.n + 31) >> 5)) {
+                reinterpret_cast<uint32_t*>(X.out + 8)[word] = mine;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- K4: chunk ends and per-chunk segment table ------------------------------
+
+template <int NT>
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* sh, uint64_t& total) {
+    // sh holds NT/32 + 1 entries
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t s = lane < NT / 32 ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < NT / 32) sh[lane] = s;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint64_t before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+    total = sh[NT / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch* B) {
+    __shared__ uint64_t scan_sh[kChunkThreads / 32 + 1];
+    const uint32_t ns = B->n_sliding;
+    crystal_unit* U = units_of(B) + B->n_direct;
+    for (uint32_t u = blockIdx.x; u < ns; u += gridDim.x) {
+        const crystal_unit X = U[u];
+        const uint64_t n = X.n;
+        const uint64_t words = (n + 31) >> 5;
+        const uint64_t fixed = 8 + 4 * words;
+        uint32_t* hdr = reinterpret_cast<uint32_t*>(X.out);
+        const uint32_t* bm = hdr + 2;
+        uint32_t* seg_prefix = reinterpret_cast<uint32_t*>(X.scratch);
+        if (X.out_cap < fixed) {
+            if (threadIdx.x == 0) atomicOr(&B->status, kDevBadRecord);
+            continue;
+        }
+        const uint64_t cap = (X.out_cap - fixed) / 20;
+        // pass 1: boundary count per contiguous word range
+        const uint64_t per = (words + kChunkThreads - 1) / kChunkThreads;
+        const uint64_t lo = threadIdx.x * per;
+        const uint64_t hi = lo + per < words ? lo + per : words;
+        uint64_t cnt = 0;
+        for (uint64_t j = lo; j < hi; ++j) cnt += __popc(bm[j]);
+        uint64_t pop;
+        uint64_t k = block_exclusive_scan<kChunkThreads>(cnt, scan_sh, pop);
+        bool last_set = false;
+        if (n >= X.window) {
+            const uint64_t i = n - X.window;
+            last_set = (bm[i >> 5] >> (i & 31)) & 1u;
+        }
+        const uint64_t n_chunks = pop + (last_set ? 0 : 1);
+        const bool fits = n_chunks <= cap;
+        if (threadIdx.x == 0) {
+            hdr[0] = (uint32_t)n_chunks;
+            hdr[1] = fits ? 0u : 1u;
+        }
+        if (!fits) {
+            if (threadIdx.x == 0) seg_prefix[0] = 0;  // no chunk segments to hash
+            __syncthreads();
+            continue;
+        }
+        uint32_t* ends = hdr + 2 + words;
+        for (uint64_t j = lo; j < hi; ++j) {
+            uint32_t x = bm[j];
+            while (x) {
+                const int b = __ffs(x) - 1;
+                x &= x - 1;
+                ends[k++] = (uint32_t)(32 * j + b + X.window);
+            }
+        }
+        if (threadIdx.x == 0 && !last_set) ends[n_chunks - 1] = (uint32_t)n;
+        __syncthreads();
+        // pass 2: segments per chunk, exclusive prefix into the scratch table
+        const uint64_t cper = (n_chunks + kChunkThreads - 1) / kChunkThreads;
+        const uint64_t clo = threadIdx.x * cper;
+        const uint64_t chi = clo + cper < n_chunks ? clo + cper : n_chunks;
+        const uint32_t S = X.seg_bytes;
+        uint64_t segs = 0;
+        for (uint64_t c = clo; c < chi; ++c) {
+            const uint64_t start = c == 0 ? 0 : ends[c - 1];
+            segs += num_segments(ends[c] - start, S);
+        }
+        uint64_t total_segs;
+        uint64_t run = block_exclusive_scan<kChunkThreads>(segs, scan_sh, total_segs);
+        for (uint64_t c = clo; c < chi; ++c) {
+            seg_prefix[c] = (uint32_t)run;
+            const uint64_t start = c == 0 ? 0 : ends[c - 1];
+            run += num_segments(ends[c] - start, S);
+        }
+        if (threadIdx.x == 0) seg_prefix[n_chunks] = (uint32_t)total_segs;
+        __syncthreads();
+    }
+}
+
+// Scratch of a sliding unit: u32 seg_prefix[cap + 1], then 16-byte aligned
+// segment digests.
+__device__ __forceinline__ uint8_t* chunk_digest_area(const crystal_unit& X, uint64_t cap) {
+    return reinterpret_cast<uint8_t*>(X.scratch) + ((4 * (cap + 1) + 15) & ~uint64_t(15));
+}
+
+// ---- K5a: chunk segment digests ---------------------------------------------
+
+__global__ void __launch_bounds__(kDigestThreads) k_chunk_segments(crystal_batch* B) {
+    const uint32_t ns = B->n_sliding;
+    const crystal_unit* U = units_of(B) + B->n_direct;
+    for (uint32_t u = blockIdx.x; u < ns; u += gridDim.x) {
+        const crystal_unit X = U[u];
+        const uint64_t words = (X.n + 31) >> 5;
+        const uint64_t fixed = 8 + 4 * words;
+        if (X.out_cap < fixed) continue;
+        const uint32_t* hdr = reinterpret_cast<const uint32_t*>(X.out);
+        if (hdr[1] & 1u) continue;
+        const uint32_t n_chunks = hdr[0];
+        const uint64_t cap = (X.out_cap - fixed) / 20;
+        const uint32_t* ends = hdr + 2 + words;
+        const uint32_t* seg_prefix = reinterpret_cast<const uint32_t*>(X.scratch);
+        const uint32_t T = seg_prefix[n_chunks];
+        uint8_t* dig = chunk_digest_area(X, cap);
+        const uint32_t S = X.seg_bytes;
+        for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) {
+            // chunk c: last with seg_prefix[c] <= t
+            uint32_t lo = 0, hi = n_chunks;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (seg_prefix[mid] <= t) lo = mid; else hi = mid;
+            }
+            const uint64_t start = lo == 0 ? 0 : ends[lo - 1];
+            const uint64_t end = ends[lo];
+            const uint64_t off = start + (uint64_t)(t - seg_prefix[lo]) * S;
+            const uint64_t len = end > off ? (end - off < S ? end - off : S) : 0;
+            uint32_t st[4];
+            md5::digest_global(reinterpret_cast<const uint8_t*>(X.in) + off, len, st);
+            store_digest16(dig + 16ull * t, st);
+        }
+    }
+}
+
+// ---- K5b: chunk digests ------------------------------------------------------
+
+__global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B) {
+    const uint32_t ns = B->n_sliding;
+    const crystal_unit* U = units_of(B) + B->n_direct;
+    for (uint32_t u = blockIdx.x; u < ns; u += gridDim.x) {
+        const crystal_unit X = U[u];
+        const uint64_t words = (X.n + 31) >> 5;
+        const uint64_t fixed = 8 + 4 * words;
+        if (X.out_cap < fixed) continue;
+        uint32_t* hdr = reinterpret_cast<uint32_t*>(X.out);
+        if (hdr[1] & 1u) continue;
+        const uint32_t n_chunks = hdr[0];
+        const uint64_t cap = (X.out_cap - fixed) / 20;
+        const uint32_t* seg_prefix = reinterpret_cast<const uint32_t*>(X.scratch);
+        const uint8_t* dig = chunk_digest_area(X, cap);
+        uint8_t* out_dig = reinterpret_cast<uint8_t*>(hdr + 2 + words + n_chunks);
+        for (uint32_t c = threadIdx.x; c < n_chunks; c += blockDim.x) {
+            const uint32_t s0 = seg_prefix[c], s1 = seg_prefix[c + 1];
+            uint32_t st[4];
+            md5::digest_global(dig + 16ull * s0, 16ull * (s1 - s0), st);
+            store_digest(out_dig + 16ull * c, st);
+        }
+    }
+}
+
+// ---- launch geometry -----------------------------------------------------------
+
+struct Geometry {
+    int sms = 0;
+    int seg_blocks = 0, outer_blocks = 0, win_blocks = 0, unit_blocks = 0;
+};
+
+constexpr int kMaxDevices = 64;
+Geometry g_geom[kMaxDevices];
+std::once_flag g_geom_once[kMaxDevices];
+
+const Geometry* geometry() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::call_once(g_geom_once[dev], [dev] {
+        Geometry g;
+        cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direct_segments, kSegThreads, 0);
+        g.seg_blocks = g.sms * (occ > 0 ? occ : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sliding_windows, kWinThreads, 0);
+        g.win_blocks = g.sms * (occ > 0 ? occ : 1);
+        g.outer_blocks = g.sms * 2;
+        g.unit_blocks = g.sms * 2;
+        g_geom[dev] = g;
+    });
+    return g_geom[dev].sms > 0 ? &g_geom[dev] : nullptr;
+}
+
+int launched(cudaError_t e, int kernels) {
+    if (e != cudaSuccess) return CRYSTAL_EDEVICE;
+    g_kernel_launches.fetch_add((uint64_t)kernels, std::memory_order_relaxed);
+    return CRYSTAL_OK;
+}
+
+}  // namespace
+
+int launch_direct_segments(crystal_batch* b, cudaStream_t s) {
+    const Geometry* g = geometry();
+    if (!g) return CRYSTAL_EDEVICE;
+    k_direct_segments<<<g->seg_blocks, kSegThreads, 0, s>>>(b);
+    return launched(cudaGetLastError(), 1);
+}
+
+int launch_direct_outer(crystal_batch* b, cudaStream_t s) {
+    const Geometry* g = geometry();
+    if (!g) return CRYSTAL_EDEVICE;
+    k_direct_outer<<<g->outer_blocks, kDigestThreads, 0, s>>>(b);
+    return launched(cudaGetLastError(), 1);
+}
+
+int launch_sliding_windows(crystal_batch* b, cudaStream_t s) {
+    const Geometry* g = geometry();
+    if (!g) return CRYSTAL_EDEVICE;
+    k_sliding_windows<<<g->win_blocks, kWinThreads, 0, s>>>(b);
+    return launched(cudaGetLastError(), 1);
+}
+
+int launch_sliding_chunks(crystal_batch* b, cudaStream_t s) {
+    const Geometry* g = geometry();
+    if (!g) return CRYSTAL_EDEVICE;
+    k_sliding_chunks<<<g->unit_blocks, kChunkThreads, 0, s>>>(b);
+    return launched(cudaGetLastError(), 1);
+}
+
+int launch_sliding_digests(crystal_batch* b, cudaStream_t s) {
+    const Geometry* g = geometry();
+    if (!g) return CRYSTAL_EDEVICE;
+    k_chunk_segments<<<g->unit_blocks, kDigestThreads, 0, s>>>(b);
+    if (cudaGetLastError() != cudaSuccess) return CRYSTAL_EDEVICE;
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_chunk_outer<<<g->unit_blocks, kDigestThreads, 0, s>>>(b);
+    return launched(cudaGetLastError(), 1);
+}
+
+}  // namespace crystal
+
+using namespace crystal;
+
+extern "C" {
+
+int crystal_launch_direct_segments(const crystal_batch* b, void* stream) {
+    if (!b) return CRYSTAL_EINVAL;
+    return launch_direct_segments(const_cast<crystal_batch*>(b), (cudaStream_t)stream);
+}
+
+int crystal_launch_direct_outer(const crystal_batch* b, void* stream) {
+    if (!b) return CRYSTAL_EINVAL;
+    return launch_direct_outer(const_cast<crystal_batch*>(b), (cudaStream_t)stream);
+}
+
+int crystal_launch_direct(const crystal_batch* b, void* stream) {
+    int st = crystal_launch_direct_segments(b, stream);
+    if (st != CRYSTAL_OK) return st;
+    return crystal_launch_direct_outer(b, stream);
+}
+
+int crystal_launch_sliding_windows(const crystal_batch* b, void* stream) {
+    if (!b) return CRYSTAL_EINVAL;
+    return launch_sliding_windows(const_cast<crystal_batch*>(b), (cudaStream_t)stream);
+}
+
+int crystal_launch_sliding_chunks(const crystal_batch* b, void* stream) {
+    if (!b) return CRYSTAL_EINVAL;
+    return launch_sliding_chunks(const_cast<crystal_batch*>(b), (cudaStream_t)stream);
+}
+
+int crystal_launch_sliding_digests(const crystal_batch* b, void* stream) {
+    if (!b) return CRYSTAL_EINVAL;
+    return launch_sliding_digests(const_cast<crystal_batch*>(b), (cudaStream_t)stream);
+}
+
+int crystal_launch_sliding(const crystal_batch* b, void* stream) {
+    int st = crystal_launch_sliding_windows(b, stream);
+    if (st == CRYSTAL_OK) st = crystal_launch_sliding_chunks(b, stream);
+    if (st == CRYSTAL_OK) st = crystal_launch_sliding_digests(b, stream);
+    return st;
+}
+
+int crystal_launch_batch(const crystal_batch* b, void* stream) {
+    int st = crystal_launch_direct(b, stream);
+    if (st == CRYSTAL_OK) st = crystal_launch_sliding(b, stream);
+    return st;
+}
+
+uint64_t crystal_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// Host-side planning of a batch and the arena allocator behind the pools.
+//
+// The arena is the bookkeeping of the paper's buffer pool (Section 3: buffers
+// pre-allocated once at init and handed out by job_get / job_put): one large
+// region, carved into 256-byte-aligned blocks, best fit, freed blocks merged
+// with their free neighbours.  It holds offsets only, so the same code serves
+// the device arena and the pinned host arena, and runs without a GPU.
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <unordered_map>
+
+#include "crystal.h"
+#include "crystal_internal.h"
+
+using namespace crystal;
+
+struct crystal_arena {
+    uint64_t size = 0;
+    uint64_t align = 256;
+    uint64_t used = 0;
+    std::map<uint64_t, uint64_t> free_by_off;             // offset -> length
+    std::set<std::pair<uint64_t, uint64_t>> free_by_len;  // (length, offset)
+    std::unordered_map<uint64_t, uint64_t> live;          // offset -> length
+    std::mutex mu;
+
+    void insert_free(uint64_t off, uint64_t len) {
+        free_by_off.emplace(off, len);
+        free_by_len.emplace(len, off);
+    }
+    void erase_free(std::map<uint64_t, uint64_t>::iterator it) {
+        free_by_len.erase({it->second, it->first});
+        free_by_off.erase(it);
+    }
+};
+
+extern "C" {
+
+int crystal_arena_create(uint64_t bytes, uint64_t alignment, crystal_arena** out) {
+    if (!out || bytes == 0 || alignment == 0 || (alignment & (alignment - 1))) return CRYSTAL_EINVAL;
+    crystal_arena* a = new (std::nothrow) crystal_arena;
+    if (!a) return CRYSTAL_ENOMEM;
+    a->size = bytes;
+    a->align = alignment;
+    a->insert_free(0, bytes);
+    *out = a;
+    return CRYSTAL_OK;
+}
+
+int crystal_arena_alloc(crystal_arena* a, uint64_t bytes, uint64_t* offset) {
+    if (!a || !offset) return CRYSTAL_EINVAL;
+    const uint64_t want = align_up(bytes ? bytes : 1, a->align);
+    if (want < bytes) return CRYSTAL_EAGAIN;  // overflow
+    std::lock_guard<std::mutex> lk(a->mu);
+    auto it = a->free_by_len.lower_bound({want, 0});
+    if (it == a->free_by_len.end()) return CRYSTAL_EAGAIN;
+    const uint64_t len = it->first, off = it->second;
+    a->free_by_len.erase(it);
+    a->free_by_off.erase(off);
+    if (len > want) a->insert_free(off + want, len - want);
+    a->live.emplace(off, want);
+    a->used += want;
+    *offset = off;
+    return CRYSTAL_OK;
+}
+
+int crystal_arena_free(crystal_arena* a, uint64_t offset) {
+    if (!a) return CRYSTAL_EINVAL;
+    std::lock_guard<std::mutex> lk(a->mu);
+    auto lv = a->live.find(offset);
+    if (lv == a->live.end()) return CRYSTAL_EINVAL;
+    uint64_t off = lv->first, len = lv->second;
+    a->live.erase(lv);
+    a->used -= len;
+    auto next = a->free_by_off.lower_bound(off);
+    if (next != a->free_by_off.end() && next->first == off + len) {
+        len += next->second;
+        a->erase_free(next);
+    }
+    auto prev = a->free_by_off.lower_bound(off);
+    if (prev != a->free_by_off.begin()) {
+        --prev;
+        if (prev->first + prev->second == off) {
+            off = prev->first;
+            len += prev->second;
+            a->erase_free(prev);
+        }
+    }
+    a->insert_free(off, len);
+    return CRYSTAL_OK;
+}
+
+uint64_t crystal_arena_used(crystal_arena* a) {
+    if (!a) return 0;
+    std::lock_guard<std::mutex> lk(a->mu);
+    return a->used;
+}
+
+uint64_t crystal_arena_largest_free(crystal_arena* a) {
+    if (!a) return 0;
+    std::lock_guard<std::mutex> lk(a->mu);
+    return a->free_by_len.empty() ? 0 : a->free_by_len.rbegin()->first;
+}
+
+void crystal_arena_destroy(crystal_arena* a) { delete a; }
+
+// ---- parameters and sizes -----------------------------------------------------
+
+void crystal_params_default(crystal_hash_params* p) {
+    if (!p) return;
+    p->segment_bytes = 4096;
+    p->window_bytes = 20;
+    p->mask = 0x1FFF;
+    p->target = 0x1FFF;
+    p->chunk_segment_bytes = 4096;
+    p->reserved = 0;
+}
+
+uint64_t crystal_sliding_out_bytes(uint64_t in_size, uint64_t max_chunks) {
+    return sliding_fixed_bytes(in_size) + 20 * max_chunks;
+}
+
+uint64_t crystal_out_bytes(int kind, uint64_t in_size, const crystal_hash_params* params) {
+    crystal_hash_params p;
+    crystal_params_default(&p);
+    if (params) {
+        if (params->window_bytes) p.window_bytes = params->window_bytes;
+    }
+    switch (kind) {
+    case CRYSTAL_KIND_NOP: return in_size;
+    case CRYSTAL_KIND_MD5_DIRECT: return 16;
+    case CRYSTAL_KIND_MD5_SLIDING: {
+        const uint64_t windows = in_size >= p.window_bytes ? in_size - p.window_bytes + 1 : 0;
+        return crystal_sliding_out_bytes(in_size, windows + 1);
+    }
+    default: return 0;
+    }
+}
+
+uint64_t crystal_scratch_bytes(int kind, uint64_t n, uint64_t out_size, const crystal_hash_params* params) {
+    crystal_hash_params p;
+    crystal_params_default(&p);
+    if (params) {
+        if (params->segment_bytes) p.segment_bytes = params->segment_bytes;
+        if (params->chunk_segment_bytes) p.chunk_segment_bytes = params->chunk_segment_bytes;
+    }
+    if (kind == CRYSTAL_KIND_MD5_DIRECT) return 16 * segments_of(n, p.segment_bytes);
+    if (kind == CRYSTAL_KIND_MD5_SLIDING) {
+        const uint64_t fixed = sliding_fixed_bytes(n);
+        if (out_size < fixed) return 0;
+        const uint64_t cap = (out_size - fixed) / 20;
+        const uint64_t table = align_up(4 * (cap + 1), 16);
+        const uint64_t chunk_segments = cap + (n + p.chunk_segment_bytes - 1) / p.chunk_segment_bytes + 1;
+        return table + 16 * chunk_segments;
+    }
+    return 0;
+}
+
+uint64_t crystal_batch_bytes(uint32_t n_units) {
+    return sizeof(crystal_batch) + (uint64_t)n_units * sizeof(crystal_unit);
+}
+
+int crystal_batch_plan(crystal_batch* b, uint32_t n_direct, uint32_t n_sliding) {
+    if (!b) return CRYSTAL_EINVAL;
+    crystal_unit* U = batch_units(b);
+    uint64_t segs = 0, tiles = 0;
+    uint32_t wmax = 0;
+    for (uint32_t i = 0; i < n_direct; ++i) {
+        crystal_unit& x = U[i];
+        if (x.kind != CRYSTAL_KIND_MD5_DIRECT || x.seg_bytes == 0 || x.out_cap < 16) return CRYSTAL_EINVAL;
+        if ((x.scratch & 15) || (x.out & 3) || !x.scratch || !x.out || (!x.in && x.n)) return CRYSTAL_EINVAL;
+        x.work_begin = segs;
+        segs += segments_of(x.n, x.seg_bytes);
+    }
+    for (uint32_t i = n_direct; i < n_direct + n_sliding; ++i) {
+        crystal_unit& x = U[i];
+        if (x.kind != CRYSTAL_KIND_MD5_SLIDING || x.seg_bytes == 0) return CRYSTAL_EINVAL;
+        if (x.window == 0 || x.window > kMaxWindow || x.n >= (1ull << 32)) return CRYSTAL_EINVAL;
+        if (x.out_cap < sliding_fixed_bytes(x.n)) return CRYSTAL_EINVAL;
+        if ((x.scratch & 15) || (x.out & 3) || !x.scratch || !x.out || (!x.in && x.n)) return CRYSTAL_EINVAL;
+        x.work_begin = tiles;
+        tiles += (x.n + CRYSTAL_SLIDING_TILE - 1) / CRYSTAL_SLIDING_TILE;
+        if (x.window > wmax) wmax = x.window;
+    }
+    b->n_direct = n_direct;
+    b->n_sliding = n_sliding;
+    b->direct_segments = segs;
+    b->sliding_tiles = tiles;
+    b->window_max = wmax;
+    b->status = 0;
+    memset(b->reserved, 0, sizeof b->reserved);
+    return CRYSTAL_OK;
+}
+
+const char* crystal_strerror(int status) {
+    switch (status) {
+    case CRYSTAL_OK: return "ok";
+    case CRYSTAL_PENDING: return "pending";
+    case CRYSTAL_EINVAL: return "invalid argument or state";
+    case CRYSTAL_EAGAIN: return "pool has no room now";
+    case CRYSTAL_ENOMEM: return "allocation failed";
+    case CRYSTAL_ETIMEDOUT: return "timed out";
+    case CRYSTAL_EOVERFLOW: return "output buffer too small for the chunk records";
+    case CRYSTAL_ESHUTDOWN: return "context is shutting down";
+    case CRYSTAL_EDEVICE: return "CUDA or device-side error";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,777 @@
+// Job runtime: the CrystalGPU master module on one B300.
+//
+// Section 4.2 of the paper: a host master thread owns the GPU, jobs move
+// through idle / outstanding / running states, the master takes outstanding
+// jobs in FIFO order, runs each as copy-in / kernel / copy-out (Figure 4) on
+// one of several streams so that the stages of different jobs overlap, finds
+// completion by polling (Section 4.1: no completion interrupt) and runs the
+// job's callback.  Section 3: job buffers come from a pool allocated once at
+// init (one device arena, one pinned host arena) instead of per job.
+//
+// B300 specifics: the master groups the outstanding jobs it finds into one
+// batch per stream slot, so a batch costs one descriptor upload and one
+// persistent-kernel chain however many jobs it holds; with
+// CRYSTAL_FLAG_GRAPHS that chain is a captured CUDA graph.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_set>
+#include <vector>
+
+#include "crystal.h"
+#include "crystal_internal.h"
+
+using namespace crystal;
+
+namespace {
+
+uint64_t now_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+enum TaskState : int { T_IDLE = 0, T_OUTSTANDING = 1, T_RUNNING = 2, T_DONE = 3 };
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;  // slots beyond the first n_streams share a stream
+    cudaEvent_t done = nullptr;
+    crystal_batch* h_desc = nullptr;  // pinned
+    crystal_batch* d_desc = nullptr;  // device, inside the device arena
+    uint64_t d_desc_off = 0;
+    std::vector<crystal_task*> tasks;
+    bool busy = false;
+    uint64_t seq = 0;
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // index: has_direct | has_sliding<<1
+};
+
+thread_local const crystal_ctx* tl_callback_ctx = nullptr;
+
+}  // namespace
+
+struct crystal_task {
+    crystal_ctx* ctx = nullptr;
+    uint8_t* h_in = nullptr;
+    uint8_t* h_out = nullptr;
+    uint8_t* d_in = nullptr;
+    uint8_t* d_out = nullptr;
+    uint8_t* d_scratch = nullptr;
+    uint64_t h_in_off = 0, h_out_off = 0, d_in_off = 0, d_out_off = 0, d_scratch_off = 0;
+    uint64_t in_cap = 0, out_cap = 0, in_size = 0, out_size = 0, scratch_bytes = 0;
+    int kind = 0;
+    crystal_hash_params params{};
+    crystal_callback cb = nullptr;
+    void* user = nullptr;
+    int state = T_IDLE;
+    int status = CRYSTAL_EINVAL;
+    bool submitted_once = false;
+    bool release_in_callback = false;
+    uint64_t t_submit = 0, t_dispatch = 0, t_done = 0;
+};
+
+struct crystal_ctx {
+    crystal_config cfg{};
+    int device = 0;
+    bool pooled = true;
+    uint8_t* d_base = nullptr;
+    bool own_d_base = false;
+    crystal_arena* d_arena = nullptr;
+    uint8_t* h_base = nullptr;
+    crystal_arena* h_arena = nullptr;
+    std::vector<Slot> slots;
+    uint32_t next_slot = 0;
+    uint32_t max_jobs = 64;
+    uint64_t max_bytes = 32ull << 20;
+
+    std::mutex mu;
+    std::condition_variable cv_master;
+    std::condition_variable cv_done;
+    std::deque<crystal_task*> outstanding;
+    std::deque<uint32_t> running;  // slot indices in dispatch order
+    std::unordered_set<crystal_task*> tasks;
+    std::thread master;
+    bool stop = false;
+    bool accepting = true;
+    uint64_t seq = 0;
+
+    std::atomic<uint64_t> jobs_completed{0};
+    std::atomic<uint64_t> batches{0};
+    uint64_t n_running_jobs = 0;
+};
+
+namespace {
+
+// ---- buffers ------------------------------------------------------------------
+
+int alloc_device(crystal_ctx* c, uint64_t bytes, uint8_t** p, uint64_t* off) {
+    if (c->pooled) {
+        int st = crystal_arena_alloc(c->d_arena, bytes, off);
+        if (st != CRYSTAL_OK) return st;
+        *p = c->d_base + *off;
+        return CRYSTAL_OK;
+    }
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes ? bytes : 1) != cudaSuccess) {
+        cudaGetLastError();
+        return CRYSTAL_ENOMEM;
+    }
+    *p = (uint8_t*)q;
+    return CRYSTAL_OK;
+}
+
+void free_device(crystal_ctx* c, uint8_t* p, uint64_t off) {
+    if (!p) return;
+    if (c->pooled) crystal_arena_free(c->d_arena, off);
+    else cudaFree(p);
+}
+
+int alloc_host(crystal_ctx* c, uint64_t bytes, uint8_t** p, uint64_t* off) {
+    if (c->pooled) {
+        int st = crystal_arena_alloc(c->h_arena, bytes, off);
+        if (st != CRYSTAL_OK) return st;
+        *p = c->h_base + *off;
+        return CRYSTAL_OK;
+    }
+    void* q = nullptr;
+    if (cudaHostAlloc(&q, bytes ? bytes : 1, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return CRYSTAL_ENOMEM;
+    }
+    *p = (uint8_t*)q;
+    return CRYSTAL_OK;
+}
+
+void free_host(crystal_ctx* c, uint8_t* p, uint64_t off) {
+    if (!p) return;
+    if (c->pooled) crystal_arena_free(c->h_arena, off);
+    else cudaFreeHost(p);
+}
+
+void free_task_buffers(crystal_task* t) {
+    crystal_ctx* c = t->ctx;
+    free_device(c, t->d_scratch, t->d_scratch_off);
+    t->d_scratch = nullptr;
+    free_device(c, t->d_in, t->d_in_off);
+    free_device(c, t->d_out, t->d_out_off);
+    free_host(c, t->h_in, t->h_in_off);
+    free_host(c, t->h_out, t->h_out_off);
+    t->d_in = t->d_out = t->h_in = t->h_out = nullptr;
+}
+
+// ---- parameters ---------------------------------------------------------------
+
+int resolve_params(int kind, const crystal_hash_params* in, uint64_t n, uint64_t out_size,
+                   crystal_hash_params* p) {
+    crystal_params_default(p);
+    if (in) {
+        if (in->reserved != 0) return CRYSTAL_EINVAL;
+        if (in->segment_bytes) p->segment_bytes = in->segment_bytes;
+        if (in->window_bytes) p->window_bytes = in->window_bytes;
+        if (in->chunk_segment_bytes) p->chunk_segment_bytes = in->chunk_segment_bytes;
+        p->mask = in->mask;
+        p->target = in->target;
+    }
+    switch (kind) {
+    case CRYSTAL_KIND_NOP: return CRYSTAL_OK;
+    case CRYSTAL_KIND_MD5_DIRECT: return out_size >= 16 ? CRYSTAL_OK : CRYSTAL_EINVAL;
+    case CRYSTAL_KIND_MD5_SLIDING:
+        if (p->window_bytes > kMaxWindow || n >= (1ull << 32)) return CRYSTAL_EINVAL;
+        if (out_size < sliding_fixed_bytes(n) || out_size >= (1ull << 32)) return CRYSTAL_EINVAL;
+        return CRYSTAL_OK;
+    default: return CRYSTAL_EINVAL;
+    }
+}
+
+// ---- issuing a batch --------------------------------------------------------------
+
+// Fill the slot's pinned descriptor from its jobs: direct units first.
+void build_descriptor(Slot& s, uint32_t* nd_out, uint32_t* ns_out) {
+    crystal_unit* U = batch_units(s.h_desc);
+    uint32_t k = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int want = pass == 0 ? CRYSTAL_KIND_MD5_DIRECT : CRYSTAL_KIND_MD5_SLIDING;
+        for (crystal_task* t : s.tasks) {
+            if (t->kind != want) continue;
+            crystal_unit& x = U[k++];
+            x.in = (uint64_t)t->d_in;
+            x.n = t->in_size;
+            x.out = (uint64_t)t->d_out;
+            x.scratch = (uint64_t)t->d_scratch;
+            x.work_begin = 0;
+            x.out_cap = (uint32_t)std::min<uint64_t>(t->out_size, 0xFFFFFFFFull);
+            x.seg_bytes = want == CRYSTAL_KIND_MD5_DIRECT ? t->params.segment_bytes
+                                                          : t->params.chunk_segment_bytes;
+            x.window = t->params.window_bytes;
+            x.mask = t->params.mask;
+            x.target = t->params.target;
+            x.kind = (uint32_t)want;
+        }
+        if (pass == 0) *nd_out = k;
+    }
+    *ns_out = k - *nd_out;
+}
+
+int launch_chain(crystal_batch* d, cudaStream_t st, bool direct, bool sliding) {
+    int r = CRYSTAL_OK;
+    if (direct) {
+        r = launch_direct_segments(d, st);
+        if (r == CRYSTAL_OK) r = launch_direct_outer(d, st);
+    }
+    if (sliding && r == CRYSTAL_OK) {
+        r = launch_sliding_windows(d, st);
+        if (r == CRYSTAL_OK) r = launch_sliding_chunks(d, st);
+        if (r == CRYSTAL_OK) r = launch_sliding_digests(d, st);
+    }
+    return r;
+}
+
+int kernels_in_chain(bool direct, bool sliding) { return (direct ? 2 : 0) + (sliding ? 4 : 0); }
+
+// Capture descriptor upload + kernel chain of one slot as a graph.
+int capture_graph(crystal_ctx* c, Slot& s, int variant) {
+    const bool direct = variant & 1, sliding = variant & 2;
+    const uint64_t desc_bytes = crystal_batch_bytes(c->max_jobs);
+    const uint64_t before = g_kernel_launches.load();
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CRYSTAL_EDEVICE;
+    cudaMemcpyAsync(s.d_desc, s.h_desc, desc_bytes, cudaMemcpyHostToDevice, s.stream);
+    int r = launch_chain(s.d_desc, s.stream, direct, sliding);
+    cudaMemcpyAsync(s.h_desc, s.d_desc, sizeof(crystal_batch), cudaMemcpyDeviceToHost, s.stream);
+    cudaError_t e = cudaStreamEndCapture(s.stream, &g);
+    g_kernel_launches.store(before);
+    if (r != CRYSTAL_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return CRYSTAL_EDEVICE;
+    }
+    e = cudaGraphInstantiate(&s.graph[variant], g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? CRYSTAL_OK : CRYSTAL_EDEVICE;
+}
+
+// Issue copy-in, kernels and copy-out of the slot's jobs on its stream.
+int issue(crystal_ctx* c, Slot& s) {
+    cudaStream_t st = s.stream;
+    for (crystal_task* t : s.tasks) {
+        if (t->in_size && cudaMemcpyAsync(t->d_in, t->h_in, t->in_size, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return CRYSTAL_EDEVICE;
+    }
+    uint32_t nd = 0, ns = 0;
+    build_descriptor(s, &nd, &ns);
+    if (nd + ns > 0) {
+        if (crystal_batch_plan(s.h_desc, nd, ns) != CRYSTAL_OK) return CRYSTAL_EINVAL;
+        const int variant = (nd ? 1 : 0) | (ns ? 2 : 0);
+        if (c->cfg.flags & CRYSTAL_FLAG_GRAPHS) {
+            if (!s.graph[variant] && capture_graph(c, s, variant) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
+            if (cudaGraphLaunch(s.graph[variant], st) != cudaSuccess) return CRYSTAL_EDEVICE;
+            g_kernel_launches.fetch_add((uint64_t)kernels_in_chain(nd, ns));
+        } else {
+            if (cudaMemcpyAsync(s.d_desc, s.h_desc, crystal_batch_bytes(nd + ns), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess)
+                return CRYSTAL_EDEVICE;
+            int r = launch_chain(s.d_desc, st, nd > 0, ns > 0);
+            if (r != CRYSTAL_OK) return r;
+            if (cudaMemcpyAsync(s.h_desc, s.d_desc, sizeof(crystal_batch), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                return CRYSTAL_EDEVICE;
+        }
+    } else {
+        s.h_desc->status = 0;
+    }
+    for (crystal_task* t : s.tasks) {
+        if (t->out_size && cudaMemcpyAsync(t->h_out, t->d_out, t->out_size, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return CRYSTAL_EDEVICE;
+    }
+    if (cudaEventRecord(s.done, st) != cudaSuccess) return CRYSTAL_EDEVICE;
+    return CRYSTAL_OK;
+}
+
+int job_status(crystal_task* t, uint32_t dev_status) {
+    if (dev_status) return CRYSTAL_EDEVICE;
+    if (t->kind == CRYSTAL_KIND_MD5_SLIDING) {
+        uint32_t flags;
+        memcpy(&flags, t->h_out + 4, 4);
+        if (flags & 1u) return CRYSTAL_EOVERFLOW;
+    }
+    return CRYSTAL_OK;
+}
+
+// Finish the jobs of a slot: statuses, scratch back to the pool, callbacks,
+// waiters.  Called by the master thread without the lock held.
+void finish_slot(crystal_ctx* c, Slot& s, int issue_status) {
+    const uint64_t t = now_ns();
+    const uint32_t dev_status = s.h_desc ? s.h_desc->status : 0;
+    std::vector<crystal_task*> jobs;
+    jobs.swap(s.tasks);
+    for (crystal_task* j : jobs) {
+        j->status = issue_status != CRYSTAL_OK ? issue_status : job_status(j, dev_status);
+        j->t_done = t;
+        free_device(c, j->d_scratch, j->d_scratch_off);
+        j->d_scratch = nullptr;
+    }
+    for (crystal_task* j : jobs) {
+        if (j->cb) {
+            tl_callback_ctx = c;
+            j->cb(j, j->status, j->user);
+            tl_callback_ctx = nullptr;
+        }
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->n_running_jobs--;
+        c->jobs_completed.fetch_add(1);
+        if (j->release_in_callback) {
+            c->tasks.erase(j);
+            free_task_buffers(j);
+            delete j;
+        } else {
+            j->state = T_DONE;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        s.busy = false;
+    }
+    c->cv_done.notify_all();
+}
+
+bool take_batch(crystal_ctx* c, Slot& s) {
+    // caller holds c->mu
+    uint64_t bytes = 0;
+    const uint32_t max_jobs = (c->cfg.flags & CRYSTAL_FLAG_NO_BATCH) ? 1 : c->max_jobs;
+    while (!c->outstanding.empty() && s.tasks.size() < max_jobs) {
+        crystal_task* t = c->outstanding.front();
+        if (!s.tasks.empty() && bytes + t->in_size > c->max_bytes) break;
+        c->outstanding.pop_front();
+        bytes += t->in_size;
+        t->state = T_RUNNING;
+        s.tasks.push_back(t);
+        c->n_running_jobs++;
+    }
+    return !s.tasks.empty();
+}
+
+void master_loop(crystal_ctx* c) {
+    cudaSetDevice(c->device);
+    const bool sequential = c->cfg.flags & CRYSTAL_FLAG_NO_OVERLAP;
+    std::unique_lock<std::mutex> lk(c->mu);
+    for (;;) {
+        bool progressed = false;
+        // completion: every running slot whose event has fired
+        for (size_t i = 0; i < c->running.size();) {
+            Slot& s = c->slots[c->running[i]];
+            cudaError_t e = cudaEventQuery(s.done);
+            if (e == cudaErrorNotReady) {
+                ++i;
+                continue;
+            }
+            c->running.erase(c->running.begin() + i);
+            lk.unlock();
+            if (e != cudaSuccess) cudaGetLastError();
+            finish_slot(c, s, e == cudaSuccess ? CRYSTAL_OK : CRYSTAL_EDEVICE);
+            lk.lock();
+            progressed = true;
+        }
+        // cancellation on shutdown
+        if (c->stop && !c->outstanding.empty()) {
+            std::vector<crystal_task*> cancel(c->outstanding.begin(), c->outstanding.end());
+            c->outstanding.clear();
+            for (crystal_task* t : cancel) t->state = T_RUNNING;  // callbacks may release it
+            lk.unlock();
+            for (crystal_task* t : cancel) {
+                free_device(c, t->d_scratch, t->d_scratch_off);
+                t->d_scratch = nullptr;
+                t->status = CRYSTAL_ESHUTDOWN;
+                t->t_done = now_ns();
+                if (t->cb) {
+                    tl_callback_ctx = c;
+                    t->cb(t, t->status, t->user);
+                    tl_callback_ctx = nullptr;
+                }
+                std::lock_guard<std::mutex> g(c->mu);
+                if (t->release_in_callback) {
+                    c->tasks.erase(t);
+                    free_task_buffers(t);
+                    delete t;
+                } else {
+                    t->state = T_DONE;
+                }
+            }
+            c->cv_done.notify_all();
+            lk.lock();
+            progressed = true;
+        }
+        // dispatch: FIFO from the outstanding queue into free slots
+        while (!c->outstanding.empty()) {
+            const uint32_t ns = (uint32_t)c->slots.size();
+            uint32_t pick = ns;
+            for (uint32_t k = 0; k < ns; ++k) {
+                const uint32_t cand = (c->next_slot + k) % ns;
+                if (!c->slots[cand].busy) {
+                    pick = cand;
+                    break;
+                }
+            }
+            if (pick == ns) break;
+            Slot& s = c->slots[pick];
+            if (!take_batch(c, s)) break;
+            s.busy = true;
+            s.seq = ++c->seq;
+            c->next_slot = (pick + 1) % ns;
+            const uint64_t t = now_ns();
+            for (crystal_task* j : s.tasks) j->t_dispatch = t;
+            lk.unlock();
+            int r = issue(c, s);
+            c->batches.fetch_add(1);
+            if (r != CRYSTAL_OK) {
+                cudaGetLastError();
+                cudaStreamSynchronize(s.stream);
+                finish_slot(c, s, r);
+            } else if (sequential) {
+                cudaEventSynchronize(s.done);
+                finish_slot(c, s, CRYSTAL_OK);
+            }
+            lk.lock();
+            if (r == CRYSTAL_OK && !sequential) c->running.push_back(pick);
+            progressed = true;
+        }
+        if (c->stop && c->running.empty() && c->outstanding.empty()) break;
+        if (progressed) continue;
+        if (c->running.empty()) {
+            c->cv_master.wait(lk);
+        } else {
+            // poll the running slots (Section 4.1: completion is found by polling)
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        }
+    }
+}
+
+void destroy_ctx(crystal_ctx* c) {
+    for (Slot& s : c->slots) {
+        for (auto& g : s.graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream && s.own_stream) cudaStreamDestroy(s.stream);
+        if (s.h_desc) cudaFreeHost(s.h_desc);
+    }
+    c->slots.clear();
+    for (crystal_task* t : c->tasks) {
+        if (!c->pooled) free_task_buffers(t);
+        delete t;
+    }
+    c->tasks.clear();
+    if (c->own_d_base && c->d_base) cudaFree(c->d_base);
+    if (c->h_base) cudaFreeHost(c->h_base);
+    crystal_arena_destroy(c->d_arena);
+    crystal_arena_destroy(c->h_arena);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void crystal_config_default(crystal_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->max_in_bytes = 64ull << 20;
+    cfg->max_out_bytes = 16ull << 20;
+    cfg->device_pool_bytes = 4ull << 30;
+    cfg->host_pool_bytes = 1ull << 30;
+    cfg->n_streams = 4;
+    cfg->device = 0;
+    cfg->flags = 0;
+    cfg->max_batch_jobs = 64;
+    cfg->max_batch_bytes = 32ull << 20;
+}
+
+int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
+    if (!user_cfg || !out) return CRYSTAL_EINVAL;
+    *out = nullptr;
+    crystal_config cfg;
+    crystal_config_default(&cfg);
+    const crystal_config& u = *user_cfg;
+    if (u.max_in_bytes) cfg.max_in_bytes = u.max_in_bytes;
+    if (u.max_out_bytes) cfg.max_out_bytes = u.max_out_bytes;
+    if (u.device_pool_bytes) cfg.device_pool_bytes = u.device_pool_bytes;
+    if (u.host_pool_bytes) cfg.host_pool_bytes = u.host_pool_bytes;
+    cfg.device_arena = u.device_arena;
+    if (u.n_streams) cfg.n_streams = u.n_streams;
+    cfg.device = u.device;
+    cfg.flags = u.flags;
+    if (u.max_batch_jobs) cfg.max_batch_jobs = u.max_batch_jobs;
+    if (u.max_batch_bytes) cfg.max_batch_bytes = u.max_batch_bytes;
+    if (cfg.n_streams < 1 || cfg.n_streams > 64 || cfg.max_batch_jobs > 65536) return CRYSTAL_EINVAL;
+    if (cfg.flags & ~(uint32_t)(CRYSTAL_FLAG_NO_POOL | CRYSTAL_FLAG_NO_OVERLAP | CRYSTAL_FLAG_NO_BATCH |
+                                CRYSTAL_FLAG_GRAPHS))
+        return CRYSTAL_EINVAL;
+    if (cfg.device_arena && (reinterpret_cast<uint64_t>(cfg.device_arena) & 255)) return CRYSTAL_EINVAL;
+    if (cudaSetDevice(cfg.device) != cudaSuccess) {
+        cudaGetLastError();
+        return CRYSTAL_EDEVICE;
+    }
+    crystal_ctx* c = new (std::nothrow) crystal_ctx;
+    if (!c) return CRYSTAL_ENOMEM;
+    c->cfg = cfg;
+    c->device = cfg.device;
+    c->pooled = !(cfg.flags & CRYSTAL_FLAG_NO_POOL);
+    if (cfg.flags & CRYSTAL_FLAG_NO_OVERLAP) c->cfg.n_streams = 1;
+    c->max_jobs = (cfg.flags & (CRYSTAL_FLAG_NO_BATCH | CRYSTAL_FLAG_NO_OVERLAP)) ? 1 : cfg.max_batch_jobs;
+    c->max_bytes = cfg.max_batch_bytes;
+    const uint32_t depth = (cfg.flags & CRYSTAL_FLAG_NO_OVERLAP) ? 1 : 2;  // slots per stream
+    const uint32_t n_slots = (uint32_t)c->cfg.n_streams * depth;
+    const uint64_t desc_bytes = align_up(crystal_batch_bytes(c->max_jobs), 256);
+
+    // device arena: job buffers (pooled mode), scratch and batch descriptors
+    uint64_t d_bytes = cfg.device_pool_bytes;
+    if (!c->pooled) d_bytes = desc_bytes * n_slots;  // descriptors only
+    if (cfg.device_arena && c->pooled) {
+        c->d_base = (uint8_t*)cfg.device_arena;
+    } else {
+        void* p = nullptr;
+        if (cudaMalloc(&p, d_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_ctx(c);
+            return CRYSTAL_ENOMEM;
+        }
+        c->d_base = (uint8_t*)p;
+        c->own_d_base = true;
+    }
+    if (crystal_arena_create(d_bytes, 256, &c->d_arena) != CRYSTAL_OK) {
+        destroy_ctx(c);
+        return CRYSTAL_ENOMEM;
+    }
+    if (c->pooled) {
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, cfg.host_pool_bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_ctx(c);
+            return CRYSTAL_ENOMEM;
+        }
+        c->h_base = (uint8_t*)h;
+        if (crystal_arena_create(cfg.host_pool_bytes, 256, &c->h_arena) != CRYSTAL_OK) {
+            destroy_ctx(c);
+            return CRYSTAL_ENOMEM;
+        }
+    }
+    c->slots.resize(n_slots);
+    for (uint32_t i = 0; i < n_slots; ++i) {
+        Slot& s = c->slots[i];
+        if (i < (uint32_t)c->cfg.n_streams) {
+            if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                destroy_ctx(c);
+                return CRYSTAL_EDEVICE;
+            }
+            s.own_stream = true;
+        } else {
+            s.stream = c->slots[i % c->cfg.n_streams].stream;
+        }
+        if (cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_ctx(c);
+            return CRYSTAL_EDEVICE;
+        }
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, desc_bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_ctx(c);
+            return CRYSTAL_ENOMEM;
+        }
+        memset(h, 0, desc_bytes);
+        s.h_desc = (crystal_batch*)h;
+        if (crystal_arena_alloc(c->d_arena, desc_bytes, &s.d_desc_off) != CRYSTAL_OK) {
+            destroy_ctx(c);
+            return CRYSTAL_ENOMEM;
+        }
+        s.d_desc = (crystal_batch*)(c->d_base + s.d_desc_off);
+    }
+    try {
+        c->master = std::thread(master_loop, c);
+    } catch (...) {
+        destroy_ctx(c);
+        return CRYSTAL_ENOMEM;
+    }
+    *out = c;
+    return CRYSTAL_OK;
+}
+
+int crystal_shutdown(crystal_ctx* c) {
+    if (!c) return CRYSTAL_EINVAL;
+    if (tl_callback_ctx == c) return CRYSTAL_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->accepting = false;
+        c->stop = true;
+    }
+    c->cv_master.notify_all();
+    if (c->master.joinable()) c->master.join();
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    destroy_ctx(c);
+    return CRYSTAL_OK;
+}
+
+int crystal_task_create(crystal_ctx* c, uint64_t in_size, uint64_t out_size, crystal_task** out) {
+    if (!c || !out) return CRYSTAL_EINVAL;
+    *out = nullptr;
+    if (in_size > c->cfg.max_in_bytes || out_size > c->cfg.max_out_bytes) return CRYSTAL_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!c->accepting) return CRYSTAL_ESHUTDOWN;
+    }
+    if (!c->pooled) cudaSetDevice(c->device);
+    crystal_task* t = new (std::nothrow) crystal_task;
+    if (!t) return CRYSTAL_ENOMEM;
+    t->ctx = c;
+    t->in_cap = t->in_size = in_size;
+    t->out_cap = t->out_size = out_size;
+    int st = alloc_host(c, in_size, &t->h_in, &t->h_in_off);
+    if (st == CRYSTAL_OK) st = alloc_host(c, out_size, &t->h_out, &t->h_out_off);
+    if (st == CRYSTAL_OK) st = alloc_device(c, in_size, &t->d_in, &t->d_in_off);
+    if (st == CRYSTAL_OK) st = alloc_device(c, out_size, &t->d_out, &t->d_out_off);
+    if (st != CRYSTAL_OK) {
+        free_task_buffers(t);
+        delete t;
+        return st;
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->tasks.insert(t);
+    *out = t;
+    return CRYSTAL_OK;
+}
+
+void* crystal_task_host_in(crystal_task* t) { return t ? t->h_in : nullptr; }
+void* crystal_task_host_out(crystal_task* t) { return t ? t->h_out : nullptr; }
+uint64_t crystal_task_device_in(crystal_task* t) { return t ? (uint64_t)t->d_in : 0; }
+uint64_t crystal_task_device_out(crystal_task* t) { return t ? (uint64_t)t->d_out : 0; }
+
+int crystal_task_resize(crystal_task* t, uint64_t in_size, uint64_t out_size) {
+    if (!t) return CRYSTAL_EINVAL;
+    std::lock_guard<std::mutex> lk(t->ctx->mu);
+    if (t->state == T_OUTSTANDING || t->state == T_RUNNING) return CRYSTAL_EINVAL;
+    if (in_size > t->in_cap || out_size > t->out_cap) return CRYSTAL_EINVAL;
+    t->in_size = in_size;
+    t->out_size = out_size;
+    return CRYSTAL_OK;
+}
+
+int crystal_task_submit(crystal_task* t, int kind, const crystal_hash_params* params, crystal_callback cb,
+                        void* user) {
+    if (!t) return CRYSTAL_EINVAL;
+    crystal_ctx* c = t->ctx;
+    crystal_hash_params p;
+    int st = resolve_params(kind, params, t->in_size, t->out_size, &p);
+    if (st != CRYSTAL_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!c->accepting) return CRYSTAL_ESHUTDOWN;
+        if (t->state == T_OUTSTANDING || t->state == T_RUNNING) return CRYSTAL_EINVAL;
+    }
+    const uint64_t scratch = crystal_scratch_bytes(kind, t->in_size, t->out_size, &p);
+    uint8_t* d_scratch = nullptr;
+    uint64_t d_scratch_off = 0;
+    if (scratch) {
+        if (!c->pooled) cudaSetDevice(c->device);
+        st = alloc_device(c, scratch, &d_scratch, &d_scratch_off);
+        if (st != CRYSTAL_OK) return st == CRYSTAL_ENOMEM ? CRYSTAL_ENOMEM : CRYSTAL_EAGAIN;
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!c->accepting) {
+            free_device(c, d_scratch, d_scratch_off);
+            return CRYSTAL_ESHUTDOWN;
+        }
+        t->kind = kind;
+        t->params = p;
+        t->cb = cb;
+        t->user = user;
+        t->d_scratch = d_scratch;
+        t->d_scratch_off = d_scratch_off;
+        t->scratch_bytes = scratch;
+        t->status = CRYSTAL_PENDING;
+        t->state = T_OUTSTANDING;
+        t->submitted_once = true;
+        t->release_in_callback = false;
+        t->t_submit = now_ns();
+        t->t_dispatch = t->t_done = 0;
+        c->outstanding.push_back(t);
+    }
+    c->cv_master.notify_one();
+    return CRYSTAL_OK;
+}
+
+int crystal_task_poll(crystal_task* t) {
+    if (!t) return CRYSTAL_EINVAL;
+    std::lock_guard<std::mutex> lk(t->ctx->mu);
+    if (!t->submitted_once) return CRYSTAL_EINVAL;
+    if (t->state != T_DONE) return CRYSTAL_PENDING;
+    return t->status;
+}
+
+int crystal_task_wait(crystal_task* t, int64_t timeout_ns) {
+    if (!t) return CRYSTAL_EINVAL;
+    crystal_ctx* c = t->ctx;
+    if (tl_callback_ctx == c) return CRYSTAL_EINVAL;
+    std::unique_lock<std::mutex> lk(c->mu);
+    if (!t->submitted_once) return CRYSTAL_EINVAL;
+    auto done = [t] { return t->state == T_DONE; };
+    if (timeout_ns < 0) {
+        c->cv_done.wait(lk, done);
+    } else if (!c->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), done)) {
+        return CRYSTAL_ETIMEDOUT;
+    }
+    return t->status;
+}
+
+int crystal_task_release(crystal_task* t) {
+    if (!t) return CRYSTAL_EINVAL;
+    crystal_ctx* c = t->ctx;
+    std::unique_lock<std::mutex> lk(c->mu);
+    if (t->state == T_RUNNING && tl_callback_ctx == c) {
+        t->release_in_callback = true;  // freed by the master after the callback returns
+        return CRYSTAL_OK;
+    }
+    if (t->state == T_OUTSTANDING || t->state == T_RUNNING) return CRYSTAL_EINVAL;
+    c->tasks.erase(t);
+    lk.unlock();
+    if (!c->pooled) cudaSetDevice(c->device);
+    free_task_buffers(t);
+    delete t;
+    return CRYSTAL_OK;
+}
+
+int crystal_task_timing(crystal_task* t, uint64_t* submit_ns, uint64_t* dispatch_ns, uint64_t* done_ns) {
+    if (!t) return CRYSTAL_EINVAL;
+    std::lock_guard<std::mutex> lk(t->ctx->mu);
+    if (submit_ns) *submit_ns = t->t_submit;
+    if (dispatch_ns) *dispatch_ns = t->t_dispatch;
+    if (done_ns) *done_ns = t->t_done;
+    return CRYSTAL_OK;
+}
+
+int crystal_get_stats(crystal_ctx* c, crystal_stats* out) {
+    if (!c || !out) return CRYSTAL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    out->jobs_completed = c->jobs_completed.load();
+    out->batches_launched = c->batches.load();
+    out->device_pool_bytes = c->pooled ? c->cfg.device_pool_bytes : 0;
+    out->device_pool_used = c->pooled ? crystal_arena_used(c->d_arena) : 0;
+    out->host_pool_bytes = c->pooled ? c->cfg.host_pool_bytes : 0;
+    out->host_pool_used = c->pooled ? crystal_arena_used(c->h_arena) : 0;
+    out->jobs_outstanding = c->outstanding.size();
+    out->jobs_running = c->n_running_jobs;
+    return CRYSTAL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+"""The C-ABI library on a machine without a GPU: it loads, exports every
+function ``include/crystal.h`` declares, and its host-only logic (arena
+allocator, batch planning, size arithmetic, status strings) behaves.  No
+call here touches a CUDA device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "crystal.h")
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_1005_1695_b300 import crystal
+
+    crystal.load()
+    return crystal
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(crystal_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_paper_api():
+    names = declared_functions()
+    for n in ["crystal_init", "crystal_shutdown", "crystal_task_create", "crystal_task_submit",
+              "crystal_task_poll", "crystal_task_wait", "crystal_task_release", "crystal_task_host_in",
+              "crystal_task_host_out", "crystal_out_bytes", "crystal_strerror"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(C):
+    lib = ctypes.CDLL(C.lib_path())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_sizes_match_header(C):
+    assert ctypes.sizeof(C.crystal_config) == 64
+    assert ctypes.sizeof(C.crystal_hash_params) == 24
+    assert C.UNIT_DTYPE.itemsize == 64
+    assert C.load().crystal_batch_bytes(3) == 64 + 3 * 64
+
+
+def test_strerror_covers_codes(C):
+    L = C.load()
+    for code in range(-7, 2):
+        assert L.crystal_strerror(code)
+    assert L.crystal_strerror(-99) == b"unknown status"
+
+
+def _arena(C, size, align=256):
+    L = C.load()
+    h = ctypes.c_void_p()
+    assert L.crystal_arena_create(size, align, ctypes.byref(h)) == 0
+    return L, h
+
+
+def _alloc(L, h, n):
+    off = ctypes.c_uint64()
+    st = L.crystal_arena_alloc(h, n, ctypes.byref(off))
+    return st, off.value
+
+
+def test_arena_alloc_free_coalesce(C):
+    L, h = _arena(C, 1 << 20)
+    offs = []
+    for _ in range(16):
+        st, o = _alloc(L, h, 65536)
+        assert st == 0
+        offs.append(o)
+    assert sorted(offs) == [i * 65536 for i in range(16)]
+    assert _alloc(L, h, 1)[0] == C.CRYSTAL_EAGAIN
+    assert L.crystal_arena_used(h) == 1 << 20
+    for o in offs[::2]:
+        assert L.crystal_arena_free(h, o) == 0
+    assert L.crystal_arena_largest_free(h) == 65536
+    assert _alloc(L, h, 65537)[0] == C.CRYSTAL_EAGAIN
+    for o in offs[1::2]:
+        assert L.crystal_arena_free(h, o) == 0
+    assert L.crystal_arena_used(h) == 0
+    assert L.crystal_arena_largest_free(h) == 1 << 20
+    assert L.crystal_arena_free(h, 12345) == C.CRYSTAL_EINVAL
+    L.crystal_arena_destroy(h)
+
+
+def test_arena_alignment_and_random_churn(C):
+    L, h = _arena(C, 64 << 20, 256)
+    rng = np.random.default_rng(0)
+    live = {}
+    for step in range(4000):
+        if live and (rng.random() < 0.45 or len(live) > 200):
+            o = int(rng.choice(list(live)))
+            assert L.crystal_arena_free(h, o) == 0
+            del live[o]
+        else:
+            n = int(rng.integers(1, 1 << 18))
+            st, o = _alloc(L, h, n)
+            if st == 0:
+                assert o % 256 == 0
+                for lo, ln in live.items():
+                    assert o + n <= lo or lo + ln <= o, "overlap"
+                live[o] = n
+    for o in list(live):
+        assert L.crystal_arena_free(h, o) == 0
+    assert L.crystal_arena_used(h) == 0 and L.crystal_arena_largest_free(h) == 64 << 20
+    L.crystal_arena_destroy(h)
+
+
+def test_sizes(C):
+    p = C.params()
+    assert C.out_bytes(C.CRYSTAL_KIND_MD5_DIRECT, 12345, p) == 16
+    n = 1 << 20
+    assert C.sliding_out_bytes(n, 0) == 8 + 4 * (n // 32)
+    assert C.out_bytes(C.CRYSTAL_KIND_MD5_SLIDING, n, p) == 8 + 4 * (n // 32) + 20 * (n - 20 + 2)
+    assert C.out_bytes(C.CRYSTAL_KIND_MD5_SLIDING, 5, p) == 8 + 4 + 20
+    assert C.scratch_bytes(C.CRYSTAL_KIND_MD5_DIRECT, 65536, 16, p) == 16 * 16
+    assert C.scratch_bytes(C.CRYSTAL_KIND_MD5_DIRECT, 0, 16, p) == 16
+    out = C.sliding_out_bytes(n, 1000)
+    cap = 1000
+    assert C.scratch_bytes(C.CRYSTAL_KIND_MD5_SLIDING, n, out, p) == \
+        ((4 * (cap + 1) + 15) // 16 * 16) + 16 * (cap + n // 4096 + 1)
+
+
+def _plan(C, units, nd, ns):
+    buf = np.zeros(64 + 64 * len(units), dtype=np.uint8)
+    rec = buf[64:].view(C.UNIT_DTYPE)
+    for i, u in enumerate(units):
+        for k, v in u.items():
+            rec[i][k] = v
+    st = C.load().crystal_batch_plan(buf.ctypes.data, nd, ns)
+    return st, buf, rec
+
+
+def _unit(kind, n, **kw):
+    u = {"in": 1 << 20, "n": n, "out": 2 << 20, "scratch": 3 << 20, "out_cap": 1 << 20,
+         "seg_bytes": 4096, "window": 20, "mask": 0x1FFF, "target": 0x1FFF, "kind": kind}
+    u.update(kw)
+    return u
+
+
+def test_batch_plan_prefixes_and_validation(C):
+    D, S = C.CRYSTAL_KIND_MD5_DIRECT, C.CRYSTAL_KIND_MD5_SLIDING
+    units = [_unit(D, 0), _unit(D, 4096), _unit(D, 4097), _unit(D, 100, seg_bytes=7),
+             _unit(S, 0), _unit(S, 1024), _unit(S, 1025), _unit(S, 10, window=55)]
+    st, buf, rec = _plan(C, units, 4, 4)
+    assert st == 0
+    assert rec["work_begin"].tolist() == [0, 1, 2, 4, 0, 0, 1, 3]
+    hdr = buf[:64]
+    assert hdr[:8].view("<u4").tolist() == [4, 4]
+    assert hdr[8:24].view("<u8").tolist() == [4 + 15, 4]
+    assert hdr[24:28].view("<u4")[0] == 55
+    bad = [
+        [_unit(S, 10)] + units[1:4],               # wrong kind order
+        [_unit(D, 10, seg_bytes=0)],               # zero segment
+        [_unit(D, 10, scratch=(3 << 20) + 8)],     # misaligned scratch
+        [_unit(D, 10, out_cap=15)],                # direct output < 16
+    ]
+    for b in bad:
+        assert _plan(C, b, len(b), 0)[0] == C.CRYSTAL_EINVAL
+    for b in ([_unit(S, 10, window=56)], [_unit(S, 10, window=0)], [_unit(S, 4096, out_cap=100)],
+              [_unit(S, 1 << 32)]):
+        assert _plan(C, b, 0, 1)[0] == C.CRYSTAL_EINVAL

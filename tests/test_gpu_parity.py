@@ -1,0 +1,218 @@
+"""GPU kernels against the CPU oracle, element by element, through the C ABI.
+
+Every output is integer/byte work, so the bar is bit-exact equality of every
+result byte (digests, bitmap words, chunk ends, header counts).  Sizes span
+several window tiles and segments with ragged tails, odd alignments, the
+empty unit, units shorter than the window, every padding branch of MD5, and
+the degenerate masks (mask 0 marks every window).
+"""
+import concurrent.futures as cf
+import os
+
+import numpy as np
+import pytest
+
+from helpers import first_difference, same_result
+
+pytestmark = pytest.mark.gpu
+
+DIRECT, SLIDING = 1, 2
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    return torch
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_1005_1695_b300 import crystal
+
+    crystal.load()
+    return crystal
+
+
+def _pack(torch, units, align_offsets=None):
+    """Place byte arrays in one device buffer at the given misalignments."""
+    offs, pos = [], 0
+    for i, u in enumerate(units):
+        mis = align_offsets[i % len(align_offsets)] if align_offsets else 0
+        pos = (pos + 255) // 256 * 256 + mis
+        offs.append(pos)
+        pos += len(u)
+    host = np.zeros(pos + 256, dtype=np.uint8)
+    for o, u in zip(offs, units):
+        host[o:o + len(u)] = np.frombuffer(bytes(u), dtype=np.uint8) if not isinstance(u, np.ndarray) else u
+    return torch.from_numpy(host).cuda(), offs
+
+
+def _run(torch, C, units, kinds, plist, out_sizes=None, align=None, mode="batch"):
+    d_in, offs = _pack(torch, units, align)
+    b = C.DeviceBatch(d_in, offs, [len(u) for u in units], kinds, out_sizes=out_sizes, per_unit_params=plist)
+    if mode == "batch":
+        b.launch()
+    else:
+        b.launch_direct_segments()
+        b.launch_direct_outer()
+        b.launch_sliding_windows()
+        b.launch_sliding_chunks()
+        b.launch_sliding_digests()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    return b.outputs()
+
+
+def _oracle_all(oracle_mod, units, kinds, plist, out_sizes):
+    def one(i):
+        p = plist[i]
+        return oracle_mod.task(kinds[i], bytes(units[i]), out_sizes[i], seg_bytes=p.segment_bytes,
+                               window=p.window_bytes, mask=p.mask, target=p.target,
+                               chunk_seg_bytes=p.chunk_segment_bytes)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return list(ex.map(one, range(len(units))))
+
+
+def _compare(units, kinds, got, want):
+    for i, (g, (st, w)) in enumerate(zip(got, want)):
+        assert st in (0, 1)
+        assert same_result(kinds[i], len(units[i]), g, w), \
+            f"unit {i} n={len(units[i])}: " + first_difference(kinds[i], len(units[i]), g, w)
+
+
+def _rand(seed, n):
+    from paper_1005_1695_b300 import inputs
+
+    return inputs.uniform_unit(seed, 99, n)
+
+
+# ---- direct hashing -------------------------------------------------------------
+
+DIRECT_SIZES = [0, 1, 3, 55, 56, 57, 63, 64, 65, 119, 120, 127, 128, 4095, 4096, 4097, 8191, 65536, 100003]
+
+
+@pytest.mark.parametrize("S", [4096, 64, 100, 1, 65536])
+def test_direct_sizes_alignments(torch_cuda, C, oracle_mod, S):
+    units = [_rand(1000 + i, n) for i, n in enumerate(DIRECT_SIZES)]
+    kinds = [DIRECT] * len(units)
+    plist = [C.params(segment_bytes=S)] * len(units)
+    got = _run(torch_cuda, C, units, kinds, plist, align=[0, 1, 2, 3, 5, 16, 4, 8])
+    want = _oracle_all(oracle_mod, units, kinds, plist, [16] * len(units))
+    _compare(units, kinds, got, want)
+
+
+def test_direct_config_64x64k(torch_cuda, C, oracle_mod):
+    """64 units of 64 KiB uniform random bytes, 4 KiB segments: every digest."""
+    from paper_1005_1695_b300 import inputs
+
+    units = [inputs.uniform_unit(1, i, 65536) for i in range(64)]
+    kinds = [DIRECT] * 64
+    plist = [C.params()] * 64
+    got = _run(torch_cuda, C, units, kinds, plist, mode="split")
+    for i, u in enumerate(units):
+        assert got[i][:16] == oracle_mod.direct(u, 4096), i
+
+
+# ---- sliding-window hashing ------------------------------------------------------
+
+@pytest.mark.parametrize("w", [1, 2, 3, 20])
+@pytest.mark.parametrize("mask,target", [(0x0, 0x0), (0x1, 0x1), (0x3, 0x0), (0x1FFF, 0x1FFF)])
+def test_sliding_tiny_every_length(torch_cuda, C, oracle_mod, w, mask, target):
+    units = [_rand(2000 + n, n) for n in range(0, 65)]
+    kinds = [SLIDING] * len(units)
+    plist = [C.params(window_bytes=w, mask=mask, target=target, chunk_segment_bytes=16)] * len(units)
+    outs = [C.out_bytes(SLIDING, len(u), plist[0]) for u in units]
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 3, 1, 2])
+    want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    _compare(units, kinds, got, want)
+
+
+@pytest.mark.parametrize("w", [20, 7, 16, 55])
+@pytest.mark.parametrize("S", [4096, 100])
+def test_sliding_ragged_tiles(torch_cuda, C, oracle_mod, w, S):
+    sizes = [1023, 1024, 1025, 2047, 2048 + 19, 3000, 10007, 65536 + 5]
+    units = [_rand(3000 + i, n) for i, n in enumerate(sizes)]
+    kinds = [SLIDING] * len(units)
+    plist = [C.params(window_bytes=w, mask=0x3F, target=0x15, chunk_segment_bytes=S)] * len(units)
+    outs = [C.sliding_out_bytes(n, n // 16 + 8) for n in sizes]
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 1, 2, 3, 7, 13])
+    want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    _compare(units, kinds, got, want)
+
+
+def test_sliding_overflow_keeps_count(torch_cuda, C, oracle_mod):
+    n = 20000
+    units = [_rand(5, n)]
+    p = C.params(mask=0x7, target=0x7)
+    kinds = [SLIDING]
+    want = _oracle_all(oracle_mod, units, kinds, [p], [C.sliding_out_bytes(n, n)])
+    need = int.from_bytes(want[0][1][:4], "little")
+    outs = [C.sliding_out_bytes(n, need - 1)]
+    got = _run(torch_cuda, C, units, kinds, [p], out_sizes=outs)
+    want = _oracle_all(oracle_mod, units, kinds, [p], outs)
+    assert want[0][0] == 1
+    _compare(units, kinds, got, want)
+    assert int.from_bytes(got[0][4:8], "little") == 1
+
+
+def test_mixed_batch_params_per_unit(torch_cuda, C, oracle_mod):
+    units, kinds, plist, outs = [], [], [], []
+    for i in range(24):
+        n = [0, 17, 5000, 70000, 1 << 20][i % 5] + i
+        units.append(_rand(4000 + i, n))
+        if i % 3 == 0:
+            kinds.append(SLIDING)
+            p = C.params(window_bytes=[20, 12, 33][(i // 3) % 3], mask=0xFF, target=i & 0xFF,
+                         chunk_segment_bytes=[4096, 512][i % 2])
+            outs.append(C.sliding_out_bytes(n, n // 64 + 4))
+        else:
+            kinds.append(DIRECT)
+            p = C.params(segment_bytes=[4096, 1000, 64][i % 3])
+            outs.append(16)
+        plist.append(p)
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 1, 16, 3])
+    want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    _compare(units, kinds, got, want)
+
+
+def test_sliding_config_256x1mib_sampled(torch_cuda, C, oracle_mod):
+    """256 units of 1 MiB (half repeated 8 KiB blocks), w = 20, mask = target =
+    0x1FFF, in the launch configuration the benchmark times: 12 sampled units
+    bit-exact against the oracle, every unit checked for consistency (chunks
+    tile the unit, ends follow the bitmap, counts match)."""
+    from paper_1005_1695_b300 import inputs
+
+    torch = torch_cuda
+    n, U = 1 << 20, 256
+    pool = inputs.dedup_pool(2)
+    host = np.empty(U * n, dtype=np.uint8)
+    for u in range(U):
+        inputs.dedup_unit(2, u, n, pool=pool, out=host[u * n:(u + 1) * n])
+    d_in = torch.from_numpy(host).cuda()
+    p = C.params()
+    out_size = C.sliding_out_bytes(n, 1024)
+    b = C.DeviceBatch(d_in, [u * n for u in range(U)], [n] * U, [SLIDING] * U, p,
+                      out_sizes=[out_size] * U)
+    b.launch_sliding_windows()
+    b.launch_sliding_chunks()
+    b.launch_sliding_digests()
+    torch.cuda.synchronize()
+    got = b.outputs()
+    words = n // 32
+    for u in range(U):
+        hdr = np.frombuffer(got[u][:8], dtype=np.uint32)
+        assert hdr[1] == 0
+        bm = np.frombuffer(got[u][8:8 + 4 * words], dtype=np.uint32)
+        bits = np.nonzero(np.unpackbits(bm.view(np.uint8), bitorder="little"))[0]
+        ends = np.frombuffer(got[u][8 + 4 * words:8 + 4 * words + 4 * int(hdr[0])], dtype=np.uint32)
+        want_ends = sorted(set((bits + 20).tolist()) | {n})
+        assert ends.tolist() == want_ends
+        assert bits.size == 0 or bits.max() <= n - 20
+    sample = list(range(0, U, U // 12))[:12]
+    units = [host[u * n:(u + 1) * n] for u in sample]
+    want = _oracle_all(oracle_mod, units, [SLIDING] * len(units), [p] * len(units), [out_size] * len(units))
+    _compare(units, [SLIDING] * len(units), [got[u] for u in sample], want)

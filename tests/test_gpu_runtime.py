@@ -1,0 +1,287 @@
+"""The job runtime (pool, streams, master thread, callbacks) on the GPU.
+
+Every job's output is compared bit for bit with the CPU oracle; the runtime
+modes (pooled / per-job allocation, overlap / sequential, batched / one job
+per launch, graphs) must all give the same bytes, and a job's result must be
+the same alone and in a mix.  Failure paths are driven from the host: a
+full pool, a too-small output buffer, a bounded wait that runs out, an
+allocation that cannot succeed at init, shutdown with jobs in flight.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+from helpers import first_difference, same_result
+
+pytestmark = pytest.mark.gpu
+
+DIRECT, SLIDING, NOP = 1, 2, 0
+SEC = 1_000_000_000
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    from paper_1005_1695_b300 import crystal
+
+    crystal.load()
+    return crystal
+
+
+def _jobs(C, count=24, seed=7):
+    from paper_1005_1695_b300 import inputs
+
+    jobs = []
+    for i in range(count):
+        n = int([65536, 1 << 20, 4097, 0, 300000, 20][i % 6]) + (i % 5) * 3
+        if i % 3 == 1:
+            data = inputs.dedup_unit(seed, i, n)
+            p = C.params(mask=0x3FF, target=0x3FF)
+            jobs.append((SLIDING, data, C.sliding_out_bytes(n, n // 256 + 16), p))
+        else:
+            data = inputs.uniform_unit(seed, i, n)
+            p = C.params(segment_bytes=[4096, 1024, 333][i % 3])
+            jobs.append((DIRECT, data, 16, p))
+    return jobs
+
+
+def _want(oracle_mod, jobs):
+    out = []
+    for kind, data, osz, p in jobs:
+        st, w = oracle_mod.task(kind, data, osz, seg_bytes=p.segment_bytes, window=p.window_bytes,
+                                mask=p.mask, target=p.target, chunk_seg_bytes=p.chunk_segment_bytes)
+        out.append((st, w))
+    return out
+
+
+def _submit_all(C, ctx, jobs, callback=None):
+    tasks = []
+    for kind, data, osz, p in jobs:
+        t = ctx.task_create(len(data), osz)
+        t.h_in[:] = data
+        assert t.submit(kind, p, callback) == C.CRYSTAL_OK
+        tasks.append(t)
+    return tasks
+
+
+def _check(C, tasks, jobs, want):
+    for i, (t, (kind, data, osz, p), (ost, w)) in enumerate(zip(tasks, jobs, want)):
+        st = t.wait(30 * SEC)
+        assert st == (C.CRYSTAL_OK if ost == 0 else C.CRYSTAL_EOVERFLOW), (i, st)
+        g = t.output()
+        assert same_result(kind, len(data), g, w), f"job {i}: " + first_difference(kind, len(data), g, w)
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2, 4, 8, 1 | 2 | 4], ids=["pooled", "no_pool", "no_overlap",
+                                                                  "no_batch", "graphs", "plain"])
+def test_runtime_modes_bit_exact(C, oracle_mod, flags):
+    jobs = _jobs(C)
+    want = _want(oracle_mod, jobs)
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=256 << 20,
+                   host_pool_bytes=128 << 20, n_streams=3, flags=flags, max_batch_jobs=8) as ctx:
+        used0 = ctx.stats().device_pool_used
+        tasks = _submit_all(C, ctx, jobs)
+        _check(C, tasks, jobs, want)
+        s = ctx.stats()
+        assert s.jobs_completed == len(jobs)
+        for t in tasks:
+            assert t.release() == C.CRYSTAL_OK
+        after = ctx.stats()
+        assert after.device_pool_used == used0 and after.host_pool_used == 0
+
+
+def test_resubmit_reuses_buffers(C, oracle_mod):
+    jobs = _jobs(C, count=6, seed=11)
+    want = _want(oracle_mod, jobs)
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=64 << 20,
+                   host_pool_bytes=64 << 20) as ctx:
+        t = ctx.task_create(2 << 20, 1 << 20)
+        for (kind, data, osz, p), (ost, w) in zip(jobs, want):
+            t.resize(len(data), osz)
+            t.h_in[:len(data)] = data
+            assert t.submit(kind, p) == C.CRYSTAL_OK
+            assert t.wait(30 * SEC) == (C.CRYSTAL_OK if ost == 0 else C.CRYSTAL_EOVERFLOW)
+            assert same_result(kind, len(data), t.output(), w)
+        assert t.release() == C.CRYSTAL_OK
+
+
+def test_alone_equals_in_mix(C, oracle_mod):
+    jobs = _jobs(C, count=18, seed=13)
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=256 << 20,
+                   host_pool_bytes=128 << 20, n_streams=4, max_batch_jobs=16) as ctx:
+        alone = []
+        for job in jobs:
+            t = _submit_all(C, ctx, [job])[0]
+            t.wait(30 * SEC)
+            alone.append(t.output())
+            t.release()
+        tasks = _submit_all(C, ctx, jobs)
+        for i, t in enumerate(tasks):
+            t.wait(30 * SEC)
+            kind, data = jobs[i][0], jobs[i][1]
+            assert same_result(kind, len(data), t.output(), alone[i]), i
+
+
+def test_callbacks_fire_once_and_may_release(C, oracle_mod):
+    jobs = _jobs(C, count=12, seed=17)
+    want = _want(oracle_mod, jobs)
+    seen = {}
+    lock = threading.Lock()
+    done = threading.Event()
+    L = C.load()
+
+    @C.crystal_callback
+    def cb(handle, status, user):
+        with lock:
+            seen[handle] = seen.get(handle, []) + [status]
+            if len(seen) == len(jobs):
+                done.set()
+
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=128 << 20,
+                   host_pool_bytes=64 << 20) as ctx:
+        tasks = _submit_all(C, ctx, jobs, callback=cb)
+        assert done.wait(30)
+        for t, (ost, _) in zip(tasks, want):
+            assert seen[t.handle] == [C.CRYSTAL_OK if ost == 0 else C.CRYSTAL_EOVERFLOW]
+        used_before = ctx.stats().host_pool_used
+
+        # a callback that releases its own job
+        released = threading.Event()
+
+        @C.crystal_callback
+        def cb_release(handle, status, user):
+            assert L.crystal_task_wait(handle, 0) == C.CRYSTAL_EINVAL  # no waiting inside a callback
+            assert L.crystal_task_release(handle) == C.CRYSTAL_OK
+            released.set()
+
+        t = ctx.task_create(4096, 16)
+        t.h_in[:] = 1
+        assert t.submit(DIRECT, None, cb_release) == C.CRYSTAL_OK
+        assert released.wait(30)
+        ctx._tasks.discard(t)
+        import time
+
+        for _ in range(100):
+            if ctx.stats().host_pool_used == used_before:
+                break
+            time.sleep(0.01)
+        assert ctx.stats().host_pool_used == used_before
+
+
+def test_overflow_status_through_runtime(C, oracle_mod):
+    from paper_1005_1695_b300 import inputs
+
+    n = 50000
+    data = inputs.uniform_unit(3, 3, n)
+    p = C.params(mask=0x3, target=0x3)
+    with C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 20, device_pool_bytes=64 << 20,
+                   host_pool_bytes=32 << 20) as ctx:
+        osz = C.sliding_out_bytes(n, 100)
+        t = ctx.task_create(n, osz)
+        t.h_in[:] = data
+        assert t.submit(SLIDING, p) == C.CRYSTAL_OK
+        assert t.wait(30 * SEC) == C.CRYSTAL_EOVERFLOW
+        st, w = oracle_mod.task(SLIDING, data, osz, mask=0x3, target=0x3)
+        assert st == 1 and same_result(SLIDING, n, t.output(), w)
+
+
+def test_pool_exhaustion_is_eagain_then_recovers(C):
+    with C.Context(max_in_bytes=8 << 20, max_out_bytes=1 << 20, device_pool_bytes=32 << 20,
+                   host_pool_bytes=32 << 20) as ctx:
+        held = []
+        with pytest.raises(C.CrystalError) as e:
+            for _ in range(64):
+                held.append(ctx.task_create(4 << 20, 16))
+        assert e.value.status == C.CRYSTAL_EAGAIN
+        assert 1 <= len(held) < 64
+        held.pop().release()
+        t = ctx.task_create(4 << 20, 16)
+        t.h_in[:] = 5
+        assert t.submit(DIRECT) in (C.CRYSTAL_OK, C.CRYSTAL_EAGAIN)
+
+
+def test_bad_arguments_are_rejected(C):
+    with C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 20, device_pool_bytes=16 << 20,
+                   host_pool_bytes=16 << 20) as ctx:
+        with pytest.raises(C.CrystalError):
+            ctx.task_create(2 << 20, 16)  # above max_in_bytes
+        t = ctx.task_create(1000, 8)
+        assert t.submit(DIRECT) == C.CRYSTAL_EINVAL  # out < 16
+        assert t.submit(SLIDING) == C.CRYSTAL_EINVAL  # out < header + bitmap
+        assert t.submit(7) == C.CRYSTAL_EINVAL
+        t2 = ctx.task_create(1000, 4096)
+        assert t2.submit(SLIDING, C.params(window_bytes=56)) == C.CRYSTAL_EINVAL
+        assert t2.poll() == C.CRYSTAL_EINVAL  # never submitted
+        assert t2.wait(0) == C.CRYSTAL_EINVAL
+
+
+def test_wait_timeout_then_completes(C):
+    with C.Context(max_in_bytes=64 << 20, max_out_bytes=4 << 20, device_pool_bytes=512 << 20,
+                   host_pool_bytes=256 << 20) as ctx:
+        n = 48 << 20
+        t = ctx.task_create(n, C.sliding_out_bytes(n, 1 << 14))
+        t.h_in[:] = 7
+        assert t.submit(SLIDING) == C.CRYSTAL_OK
+        assert t.wait(0) == C.CRYSTAL_ETIMEDOUT
+        assert t.poll() in (C.CRYSTAL_PENDING, C.CRYSTAL_OK)
+        assert t.wait(60 * SEC) == C.CRYSTAL_OK
+        assert t.poll() == C.CRYSTAL_OK
+
+
+def test_init_allocation_failure_is_clean(C):
+    with pytest.raises(RuntimeError):
+        C.Context(device_pool_bytes=1 << 50)
+    with pytest.raises(RuntimeError):
+        C.Context(n_streams=0 - 1)
+    with C.Context(device_pool_bytes=16 << 20, host_pool_bytes=16 << 20) as ctx:  # still usable
+        t = ctx.task_create(100, 16)
+        t.h_in[:] = 0
+        assert t.submit(DIRECT) == 0 and t.wait(10 * SEC) == 0
+
+
+def test_shutdown_with_jobs_in_flight(C):
+    ctx = C.Context(max_in_bytes=4 << 20, max_out_bytes=1 << 20, device_pool_bytes=256 << 20,
+                    host_pool_bytes=128 << 20, n_streams=2, max_batch_jobs=2)
+    statuses = []
+
+    @C.crystal_callback
+    def cb(handle, status, user):
+        statuses.append(status)
+
+    for i in range(20):
+        t = ctx.task_create(4 << 20, 16)
+        t.h_in[:] = i
+        assert t.submit(DIRECT, None, cb) == C.CRYSTAL_OK
+    assert ctx.shutdown() == C.CRYSTAL_OK
+    assert len(statuses) == 20
+    assert set(statuses) <= {C.CRYSTAL_OK, C.CRYSTAL_ESHUTDOWN}
+
+
+def test_nop_jobs_copy_through(C):
+    with C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 20, device_pool_bytes=16 << 20,
+                   host_pool_bytes=16 << 20) as ctx:
+        t = ctx.task_create(4096, 4096)
+        t.h_in[:] = 3
+        assert t.submit(NOP) == C.CRYSTAL_OK
+        assert t.wait(10 * SEC) == C.CRYSTAL_OK
+        s, d, e = t.timing()
+        assert 0 < s <= d <= e
+
+
+def test_external_device_arena(C, oracle_mod):
+    import torch
+
+    arena = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    jobs = _jobs(C, count=6, seed=23)
+    want = _want(oracle_mod, jobs)
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, host_pool_bytes=32 << 20,
+                   device_arena=arena) as ctx:
+        tasks = _submit_all(C, ctx, jobs)
+        _check(C, tasks, jobs, want)
+        base = arena.data_ptr()
+        for t in tasks:
+            assert base <= C.load().crystal_task_device_in(t.handle) < base + arena.numel()
