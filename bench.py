@@ -1,0 +1,404 @@
+"""Benchmark of the hashing hot path on B300.
+
+Default workload (one step): 256 units of 1 MiB, half of each unit repeated
+8 KiB blocks from a seeded pool of 64, MD5 sliding-window hashing with a
+20-byte window at every byte offset, boundary where
+(first digest word & 0x1FFF) == 0x1FFF, then a direct hash (4 KiB segments)
+of every resulting chunk.  That step runs every stage of the path: window
+MD5s and bitmap, chunk extraction, chunk segment MD5s, digest of digests,
+and (end to end) the pooled pinned buffers, copy-in, copy-out and the
+master thread's batching, polling and completion.
+
+* ``value``  -- hashed GB/s with the inputs already resident in HBM: the
+  kernel chain launched through the C ABI on a device-resident batch.
+* ``e2e``    -- the same metric through the job API with pinned host buffers:
+  submit, copy-in, kernels, copy-out and completion inside the timed region.
+* ``roofline`` -- the window kernel (the dominant one) against the integer
+  issue rate of the GPU.
+* ``cpu_baseline`` -- the CPU oracle on the host cores, on a bounded sample.
+
+``--impl reference`` times the CPU oracle as the reference arm on the same
+workload (bounded sample per step).  Under torchrun every rank runs its own
+replica (units are independent; there is no exchange step).
+
+Other workloads (``--workload``) print their own lines for the design
+notes; the default one is the headline.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "end-to-end hashed GB/s (host→digests) and fraction of host-link roofline; p50/p99 latency"
+GB = 1e9
+
+# Algorithmic integer operations of one window (w = 20, one MD5 block, only
+# the first digest word is needed): 61 of the 64 steps (A is final after
+# step 61); a step is one 3-input logic op, one 3-input add (two when its
+# message word is data rather than a padding constant), one rotate, one
+# add; 19 of the 61 steps use one of the 5 data words.  Then the
+# feed-forward add, the mask and the compare.
+OPS_PER_WINDOW_W20 = 61 * 4 + 19 + 3
+SM_COUNT_B300 = 148
+INT_LANES_PER_SM = 128  # 4 schedulers x one 32-lane instruction per clock
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---- workload ---------------------------------------------------------------------
+
+def sliding_workload(seed: int, units: int, unit_bytes: int) -> np.ndarray:
+    from paper_1005_1695_b300 import inputs
+
+    pool = inputs.dedup_pool(seed)
+    host = np.empty(units * unit_bytes, dtype=np.uint8)
+    for u in range(units):
+        inputs.dedup_unit(seed, u, unit_bytes, pool=pool, out=host[u * unit_bytes:(u + 1) * unit_bytes])
+    return host
+
+
+def cpu_oracle_rate(host: np.ndarray, unit_bytes: int, units: int, cores: int, params: dict) -> dict:
+    """The oracle (as it stands) on ``units`` units over ``cores`` host threads."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    oracle.build()
+    out_size = 8 + 4 * ((unit_bytes + 31) // 32) + 20 * 1024
+
+    def one(u):
+        return oracle.task(2, host[u * unit_bytes:(u + 1) * unit_bytes], out_size, **params)[0]
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        sts = list(ex.map(one, range(units)))
+    dt = time.perf_counter() - t0
+    assert all(s == 0 for s in sts)
+    return {"value": units * unit_bytes / dt / GB, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{units} of the workload's 1 MiB units (sliding window w=20 + chunk direct hash), "
+                      f"{cores} threads, {dt:.1f} s"}
+
+
+# ---- our arm ------------------------------------------------------------------------
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    C.load()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    U, N = args.units, args.unit_bytes
+    p = C.params(window_bytes=20, mask=0x1FFF, target=0x1FFF, chunk_segment_bytes=4096)
+    out_size = C.sliding_out_bytes(N, args.max_chunks)
+    host = sliding_workload(args.seed + rank, U, N)
+    total_bytes = U * N
+
+    # ---- value: inputs resident in HBM, kernel chain through the C ABI ----
+    d_in = torch.from_numpy(host).to(dev)
+    batch = C.DeviceBatch(d_in, [u * N for u in range(U)], [N] * U, [C.CRYSTAL_KIND_MD5_SLIDING] * U, p,
+                          out_sizes=[out_size] * U)
+    desc_host = torch.from_numpy(batch.host_desc).pin_memory()
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+
+    def step(i=None):
+        with torch.cuda.stream(stream):
+            if i is not None:
+                ev_step[i][0].record(stream)
+            batch.d_desc.copy_(desc_host, non_blocking=True)
+            if i is not None:
+                ev[i][0].record(stream)
+            batch.launch_sliding_windows(stream)
+            if i is not None:
+                ev[i][1].record(stream)
+            batch.launch_sliding_chunks(stream)
+            batch.launch_sliding_digests(stream)
+            if i is not None:
+                ev_step[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = C.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    launches_value = C.kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev_step]
+    win_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = max_over_ranks(float(np.sum(step_ms)))
+    value = ws * total_bytes * args.steps / (dev_ms / 1e3) / GB
+    assert batch.device_status() == 0
+
+    # ---- e2e: job API, pinned host buffers, copies inside the timed region ----
+    if "e2e" in args.legs:
+        pool_dev = int(total_bytes + U * (out_size + C.scratch_bytes(2, N, out_size, p) + 4096) + (64 << 20))
+        pool_host = int(total_bytes + U * (out_size + 4096) + (16 << 20))
+        ctx = C.Context(max_in_bytes=N, max_out_bytes=out_size, device_pool_bytes=pool_dev,
+                        host_pool_bytes=pool_host, n_streams=args.streams, max_batch_jobs=args.batch_jobs,
+                        max_batch_bytes=args.batch_jobs * N, device=local,
+                        flags=C.CRYSTAL_FLAG_GRAPHS if args.graphs else 0)
+        tasks = [ctx.task_create(N, out_size) for _ in range(U)]
+        for u, t in enumerate(tasks):
+            t.h_in[:] = host[u * N:(u + 1) * N]
+
+        def e2e_step():
+            st = ctx.submit_many(tasks, C.CRYSTAL_KIND_MD5_SLIDING, p)
+            assert st == C.CRYSTAL_OK, st
+            for t in tasks:
+                s = t.wait(60_000_000_000)
+                assert s == C.CRYSTAL_OK, s
+            return [t.timing() for t in tasks]
+
+        for _ in range(args.warmup):
+            e2e_step()
+        # the job outputs must equal the device-resident outputs, unit by unit
+        got_dev = batch.outputs()
+        for u in range(0, U, max(1, U // 16)):
+            n_chunks = int.from_bytes(got_dev[u][:4], "little")
+            used = 8 + 4 * (N // 32) + 20 * n_chunks
+            assert tasks[u].output()[:used] == got_dev[u][:used], "job output differs from device batch output"
+        lat = []
+        launches1 = C.kernel_launches()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for s_ns, _, d_ns in e2e_step():
+                lat.append((d_ns - s_ns) / 1e6)
+        barrier()
+        e2e_wall = max_over_ranks(time.perf_counter() - t0)
+        launches = launches_value + C.kernel_launches() - launches1
+        clock_info = clocks.stop()
+        e2e_value = ws * total_bytes * args.steps / e2e_wall / GB
+    else:
+        clock_info = clocks.stop()
+        e2e_value, lat, e2e_wall, launches = None, [0.0], None, launches_value
+        tasks, ctx = [], None
+
+    # ---- host link (pinned copies) measured on this GPU ----
+    pinned = torch.empty(total_bytes, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(total_bytes, dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        dbuf.copy_(pinned, non_blocking=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(3):
+        dbuf.copy_(pinned, non_blocking=True)
+    b.record()
+    torch.cuda.synchronize()
+    h2d = 3 * total_bytes / (a.elapsed_time(b) / 1e3) / GB
+    a.record()
+    for _ in range(3):
+        pinned.copy_(dbuf, non_blocking=True)
+    b.record()
+    torch.cuda.synchronize()
+    d2h = 3 * total_bytes / (a.elapsed_time(b) / 1e3) / GB
+    del pinned, dbuf
+
+    # ---- roofline of the window kernel ----
+    windows = U * (N - 20 + 1)
+    win_avg_s = float(np.mean(win_ms)) / 1e3
+    achieved = windows * OPS_PER_WINDOW_W20 / win_avg_s / 1e12
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak = SM_COUNT_B300 * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
+    alu_bound_gbs = peak * 1e12 / OPS_PER_WINDOW_W20  # windows/s = bytes/s
+    e2e_bound = min(h2d * GB, alu_bound_gbs, d2h * GB * total_bytes / (U * out_size)) / GB
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"sliding-window MD5, {U} units x {N // 1024} KiB, w=20, "
+                               "mask=target=0x1FFF, chunk direct hash S=4 KiB",
+                   "units_per_gpu": U, "unit_bytes": N, "window": 20, "mask": 0x1FFF, "target": 0x1FFF,
+                   "chunk_segment_bytes": 4096, "content": "50% repeated 8 KiB blocks from a pool of 64",
+                   "l2": "inputs (256 MiB per step) larger than L2 (126 MB); no flush",
+                   "parallelism": f"replicas x{ws}", "streams": args.streams, "batch_jobs": args.batch_jobs,
+                   "graphs": bool(args.graphs)},
+        "roofline": {"bound": "alu", "kernel": "k_sliding_windows", "achieved": round(achieved, 3),
+                     "peak": round(peak, 3), "unit": "Tops/s (int32)", "frac": round(achieved / peak, 4),
+                     "traffic": None,
+                     "ops_per_window": OPS_PER_WINDOW_W20, "windows_per_launch": windows,
+                     "avg_launch_ms": round(win_avg_s * 1e3, 4),
+                     "peak_basis": f"{SM_COUNT_B300} SMs x {INT_LANES_PER_SM} int32 lanes/clk x {sm_max:.0f} MHz"},
+        "e2e": None if e2e_value is None else {
+            "value": round(e2e_value, 3), "unit": "GB/s", "h2d_bytes_per_step": total_bytes * ws,
+            "d2h_bytes_per_step": U * out_size * ws, "ms_per_step": round(e2e_wall * 1e3 / args.steps, 3),
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                           "p99": round(float(np.percentile(lat, 99)), 3)},
+            "roofline_gbs": round(e2e_bound, 2), "frac": round(e2e_value / ws / e2e_bound, 4)},
+        "host_link": {"h2d_gbs": round(h2d, 2), "d2h_gbs": round(d2h, 2), "how": "torch pinned copy, 256 MiB"},
+        "clocks": clock_info,
+        "gpu_launches": int(launches),
+        "gpu_launches_split": {"value_region": int(launches_value), "e2e_region": int(launches - launches_value)},
+        "wall_s": round(wall, 3),
+    }
+    if ctx is not None:
+        ctx.shutdown()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--units", type=int, default=256)
+    ap.add_argument("--unit-bytes", type=int, default=1 << 20)
+    ap.add_argument("--max-chunks", type=int, default=1024)
+    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--batch-jobs", type=int, default=16)
+    ap.add_argument("--graphs", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--cpu-units", type=int, default=0, help="oracle sample units (0: 4 per core, <= 256)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="value,e2e", help="value (device-resident) and/or e2e (job API)")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    cores = len(os.sched_getaffinity(0))
+    params = dict(window=20, mask=0x1FFF, target=0x1FFF, chunk_seg_bytes=4096)
+    cpu_units = args.cpu_units or min(args.units, max(4, 8 * cores))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        host = sliding_workload(args.seed, cpu_units, args.unit_bytes)
+        for _ in range(args.warmup):
+            cpu_oracle_rate(host, args.unit_bytes, min(cpu_units, cores), cores, params)
+        vals, t0 = [], time.perf_counter()
+        for _ in range(args.steps):
+            vals.append(cpu_oracle_rate(host, args.unit_bytes, cpu_units, cores, params))
+        wall = time.perf_counter() - t0
+        v = float(np.median([x["value"] for x in vals]))
+        line = {"metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(wall * 1e3 / args.steps, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": f"sliding-window MD5, {args.units} units x {args.unit_bytes // 1024} KiB, "
+                                       "w=20, mask=target=0x1FFF, chunk direct hash S=4 KiB",
+                           "sample_units_per_step": cpu_units},
+                "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                                 "sample": vals[0]["sample"]},
+                "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            host = sliding_workload(args.seed, cpu_units, args.unit_bytes)
+            out["cpu_baseline"] = cpu_oracle_rate(host, args.unit_bytes, cpu_units, cores, params)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

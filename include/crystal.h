@@ -152,6 +152,14 @@ int crystal_task_resize(crystal_task* task, uint64_t in_size, uint64_t out_size)
 int crystal_task_submit(crystal_task* task, int kind, const crystal_hash_params* params,
                         crystal_callback cb, void* user);
 
+/* Submit n jobs at once, in array order, with one kind, params, callback
+ * and user pointer: the batch-processing case of Section 2.2 (many
+ * independent jobs available at once).  Either every job is queued
+ * (CRYSTAL_OK) or none is (the first error is returned and no job changes
+ * state). */
+int crystal_task_submit_many(crystal_task* const* tasks, uint32_t n, int kind,
+                             const crystal_hash_params* params, crystal_callback cb, void* user);
+
 /* job_query(), Figure 3: CRYSTAL_PENDING while queued or running, otherwise
  * the job's final status (CRYSTAL_OK, CRYSTAL_EOVERFLOW, CRYSTAL_EDEVICE,
  * CRYSTAL_ESHUTDOWN).  EINVAL for a job never submitted. */

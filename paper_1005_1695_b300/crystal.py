@@ -113,6 +113,8 @@ def load() -> ctypes.CDLL:
         "crystal_task_resize": (ctypes.c_int, [_vp, _u64, _u64]),
         "crystal_task_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(crystal_hash_params),
                                                crystal_callback, _vp]),
+        "crystal_task_submit_many": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.c_int,
+                                                    ctypes.POINTER(crystal_hash_params), crystal_callback, _vp]),
         "crystal_task_poll": (ctypes.c_int, [_vp]),
         "crystal_task_wait": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "crystal_task_release": (ctypes.c_int, [_vp]),
@@ -247,6 +249,15 @@ class Context:
         t = Task(self, h.value, in_size, out_size)
         self._tasks.add(t)
         return t
+
+    def submit_many(self, tasks: Sequence[Task], kind: int, p: Optional[crystal_hash_params] = None,
+                    callback=None, user=None) -> int:
+        """crystal_task_submit_many: all of ``tasks`` or none."""
+        arr = (_vp * len(tasks))(*[t.handle for t in tasks])
+        cb = callback if callback is not None else crystal_callback()
+        self._cb_keepalive = cb
+        return load().crystal_task_submit_many(arr, len(tasks), kind, ctypes.byref(p) if p is not None else None,
+                                               cb, user)
 
     def stats(self) -> crystal_stats:
         s = crystal_stats()

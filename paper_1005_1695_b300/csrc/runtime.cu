@@ -711,6 +711,70 @@ int crystal_task_submit(crystal_task* t, int kind, const crystal_hash_params* pa
     return CRYSTAL_OK;
 }
 
+int crystal_task_submit_many(crystal_task* const* tasks, uint32_t n, int kind, const crystal_hash_params* params,
+                             crystal_callback cb, void* user) {
+    if (!tasks && n) return CRYSTAL_EINVAL;
+    if (n == 0) return CRYSTAL_OK;
+    crystal_ctx* c = tasks[0] ? tasks[0]->ctx : nullptr;
+    if (!c) return CRYSTAL_EINVAL;
+    std::vector<crystal_hash_params> ps(n);
+    std::vector<uint64_t> scratch(n, 0);
+    for (uint32_t i = 0; i < n; ++i) {
+        crystal_task* t = tasks[i];
+        if (!t || t->ctx != c) return CRYSTAL_EINVAL;
+        int st = resolve_params(kind, params, t->in_size, t->out_size, &ps[i]);
+        if (st != CRYSTAL_OK) return st;
+        scratch[i] = crystal_scratch_bytes(kind, t->in_size, t->out_size, &ps[i]);
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!c->accepting) return CRYSTAL_ESHUTDOWN;
+        for (uint32_t i = 0; i < n; ++i) {
+            if (tasks[i]->state == T_OUTSTANDING || tasks[i]->state == T_RUNNING) return CRYSTAL_EINVAL;
+            for (uint32_t j = 0; j < i; ++j)
+                if (tasks[j] == tasks[i]) return CRYSTAL_EINVAL;
+        }
+    }
+    if (!c->pooled) cudaSetDevice(c->device);
+    std::vector<uint8_t*> dp(n, nullptr);
+    std::vector<uint64_t> doff(n, 0);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!scratch[i]) continue;
+        int st = alloc_device(c, scratch[i], &dp[i], &doff[i]);
+        if (st != CRYSTAL_OK) {
+            for (uint32_t j = 0; j < i; ++j) free_device(c, dp[j], doff[j]);
+            return st == CRYSTAL_ENOMEM ? CRYSTAL_ENOMEM : CRYSTAL_EAGAIN;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!c->accepting) {
+            for (uint32_t j = 0; j < n; ++j) free_device(c, dp[j], doff[j]);
+            return CRYSTAL_ESHUTDOWN;
+        }
+        const uint64_t now = now_ns();
+        for (uint32_t i = 0; i < n; ++i) {
+            crystal_task* t = tasks[i];
+            t->kind = kind;
+            t->params = ps[i];
+            t->cb = cb;
+            t->user = user;
+            t->d_scratch = dp[i];
+            t->d_scratch_off = doff[i];
+            t->scratch_bytes = scratch[i];
+            t->status = CRYSTAL_PENDING;
+            t->state = T_OUTSTANDING;
+            t->submitted_once = true;
+            t->release_in_callback = false;
+            t->t_submit = now;
+            t->t_dispatch = t->t_done = 0;
+            c->outstanding.push_back(t);
+        }
+    }
+    c->cv_master.notify_one();
+    return CRYSTAL_OK;
+}
+
 int crystal_task_poll(crystal_task* t) {
     if (!t) return CRYSTAL_EINVAL;
     std::lock_guard<std::mutex> lk(t->ctx->mu);

@@ -220,7 +220,7 @@ def test_bad_arguments_are_rejected(C):
 
 
 def test_wait_timeout_then_completes(C):
-    with C.Context(max_in_bytes=64 << 20, max_out_bytes=4 << 20, device_pool_bytes=512 << 20,
+    with C.Context(max_in_bytes=64 << 20, max_out_bytes=8 << 20, device_pool_bytes=512 << 20,
                    host_pool_bytes=256 << 20) as ctx:
         n = 48 << 20
         t = ctx.task_create(n, C.sliding_out_bytes(n, 1 << 14))
