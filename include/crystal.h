@@ -236,19 +236,25 @@ typedef struct crystal_unit {
     uint64_t work_begin; /* filled by crystal_batch_plan: first global work item */
     uint32_t out_cap;    /* output bytes available */
     uint32_t seg_bytes;  /* direct: S; sliding: chunk S */
-    uint32_t window, mask, target;
-    uint32_t kind;       /* CRYSTAL_KIND_MD5_DIRECT or CRYSTAL_KIND_MD5_SLIDING */
+    uint16_t window;     /* sliding: w */
+    uint16_t kind;       /* CRYSTAL_KIND_MD5_DIRECT or CRYSTAL_KIND_MD5_SLIDING */
+    uint32_t mask, target;
+    uint32_t seg_base;   /* sliding: written by the kernels (first chunk segment of
+                            this unit among the batch's chunk segments) */
 } crystal_unit;
 
 typedef struct crystal_batch {
-    uint32_t n_direct;        /* units [0, n_direct) are direct */
-    uint32_t n_sliding;       /* units [n_direct, n_direct + n_sliding) are sliding */
-    uint64_t direct_segments; /* total segments over the direct units */
-    uint64_t sliding_tiles;   /* total window tiles over the sliding units */
-    uint32_t window_max;      /* largest window among the sliding units */
-    uint32_t status;          /* device status word: 0, or a bit set by a kernel that met
-                                 an inconsistent record (the record is skipped) */
-    uint64_t reserved[4];     /* header is 64 bytes */
+    uint32_t n_direct;          /* units [0, n_direct) are direct */
+    uint32_t n_sliding;         /* units [n_direct, n_direct + n_sliding) are sliding */
+    uint64_t direct_segments;   /* total segments over the direct units */
+    uint64_t sliding_tiles;     /* total window tiles over the sliding units */
+    uint32_t window_max;        /* largest window among the sliding units */
+    uint32_t status;            /* device status word: 0, or a bit set by a kernel that met
+                                   an inconsistent record (the record is skipped) */
+    uint64_t sliding_tiles_w20; /* tiles of the sliding units with w = 20, which the
+                                   planner places first */
+    uint64_t chunk_segments;    /* written by the kernels: chunk segments of the batch */
+    uint64_t reserved[2];       /* header is 64 bytes */
     /* crystal_unit units[n_direct + n_sliding] follow */
 } crystal_batch;
 
@@ -261,10 +267,13 @@ typedef struct crystal_batch {
 uint64_t crystal_scratch_bytes(int kind, uint64_t n, uint64_t out_size, const crystal_hash_params* params);
 
 /* Host-side planning of a batch in host memory (the header followed by the
- * unit records, units filled by the caller except work_begin): checks every
- * unit (kinds in order, sizes, windows 1..55, out_cap large enough, 16-byte
- * aligned scratch), fills work_begin and the header's totals.  The buffer is
- * then copied to the device as is.  Returns CRYSTAL_OK or CRYSTAL_EINVAL. */
+ * unit records, units filled by the caller except work_begin and seg_base):
+ * checks every unit (kinds in order, sizes, windows 1..55, out_cap large
+ * enough, 16-byte aligned scratch), moves the sliding units with w = 20 in
+ * front of the other sliding units (stable; each record keeps its own
+ * pointers, so results do not depend on the order), fills work_begin and the
+ * header's totals.  The buffer is then copied to the device as is.  Returns
+ * CRYSTAL_OK or CRYSTAL_EINVAL. */
 int crystal_batch_plan(crystal_batch* batch_host, uint32_t n_direct, uint32_t n_sliding);
 
 /* Bytes of a batch buffer holding n_units records. */

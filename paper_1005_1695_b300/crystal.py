@@ -74,8 +74,8 @@ class crystal_stats(ctypes.Structure):
 
 UNIT_DTYPE = np.dtype([
     ("in", "<u8"), ("n", "<u8"), ("out", "<u8"), ("scratch", "<u8"), ("work_begin", "<u8"),
-    ("out_cap", "<u4"), ("seg_bytes", "<u4"), ("window", "<u4"), ("mask", "<u4"), ("target", "<u4"),
-    ("kind", "<u4"),
+    ("out_cap", "<u4"), ("seg_bytes", "<u4"), ("window", "<u2"), ("kind", "<u2"), ("mask", "<u4"),
+    ("target", "<u4"), ("seg_base", "<u4"),
 ])
 assert UNIT_DTYPE.itemsize == 64
 BATCH_HEADER_BYTES = 64

@@ -3,7 +3,9 @@
 //   k_direct_segments  K1  one MD5 per segment of every direct unit
 //   k_direct_outer     K2  MD5 over each unit's concatenated segment digests
 //   k_sliding_windows  K3  MD5 of every w-byte window, boundary bitmap
+//                          (one instance for w = 20, one for any w in 1..55)
 //   k_sliding_chunks   K4  chunk ends from the bitmap, per-chunk segment table
+//   k_chunk_seg_scan   K4b where each unit's chunk segments start in the batch
 //   k_chunk_segments   K5a one MD5 per segment of every chunk
 //   k_chunk_outer      K5b MD5 over each chunk's segment digests
 //
@@ -42,6 +44,7 @@ constexpr int kStageWords = 284;
 constexpr int kSegThreads = 128;
 constexpr int kChunkThreads = 512;
 constexpr int kDigestThreads = 256;
+constexpr int kScanThreads = 1024;
 
 constexpr uint32_t kDevBadRecord = 1u;
 
@@ -78,7 +81,7 @@ __device__ __forceinline__ uint64_t num_segments(uint64_t n, uint32_t S) {
 
 // ---- K1: segment digests of direct units ------------------------------------
 
-__global__ void __launch_bounds__(kSegThreads) k_direct_segments(crystal_batch* B) {
+__global__ void __launch_bounds__(kSegThreads, 8) k_direct_segments(crystal_batch* B, uint32_t one) {
     const uint32_t nd = B->n_direct;
     const uint64_t total = B->direct_segments;
     const crystal_unit* U = units_of(B);
@@ -90,21 +93,21 @@ __global__ void __launch_bounds__(kSegThreads) k_direct_segments(crystal_batch* 
         const uint64_t off = j * X.seg_bytes;
         const uint64_t len = X.n > off ? (X.n - off < X.seg_bytes ? X.n - off : X.seg_bytes) : 0;
         uint32_t st[4];
-        md5::digest_global(reinterpret_cast<const uint8_t*>(X.in) + off, len, st);
+        md5::digest_global(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
         store_digest16(reinterpret_cast<uint8_t*>(X.scratch) + 16 * j, st);
     }
 }
 
 // ---- K2: digest of digests -------------------------------------------------
 
-__global__ void __launch_bounds__(kDigestThreads) k_direct_outer(crystal_batch* B) {
+__global__ void __launch_bounds__(kDigestThreads) k_direct_outer(crystal_batch* B, uint32_t one) {
     const uint32_t nd = B->n_direct;
     const crystal_unit* U = units_of(B);
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nd; u += gridDim.x * blockDim.x) {
         const crystal_unit X = U[u];
         const uint64_t m = num_segments(X.n, X.seg_bytes);
         uint32_t st[4];
-        md5::digest_global(reinterpret_cast<const uint8_t*>(X.scratch), 16 * m, st);
+        md5::digest_global(reinterpret_cast<const uint8_t*>(X.scratch), 16 * m, st, one);
         store_digest(reinterpret_cast<uint8_t*>(X.out), st);
     }
 }
@@ -152,9 +155,8 @@ __device__ __forceinline__ void window_block(const uint32_t* sw, uint32_t p, uin
 }
 
 template <int W>
-__device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t delta, uint64_t base,
-                                                 uint64_t n, uint32_t w, uint32_t mask,
-                                                 uint32_t target) {
+__device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t delta, uint32_t lim, uint32_t w,
+                                                 uint32_t mask, uint32_t target, uint32_t one) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t A[kWinPerThread];
@@ -163,56 +165,84 @@ __device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t de
         const uint32_t rel = warp * 128 + r * 32 + lane;
         uint32_t X[16];
         window_block<W>(sw, rel + delta, w, X);
-        A[r] = md5::first_word_one_block(X);
+        A[r] = md5::first_word_one_block(X, one);
     }
     uint32_t mine = 0;
 #pragma unroll
     for (int r = 0; r < kWinPerThread; ++r) {
-        const uint64_t i = base + warp * 128 + r * 32 + lane;
-        const bool hit = (i + w <= n) && ((A[r] & mask) == target);
+        const uint32_t rel = warp * 128 + r * 32 + lane;
+        const bool hit = (rel + w <= lim) && ((A[r] & mask) == target);
         const uint32_t word = __ballot_sync(0xffffffffu, hit);
         if (lane == (uint32_t)r) mine = word;
     }
     return mine;
 }
 
-__global__ void __launch_bounds__(kWinThreads) k_sliding_windows(crystal_batch* B) {
-    __shared__ __align__(16) uint32_t sw[kStageWords];
+__device__ __forceinline__ void cp_async16(uint32_t* smem_dst, uint64_t gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Issue the copies of one tile's bytes [base, min(n, base + kTile + w - 1))
+// from their 16-byte aligned block on into smem; vectors past the unit's end
+// are not loaded.
+__device__ __forceinline__ void stage_tile(uint32_t* sw, const crystal_unit& X, uint64_t base) {
+    const uint64_t a = X.in + base;
+    const uint32_t delta = (uint32_t)(a & 15);
+    const uint64_t a0 = a - delta;
+    const uint64_t span = (uint64_t)(kTile + X.window - 1);
+    const uint64_t want = X.n - base < span ? X.n - base : span;
+    const uint32_t nvec = (uint32_t)((delta + want + 15) >> 4);
+    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) cp_async16(sw + 4 * v, a0 + 16ull * v);
+}
+
+// W = 20: tiles [0, sliding_tiles_w20), whose units all have w = 20 (the
+// planner puts them first); W = 0: the remaining tiles, any w in 1..55.
+// The next tile's bytes are copied into the other half of a double buffer
+// while the current tile is hashed.
+template <int W>
+__global__ void __launch_bounds__(kWinThreads) k_sliding_windows(crystal_batch* B, uint32_t one) {
+    __shared__ __align__(16) uint32_t sw[2][kStageWords];
     const uint32_t ns = B->n_sliding;
-    const uint64_t total = B->sliding_tiles;
     const crystal_unit* U = units_of(B) + B->n_direct;
-    for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        const uint32_t u = owner_of(U, ns, t);
-        const crystal_unit X = U[u];
-        const uint64_t base = (t - X.work_begin) * (uint64_t)kTile;
-        const uint32_t w = X.window;
-        // Stage bytes [base, min(n, base + kTile + w - 1)) from their 16-byte
-        // aligned block on; vectors past the unit's end are not loaded.
-        const uint64_t a = X.in + base;
-        const uint32_t delta = (uint32_t)(a & 15);
-        const uint64_t a0 = a - delta;
-        const uint64_t want = X.n - base < (uint64_t)(kTile + w - 1) ? X.n - base : (uint64_t)(kTile + w - 1);
-        const uint32_t nvec = (uint32_t)((delta + want + 15) >> 4);
-        uint4* sv = reinterpret_cast<uint4*>(sw);
-        for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
-            sv[v] = md5::ldg_stream16(reinterpret_cast<const void*>(a0 + 16ull * v));
+    const uint64_t lo = W == 20 ? 0 : B->sliding_tiles_w20;
+    const uint64_t hi = W == 20 ? B->sliding_tiles_w20 : B->sliding_tiles;
+    uint64_t t = lo + blockIdx.x;
+    if (t >= hi) return;
+    uint32_t u = owner_of(U, ns, t);
+    stage_tile(sw[0], U[u], (t - U[u].work_begin) * (uint64_t)kTile);
+    cp_async_commit();
+    int buf = 0;
+    for (; t < hi; t += gridDim.x) {
+        const uint64_t tn = t + gridDim.x;
+        uint32_t un = 0;
+        if (tn < hi) {
+            un = owner_of(U, ns, tn);
+            stage_tile(sw[buf ^ 1], U[un], (tn - U[un].work_begin) * (uint64_t)kTile);
         }
+        cp_async_commit();
+        cp_async_wait<1>();
         __syncthreads();
-        uint32_t mine;
-        if (w == 20) {
-            mine = tile_windows<20>(sw, delta, base, X.n, w, X.mask, X.target);
-        } else {
-            mine = tile_windows<0>(sw, delta, base, X.n, w, X.mask, X.target);
-        }
+        const crystal_unit& X = U[u];
+        const uint64_t base = (t - X.work_begin) * (uint64_t)kTile;
+        const uint32_t delta = (uint32_t)((X.in + base) & 15);
+        const uint64_t left = X.n - base;
+        const uint32_t lim = left < (uint64_t)(2 * kTile) ? (uint32_t)left : (uint32_t)(2 * kTile);
+        const uint32_t w = W > 0 ? (uint32_t)W : (uint32_t)X.window;
+        const uint32_t mine = tile_windows<W>(sw[buf], delta, lim, w, X.mask, X.target, one);
         const uint32_t lane = threadIdx.x & 31;
         if (lane < (uint32_t)kWinPerThread) {
             const uint64_t word = (base >> 5) + (threadIdx.x >> 5) * 4 + lane;
-            if (word < ((X.n + 31) >> 5)) {
-                reinterpret_cast<uint32_t*>(X.out + 8)[word] = mine;
-            }
+            if (word < ((X.n + 31) >> 5)) reinterpret_cast<uint32_t*>(X.out + 8)[word] = mine;
         }
         __syncthreads();
+        u = un;
+        buf ^= 1;
     }
+    cp_async_wait<0>();
 }
 
 // ---- K4: chunk ends and per-chunk segment table ------------------------------
@@ -258,7 +288,10 @@ __global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch*
         const uint32_t* bm = hdr + 2;
         uint32_t* seg_prefix = reinterpret_cast<uint32_t*>(X.scratch);
         if (X.out_cap < fixed) {
-            if (threadIdx.x == 0) atomicOr(&B->status, kDevBadRecord);
+            if (threadIdx.x == 0) {
+                atomicOr(&B->status, kDevBadRecord);
+                U[u].seg_base = 0;
+            }
             continue;
         }
         const uint64_t cap = (X.out_cap - fixed) / 20;
@@ -282,7 +315,10 @@ __global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch*
             hdr[1] = fits ? 0u : 1u;
         }
         if (!fits) {
-            if (threadIdx.x == 0) seg_prefix[0] = 0;  // no chunk segments to hash
+            if (threadIdx.x == 0) {
+                seg_prefix[0] = 0;  // no chunk segments to hash
+                U[u].seg_base = 0;
+            }
             __syncthreads();
             continue;
         }
@@ -314,8 +350,37 @@ __global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch*
             const uint64_t start = c == 0 ? 0 : ends[c - 1];
             run += num_segments(ends[c] - start, S);
         }
-        if (threadIdx.x == 0) seg_prefix[n_chunks] = (uint32_t)total_segs;
+        if (threadIdx.x == 0) {
+            seg_prefix[n_chunks] = (uint32_t)total_segs;
+            U[u].seg_base = (uint32_t)total_segs;  // a count here; k_chunk_seg_scan makes it a start
+        }
         __syncthreads();
+    }
+}
+
+// ---- K4b: where each unit's chunk segments start ---------------------------
+
+// One block: turns the per-unit chunk-segment counts K4 left in seg_base into
+// exclusive starts and stores the batch total.
+__global__ void __launch_bounds__(kScanThreads) k_chunk_seg_scan(crystal_batch* B) {
+    __shared__ uint64_t scan_sh[kScanThreads / 32 + 1];
+    const uint32_t ns = B->n_sliding;
+    crystal_unit* U = units_of(B) + B->n_direct;
+    uint64_t carry = 0;
+    for (uint32_t lo = 0; lo < ns; lo += kScanThreads) {
+        const uint32_t i = lo + threadIdx.x;
+        const uint64_t v = i < ns ? U[i].seg_base : 0;
+        uint64_t total;
+        const uint64_t before = block_exclusive_scan<kScanThreads>(v, scan_sh, total);
+        if (i < ns) U[i].seg_base = (uint32_t)(carry + before);
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        if (carry >> 32) {  // starts no longer fit 32 bits: hash no chunk segment, flag the batch
+            atomicOr(&B->status, kDevBadRecord);
+            carry = 0;
+        }
+        B->chunk_segments = carry;
     }
 }
 
@@ -327,44 +392,47 @@ __device__ __forceinline__ uint8_t* chunk_digest_area(const crystal_unit& X, uin
 
 // ---- K5a: chunk segment digests ---------------------------------------------
 
-__global__ void __launch_bounds__(kDigestThreads) k_chunk_segments(crystal_batch* B) {
+// One thread per chunk segment of the whole batch: the unit comes from the
+// starts K4b wrote, the chunk from the unit's segment table.
+__global__ void __launch_bounds__(kDigestThreads, 4) k_chunk_segments(crystal_batch* B, uint32_t one) {
     const uint32_t ns = B->n_sliding;
     const crystal_unit* U = units_of(B) + B->n_direct;
-    for (uint32_t u = blockIdx.x; u < ns; u += gridDim.x) {
-        const crystal_unit X = U[u];
+    const uint64_t total = B->chunk_segments;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        uint32_t lo = 0, hi = ns;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (U[mid].seg_base <= g) lo = mid; else hi = mid;
+        }
+        const crystal_unit X = U[lo];
+        const uint32_t t = (uint32_t)(g - X.seg_base);
         const uint64_t words = (X.n + 31) >> 5;
         const uint64_t fixed = 8 + 4 * words;
-        if (X.out_cap < fixed) continue;
         const uint32_t* hdr = reinterpret_cast<const uint32_t*>(X.out);
-        if (hdr[1] & 1u) continue;
         const uint32_t n_chunks = hdr[0];
         const uint64_t cap = (X.out_cap - fixed) / 20;
         const uint32_t* ends = hdr + 2 + words;
         const uint32_t* seg_prefix = reinterpret_cast<const uint32_t*>(X.scratch);
-        const uint32_t T = seg_prefix[n_chunks];
-        uint8_t* dig = chunk_digest_area(X, cap);
-        const uint32_t S = X.seg_bytes;
-        for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) {
-            // chunk c: last with seg_prefix[c] <= t
-            uint32_t lo = 0, hi = n_chunks;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (seg_prefix[mid] <= t) lo = mid; else hi = mid;
-            }
-            const uint64_t start = lo == 0 ? 0 : ends[lo - 1];
-            const uint64_t end = ends[lo];
-            const uint64_t off = start + (uint64_t)(t - seg_prefix[lo]) * S;
-            const uint64_t len = end > off ? (end - off < S ? end - off : S) : 0;
-            uint32_t st[4];
-            md5::digest_global(reinterpret_cast<const uint8_t*>(X.in) + off, len, st);
-            store_digest16(dig + 16ull * t, st);
+        uint32_t clo = 0, chi = n_chunks;  // chunk: last with seg_prefix[c] <= t
+        while (chi - clo > 1) {
+            const uint32_t mid = (clo + chi) >> 1;
+            if (seg_prefix[mid] <= t) clo = mid; else chi = mid;
         }
+        const uint32_t S = X.seg_bytes;
+        const uint64_t start = clo == 0 ? 0 : ends[clo - 1];
+        const uint64_t end = ends[clo];
+        const uint64_t off = start + (uint64_t)(t - seg_prefix[clo]) * S;
+        const uint64_t len = end > off ? (end - off < S ? end - off : S) : 0;
+        uint32_t st[4];
+        md5::digest_global(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
+        store_digest16(chunk_digest_area(X, cap) + 16ull * t, st);
     }
 }
 
 // ---- K5b: chunk digests ------------------------------------------------------
 
-__global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B) {
+__global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B, uint32_t one) {
     const uint32_t ns = B->n_sliding;
     const crystal_unit* U = units_of(B) + B->n_direct;
     for (uint32_t u = blockIdx.x; u < ns; u += gridDim.x) {
@@ -382,7 +450,7 @@ __global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B
         for (uint32_t c = threadIdx.x; c < n_chunks; c += blockDim.x) {
             const uint32_t s0 = seg_prefix[c], s1 = seg_prefix[c + 1];
             uint32_t st[4];
-            md5::digest_global(dig + 16ull * s0, 16ull * (s1 - s0), st);
+            md5::digest_global(dig + 16ull * s0, 16ull * (s1 - s0), st, one);
             store_digest(out_dig + 16ull * c, st);
         }
     }
@@ -392,12 +460,18 @@ __global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B
 
 struct Geometry {
     int sms = 0;
-    int seg_blocks = 0, outer_blocks = 0, win_blocks = 0, unit_blocks = 0;
+    int seg_blocks = 0, outer_blocks = 0, win20_blocks = 0, win_blocks = 0, unit_blocks = 0, digest_blocks = 0;
 };
 
 constexpr int kMaxDevices = 64;
 Geometry g_geom[kMaxDevices];
 std::once_flag g_geom_once[kMaxDevices];
+
+int resident(const void* fn, int threads) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0);
+    return occ > 0 ? occ : 1;
+}
 
 const Geometry* geometry() {
     int dev = 0;
@@ -405,11 +479,10 @@ const Geometry* geometry() {
     std::call_once(g_geom_once[dev], [dev] {
         Geometry g;
         cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev);
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direct_segments, kSegThreads, 0);
-        g.seg_blocks = g.sms * (occ > 0 ? occ : 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sliding_windows, kWinThreads, 0);
-        g.win_blocks = g.sms * (occ > 0 ? occ : 1);
+        g.seg_blocks = g.sms * resident((const void*)k_direct_segments, kSegThreads);
+        g.win20_blocks = g.sms * resident((const void*)k_sliding_windows<20>, kWinThreads);
+        g.win_blocks = g.sms * resident((const void*)k_sliding_windows<0>, kWinThreads);
+        g.digest_blocks = g.sms * resident((const void*)k_chunk_segments, kDigestThreads);
         g.outer_blocks = g.sms * 2;
         g.unit_blocks = g.sms * 2;
         g_geom[dev] = g;
@@ -417,8 +490,11 @@ const Geometry* geometry() {
     return g_geom[dev].sms > 0 ? &g_geom[dev] : nullptr;
 }
 
-int launched(cudaError_t e, int kernels) {
-    if (e != cudaSuccess) return CRYSTAL_EDEVICE;
+// Passed to every hashing kernel as its `one` argument (see md5::add_on_fma).
+uint32_t g_one = 1;
+
+int launched(int kernels) {
+    if (cudaGetLastError() != cudaSuccess) return CRYSTAL_EDEVICE;
     g_kernel_launches.fetch_add((uint64_t)kernels, std::memory_order_relaxed);
     return CRYSTAL_OK;
 }
@@ -428,39 +504,39 @@ int launched(cudaError_t e, int kernels) {
 int launch_direct_segments(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
     if (!g) return CRYSTAL_EDEVICE;
-    k_direct_segments<<<g->seg_blocks, kSegThreads, 0, s>>>(b);
-    return launched(cudaGetLastError(), 1);
+    k_direct_segments<<<g->seg_blocks, kSegThreads, 0, s>>>(b, g_one);
+    return launched(1);
 }
 
 int launch_direct_outer(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
     if (!g) return CRYSTAL_EDEVICE;
-    k_direct_outer<<<g->outer_blocks, kDigestThreads, 0, s>>>(b);
-    return launched(cudaGetLastError(), 1);
+    k_direct_outer<<<g->outer_blocks, kDigestThreads, 0, s>>>(b, g_one);
+    return launched(1);
 }
 
 int launch_sliding_windows(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
     if (!g) return CRYSTAL_EDEVICE;
-    k_sliding_windows<<<g->win_blocks, kWinThreads, 0, s>>>(b);
-    return launched(cudaGetLastError(), 1);
+    k_sliding_windows<20><<<g->win20_blocks, kWinThreads, 0, s>>>(b, g_one);
+    k_sliding_windows<0><<<g->win_blocks, kWinThreads, 0, s>>>(b, g_one);
+    return launched(2);
 }
 
 int launch_sliding_chunks(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
     if (!g) return CRYSTAL_EDEVICE;
     k_sliding_chunks<<<g->unit_blocks, kChunkThreads, 0, s>>>(b);
-    return launched(cudaGetLastError(), 1);
+    k_chunk_seg_scan<<<1, kScanThreads, 0, s>>>(b);
+    return launched(2);
 }
 
 int launch_sliding_digests(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
     if (!g) return CRYSTAL_EDEVICE;
-    k_chunk_segments<<<g->unit_blocks, kDigestThreads, 0, s>>>(b);
-    if (cudaGetLastError() != cudaSuccess) return CRYSTAL_EDEVICE;
-    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-    k_chunk_outer<<<g->unit_blocks, kDigestThreads, 0, s>>>(b);
-    return launched(cudaGetLastError(), 1);
+    k_chunk_segments<<<g->digest_blocks, kDigestThreads, 0, s>>>(b, g_one);
+    k_chunk_outer<<<g->unit_blocks, kDigestThreads, 0, s>>>(b, g_one);
+    return launched(2);
 }
 
 }  // namespace crystal

@@ -49,12 +49,24 @@ constexpr uint32_t kIV3 = 0x10325476u;
 
 __device__ __forceinline__ uint32_t rotl(uint32_t x, int s) { return __funnelshift_l(x, x, s); }
 
+// x * one + y with `one` a run-time 1 the compiler cannot see through: the
+// add then issues as an integer multiply-add on the FMA pipe instead of the
+// integer ALU pipe.  On sm_103a the ALU pipe takes one warp instruction every
+// two cycles per scheduler and bounds this hash; moving the add that joins
+// the round function into the running sum to the FMA pipe was measured
+// faster (moving the other adds, or the rotate, was measured slower).
+__device__ __forceinline__ uint32_t add_on_fma(uint32_t x, uint32_t one, uint32_t y) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(y));
+    return d;
+}
+
 // One step: b' = b + ((a + f(b,c,d) + X[k] + T[i]) <<< s), then the register
 // names rotate (a, b, c, d) <- (d, b', b, c).  The sum not involving b is
 // formed first so the dependent chain through b is f -> add -> rotate -> add.
 template <int I>
 __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d,
-                                     const uint32_t (&X)[16]) {
+                                     const uint32_t (&X)[16], uint32_t one) {
     uint32_t f;
     if constexpr (I < 16) {
         f = d ^ (b & (c ^ d));          // F = (b & c) | (~b & d)
@@ -66,7 +78,7 @@ __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint
         f = c ^ (b | ~d);               // I
     }
     const uint32_t pre = a + (kT(I) + X[kWord(I)]);
-    const uint32_t t = pre + f;
+    const uint32_t t = add_on_fma(f, one, pre);
     const uint32_t nb = b + rotl(t, kRot(I));
     a = d;
     d = c;
@@ -76,21 +88,21 @@ __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint
 
 template <int... I>
 __device__ __forceinline__ void steps_seq(std::integer_sequence<int, I...>, uint32_t& a, uint32_t& b,
-                                          uint32_t& c, uint32_t& d, const uint32_t (&X)[16]) {
-    (step<I>(a, b, c, d, X), ...);
+                                          uint32_t& c, uint32_t& d, const uint32_t (&X)[16], uint32_t one) {
+    (step<I>(a, b, c, d, X, one), ...);
 }
 
 // The first N steps of the compression function.
 template <int N>
 __device__ __forceinline__ void steps(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d,
-                                      const uint32_t (&X)[16]) {
-    steps_seq(std::make_integer_sequence<int, N>{}, a, b, c, d, X);
+                                      const uint32_t (&X)[16], uint32_t one) {
+    steps_seq(std::make_integer_sequence<int, N>{}, a, b, c, d, X, one);
 }
 
 // Full compression of one 16-word block into the chaining state.
-__device__ __forceinline__ void compress(uint32_t (&st)[4], const uint32_t (&X)[16]) {
+__device__ __forceinline__ void compress(uint32_t (&st)[4], const uint32_t (&X)[16], uint32_t one) {
     uint32_t a = st[0], b = st[1], c = st[2], d = st[3];
-    steps<64>(a, b, c, d, X);
+    steps<64>(a, b, c, d, X, one);
     st[0] += a;
     st[1] += b;
     st[2] += c;
@@ -100,9 +112,9 @@ __device__ __forceinline__ void compress(uint32_t (&st)[4], const uint32_t (&X)[
 // First digest word of a one-block message: after step 61 the register A
 // holds its final value (steps 62..64 only update D, C, B), so three steps
 // are skipped.  Returns A + IV_A, i.e. LE32 of digest bytes 0..3.
-__device__ __forceinline__ uint32_t first_word_one_block(const uint32_t (&X)[16]) {
+__device__ __forceinline__ uint32_t first_word_one_block(const uint32_t (&X)[16], uint32_t one) {
     uint32_t a = kIV0, b = kIV1, c = kIV2, d = kIV3;
-    steps<61>(a, b, c, d, X);
+    steps<61>(a, b, c, d, X, one);
     return kIV0 + b;
 }
 
@@ -128,41 +140,60 @@ __device__ __forceinline__ uint32_t ldg32(const uint32_t* p) { return __ldg(p); 
 // MD5 of len bytes at p (any alignment) in global memory; the digest words
 // (A, B, C, D) land in st.  Bytes outside [p, p + len) are read only inside
 // 4-byte-aligned words that also hold a byte of the message, and never used.
-__device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, uint32_t (&st)[4]) {
+__device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, uint32_t (&st)[4], uint32_t one) {
     init(st);
     const uint64_t addr = reinterpret_cast<uint64_t>(p);
     const uint64_t full = len >> 6;
     uint32_t X[16];
     if ((addr & 15) == 0) {
+        // the next block's loads are in flight while this block compresses
         const uint8_t* q = p;
-        for (uint64_t blk = 0; blk < full; ++blk, q += 64) {
+        uint4 nx[4];
+        if (full) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) nx[v] = ldg_stream16(q + 16 * v);
+        }
+        for (uint64_t blk = 0; blk < full; ++blk) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                uint4 w = ldg_stream16(q + 16 * v);
-                X[4 * v + 0] = w.x;
-                X[4 * v + 1] = w.y;
-                X[4 * v + 2] = w.z;
-                X[4 * v + 3] = w.w;
+                X[4 * v + 0] = nx[v].x;
+                X[4 * v + 1] = nx[v].y;
+                X[4 * v + 2] = nx[v].z;
+                X[4 * v + 3] = nx[v].w;
             }
-            compress(st, X);
+            q += 64;
+            if (blk + 1 < full) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) nx[v] = ldg_stream16(q + 16 * v);
+            }
+            compress(st, X, one);
         }
     } else if ((addr & 3) == 0) {
         const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
         for (uint64_t blk = 0; blk < full; ++blk, q += 16) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) X[k] = ldg32(q + k);
-            compress(st, X);
+            compress(st, X, one);
         }
     } else {
         const uint32_t sh = (uint32_t)(addr & 3) * 8;
         const uint32_t* q = reinterpret_cast<const uint32_t*>(addr & ~uint64_t(3));
-        for (uint64_t blk = 0; blk < full; ++blk, q += 16) {
-            uint32_t x[17];
+        uint32_t x[17];
+        if (full) {
 #pragma unroll
             for (int k = 0; k < 17; ++k) x[k] = ldg32(q + k);
+        }
+        for (uint64_t blk = 0; blk < full; ++blk) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) X[k] = __funnelshift_r(x[k], x[k + 1], sh);
-            compress(st, X);
+            q += 16;
+            // next block: words 1..17 of it; word 0 is this block's word 16
+            if (blk + 1 < full) {
+                x[0] = x[16];
+#pragma unroll
+                for (int k = 1; k < 17; ++k) x[k] = ldg32(q + k);
+            }
+            compress(st, X, one);
         }
     }
     // Tail: rem < 64 bytes, then 0x80, zeros, 64-bit bit length.
@@ -190,14 +221,14 @@ __device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, ui
     if (rem < 56) {
         X[14] = (uint32_t)bits;
         X[15] = (uint32_t)(bits >> 32);
-        compress(st, X);
+        compress(st, X, one);
     } else {
-        compress(st, X);
+        compress(st, X, one);
 #pragma unroll
         for (int k = 0; k < 14; ++k) X[k] = 0;
         X[14] = (uint32_t)bits;
         X[15] = (uint32_t)(bits >> 32);
-        compress(st, X);
+        compress(st, X, one);
     }
 }
 

@@ -8,6 +8,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -176,14 +177,24 @@ int crystal_batch_plan(crystal_batch* b, uint32_t n_direct, uint32_t n_sliding) 
         x.work_begin = segs;
         segs += segments_of(x.n, x.seg_bytes);
     }
-    for (uint32_t i = n_direct; i < n_direct + n_sliding; ++i) {
-        crystal_unit& x = U[i];
+    crystal_unit* S = U + n_direct;
+    for (uint32_t i = 0; i < n_sliding; ++i) {
+        const crystal_unit& x = S[i];
         if (x.kind != CRYSTAL_KIND_MD5_SLIDING || x.seg_bytes == 0) return CRYSTAL_EINVAL;
         if (x.window == 0 || x.window > kMaxWindow || x.n >= (1ull << 32)) return CRYSTAL_EINVAL;
         if (x.out_cap < sliding_fixed_bytes(x.n)) return CRYSTAL_EINVAL;
         if ((x.scratch & 15) || (x.out & 3) || !x.scratch || !x.out || (!x.in && x.n)) return CRYSTAL_EINVAL;
+    }
+    // w = 20 units first (stable): the window kernel has a specialised
+    // instance for them and one for every other window length
+    std::stable_partition(S, S + n_sliding, [](const crystal_unit& x) { return x.window == 20; });
+    uint64_t tiles_w20 = 0;
+    for (uint32_t i = 0; i < n_sliding; ++i) {
+        crystal_unit& x = S[i];
         x.work_begin = tiles;
+        x.seg_base = 0;
         tiles += (x.n + CRYSTAL_SLIDING_TILE - 1) / CRYSTAL_SLIDING_TILE;
+        if (x.window == 20) tiles_w20 = tiles;
         if (x.window > wmax) wmax = x.window;
     }
     b->n_direct = n_direct;
@@ -192,6 +203,8 @@ int crystal_batch_plan(crystal_batch* b, uint32_t n_direct, uint32_t n_sliding) 
     b->sliding_tiles = tiles;
     b->window_max = wmax;
     b->status = 0;
+    b->sliding_tiles_w20 = tiles_w20;
+    b->chunk_segments = 0;
     memset(b->reserved, 0, sizeof b->reserved);
     return CRYSTAL_OK;
 }

@@ -212,10 +212,11 @@ void build_descriptor(Slot& s, uint32_t* nd_out, uint32_t* ns_out) {
             x.out_cap = (uint32_t)std::min<uint64_t>(t->out_size, 0xFFFFFFFFull);
             x.seg_bytes = want == CRYSTAL_KIND_MD5_DIRECT ? t->params.segment_bytes
                                                           : t->params.chunk_segment_bytes;
-            x.window = t->params.window_bytes;
+            x.window = (uint16_t)t->params.window_bytes;
             x.mask = t->params.mask;
             x.target = t->params.target;
-            x.kind = (uint32_t)want;
+            x.kind = (uint16_t)want;
+            x.seg_base = 0;
         }
         if (pass == 0) *nd_out = k;
     }
@@ -236,7 +237,7 @@ int launch_chain(crystal_batch* d, cudaStream_t st, bool direct, bool sliding) {
     return r;
 }
 
-int kernels_in_chain(bool direct, bool sliding) { return (direct ? 2 : 0) + (sliding ? 4 : 0); }
+int kernels_in_chain(bool direct, bool sliding) { return (direct ? 2 : 0) + (sliding ? 6 : 0); }
 
 // Capture descriptor upload + kernel chain of one slot as a graph.
 int capture_graph(crystal_ctx* c, Slot& s, int variant) {
