@@ -301,6 +301,41 @@ int crystal_launch_sliding_chunks(const crystal_batch* batch_dev, void* stream);
 int crystal_launch_sliding_digests(const crystal_batch* batch_dev, void* stream);
 int crystal_launch_batch(const crystal_batch* batch_dev, void* stream);
 
+/* ---- direct hashing that allocates nothing --------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory where they hash: a thread on a storage or network
+ * data path with a fixed latency budget (cudaMalloc and cudaFree can
+ * synchronise the whole device and take milliseconds), or a process whose
+ * free device memory already belongs to another allocator, so that a new
+ * cudaMalloc would fail.
+ *
+ * crystal_md5_direct_noalloc hashes n_units units of unit_bytes each, lying
+ * back to back from d_in (device memory), with direct hashing at segment size
+ * segment_bytes, and writes unit u's 16-byte digest at d_digests + 16 u
+ * (device memory, 4-byte aligned).  It is asynchronous on `stream`
+ * (cudaStream_t as void*).  Its batch descriptor and segment digests live in
+ * a fixed device array of CRYSTAL_NOALLOC_SCRATCH_BYTES inside the library,
+ * which every GPU that loads the library holds until the process exits; the
+ * call itself allocates nothing.
+ *   - Limit: align_up(64 + 64 n_units, 256) + 16 n_units ceil(unit_bytes /
+ *     segment_bytes) (a unit of 0 bytes counts one segment) must not exceed
+ *     CRYSTAL_NOALLOC_SCRATCH_BYTES; a larger request returns CRYSTAL_EINVAL
+ *     and launches nothing.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.  A failed lookup returns CRYSTAL_EDEVICE.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; each call rewrites everything it reads before reading it.
+ *     Calls whose work overlaps on the GPU (different streams, or different
+ *     host threads without ordering between them) race on the array and give
+ *     wrong digests: order them, e.g. issue them on one stream.
+ * Returns CRYSTAL_OK (also for n_units = 0), CRYSTAL_EINVAL (NULL pointers,
+ * segment_bytes = 0, misaligned d_digests, or the size limit) or
+ * CRYSTAL_EDEVICE (launch failure). */
+#define CRYSTAL_NOALLOC_SCRATCH_BYTES (8u << 20)
+int crystal_md5_direct_noalloc(const void* d_in, uint64_t unit_bytes, uint32_t n_units, uint32_t segment_bytes,
+                               void* d_digests, void* stream);
+
 /* Host-side arena allocator the pools use (exposed for tests; no GPU
  * needed).  Offsets are relative to 0; alignment is a power of two. */
 typedef struct crystal_arena crystal_arena;

@@ -539,11 +539,100 @@ int launch_sliding_digests(crystal_batch* b, cudaStream_t s) {
     return launched(2);
 }
 
+// ---- direct hashing that allocates nothing ------------------------------------
+//
+// Some callers cannot allocate device memory on their data path: a host
+// thread in a storage or network data path with a fixed latency budget
+// (cudaMalloc and cudaFree may synchronise the whole device and take
+// milliseconds), or a process whose free device memory has all been handed
+// to another allocator, so a new cudaMalloc would fail.  For them the batch
+// descriptor and the segment digests of crystal_md5_direct_noalloc live in
+// this fixed array instead of caller-allocated scratch.  Every GPU that loads
+// the library holds it until the process exits.
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[CRYSTAL_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_noalloc_scratch per device, looked up once per device.
+uint8_t* g_noalloc_addr[kMaxDevices];
+std::once_flag g_noalloc_once[kMaxDevices];
+cudaError_t g_noalloc_err[kMaxDevices];
+
+// Writes the batch header and one record per unit (units back to back in
+// d_in, digests of unit u at d_out + 16u) into the fixed array.
+__global__ void k_noalloc_describe(crystal_batch* B, uint64_t in, uint64_t unit_bytes, uint32_t n_units,
+                                   uint32_t seg_bytes, uint64_t out, uint64_t digests) {
+    const uint64_t m = num_segments(unit_bytes, seg_bytes);
+    crystal_unit* U = units_of(B);
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
+        crystal_unit x;
+        x.in = in + (uint64_t)u * unit_bytes;
+        x.n = unit_bytes;
+        x.out = out + 16ull * u;
+        x.scratch = digests + 16ull * m * u;
+        x.work_begin = m * u;
+        x.out_cap = 16;
+        x.seg_bytes = seg_bytes;
+        x.window = 0;
+        x.kind = CRYSTAL_KIND_MD5_DIRECT;
+        x.mask = 0;
+        x.target = 0;
+        x.seg_base = 0;
+        U[u] = x;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        B->n_direct = n_units;
+        B->n_sliding = 0;
+        B->direct_segments = m * n_units;
+        B->sliding_tiles = 0;
+        B->window_max = 0;
+        B->status = 0;
+        B->sliding_tiles_w20 = 0;
+        B->chunk_segments = 0;
+        B->reserved[0] = B->reserved[1] = 0;
+    }
+}
+
+}  // namespace
+
 }  // namespace crystal
 
 using namespace crystal;
 
 extern "C" {
+
+int crystal_md5_direct_noalloc(const void* d_in, uint64_t unit_bytes, uint32_t n_units, uint32_t segment_bytes,
+                               void* d_digests, void* stream) {
+    if (n_units == 0) return CRYSTAL_OK;
+    if (!d_in || !d_digests || segment_bytes == 0 || (reinterpret_cast<uint64_t>(d_digests) & 3))
+        return CRYSTAL_EINVAL;
+    const uint64_t m = segments_of(unit_bytes, segment_bytes);
+    const uint64_t desc = align_up(crystal_batch_bytes(n_units), 256);
+    // bound every term before multiplying so the size test cannot wrap
+    if (m > CRYSTAL_NOALLOC_SCRATCH_BYTES || n_units > CRYSTAL_NOALLOC_SCRATCH_BYTES) return CRYSTAL_EINVAL;
+    if (desc + 16 * m * (uint64_t)n_units > CRYSTAL_NOALLOC_SCRATCH_BYTES) return CRYSTAL_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CRYSTAL_EDEVICE;
+    std::call_once(g_noalloc_once[dev], [dev] {
+        void* p = nullptr;
+        g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        g_noalloc_addr[dev] = g_noalloc_err[dev] == cudaSuccess ? static_cast<uint8_t*>(p) : nullptr;
+    });
+    if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_addr[dev]) return CRYSTAL_EDEVICE;
+    const Geometry* g = geometry();
+    if (!g) return CRYSTAL_EDEVICE;
+    crystal_batch* B = reinterpret_cast<crystal_batch*>(g_noalloc_addr[dev]);
+    const uint64_t digests = reinterpret_cast<uint64_t>(g_noalloc_addr[dev]) + desc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int threads = 256;
+    const int blocks = (int)((n_units + threads - 1) / threads < 1024 ? (n_units + threads - 1) / threads : 1024);
+    k_noalloc_describe<<<blocks, threads, 0, s>>>(B, reinterpret_cast<uint64_t>(d_in), unit_bytes, n_units,
+                                                   segment_bytes, reinterpret_cast<uint64_t>(d_digests), digests);
+    k_direct_segments<<<g->seg_blocks, kSegThreads, 0, s>>>(B, g_one);
+    k_direct_outer<<<g->outer_blocks, kDigestThreads, 0, s>>>(B, g_one);
+    return launched(3);
+}
 
 int crystal_launch_direct_segments(const crystal_batch* b, void* stream) {
     if (!b) return CRYSTAL_EINVAL;
