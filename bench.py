@@ -61,6 +61,27 @@ def _dist():
     return ws, rank, local
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Each replica hashes its own synthetic data (weak scaling)."""
+    return seed + rank
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """Largest value of x over the ranks (the slowest replica sets the time)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gbs(ws: int, bytes_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's bytes over the slowest rank's time."""
+    return ws * bytes_per_rank * steps / seconds / GB
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -174,17 +195,13 @@ def run_ours(args, ws, rank, local):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x: float) -> float:
+        return max_over_ranks(x, dist, dev)
 
     U, N = args.units, args.unit_bytes
     p = C.params(window_bytes=20, mask=0x1FFF, target=0x1FFF, chunk_segment_bytes=4096)
     out_size = C.sliding_out_bytes(N, args.max_chunks)
-    host = sliding_workload(args.seed + rank, U, N)
+    host = sliding_workload(rank_seed(args.seed, rank), U, N)
     total_bytes = U * N
 
     # ---- value: inputs resident in HBM, kernel chain through the C ABI ----
@@ -230,8 +247,8 @@ def run_ours(args, ws, rank, local):
     launches_value = C.kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev_step]
     win_ms = [a.elapsed_time(b) for a, b in ev]
-    dev_ms = max_over_ranks(float(np.sum(step_ms)))
-    value = ws * total_bytes * args.steps / (dev_ms / 1e3) / GB
+    dev_ms = slowest(float(np.sum(step_ms)))
+    value = aggregate_gbs(ws, total_bytes, args.steps, dev_ms / 1e3)
     assert batch.device_status() == 0
 
     # ---- e2e: job API, pinned host buffers, copies inside the timed region ----
@@ -270,10 +287,10 @@ def run_ours(args, ws, rank, local):
             for s_ns, _, d_ns in e2e_step():
                 lat.append((d_ns - s_ns) / 1e6)
         barrier()
-        e2e_wall = max_over_ranks(time.perf_counter() - t0)
+        e2e_wall = slowest(time.perf_counter() - t0)
         launches = launches_value + C.kernel_launches() - launches1
         clock_info = clocks.stop()
-        e2e_value = ws * total_bytes * args.steps / e2e_wall / GB
+        e2e_value = aggregate_gbs(ws, total_bytes, args.steps, e2e_wall)
     else:
         clock_info = clocks.stop()
         e2e_value, lat, e2e_wall, launches = None, [0.0], None, launches_value
@@ -412,8 +429,8 @@ def main():
     ap.add_argument("--units", type=int, default=256)
     ap.add_argument("--unit-bytes", type=int, default=1 << 20)
     ap.add_argument("--max-chunks", type=int, default=1024)
-    ap.add_argument("--streams", type=int, default=4)
-    ap.add_argument("--batch-jobs", type=int, default=16)
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--batch-jobs", type=int, default=8)
     ap.add_argument("--graphs", type=int, default=1)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--cpu-units", type=int, default=0, help="oracle sample units (0: 4 per core, <= 256)")

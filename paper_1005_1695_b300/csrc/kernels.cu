@@ -81,7 +81,7 @@ __device__ __forceinline__ uint64_t num_segments(uint64_t n, uint32_t S) {
 
 // ---- K1: segment digests of direct units ------------------------------------
 
-__global__ void __launch_bounds__(kSegThreads, 8) k_direct_segments(crystal_batch* B, uint32_t one) {
+__global__ void __launch_bounds__(kSegThreads, 5) k_direct_segments(crystal_batch* B, uint32_t one) {
     const uint32_t nd = B->n_direct;
     const uint64_t total = B->direct_segments;
     const crystal_unit* U = units_of(B);
@@ -203,8 +203,16 @@ __device__ __forceinline__ void stage_tile(uint32_t* sw, const crystal_unit& X, 
 // planner puts them first); W = 0: the remaining tiles, any w in 1..55.
 // The next tile's bytes are copied into the other half of a double buffer
 // while the current tile is hashed.
+// Resident CTAs per SM the window kernel is compiled for (sets its register
+// budget: 65536 / (256 * blocks)).  Eight (32 registers) was measured
+// fastest among 3..8 on B300.
+#ifndef CRYSTAL_WIN_MIN_BLOCKS
+#define CRYSTAL_WIN_MIN_BLOCKS 8
+#endif
+
 template <int W>
-__global__ void __launch_bounds__(kWinThreads) k_sliding_windows(crystal_batch* B, uint32_t one) {
+__global__ void __launch_bounds__(kWinThreads, CRYSTAL_WIN_MIN_BLOCKS) k_sliding_windows(crystal_batch* B,
+                                                                                          uint32_t one) {
     __shared__ __align__(16) uint32_t sw[2][kStageWords];
     const uint32_t ns = B->n_sliding;
     const crystal_unit* U = units_of(B) + B->n_direct;
@@ -394,7 +402,7 @@ __device__ __forceinline__ uint8_t* chunk_digest_area(const crystal_unit& X, uin
 
 // One thread per chunk segment of the whole batch: the unit comes from the
 // starts K4b wrote, the chunk from the unit's segment table.
-__global__ void __launch_bounds__(kDigestThreads, 4) k_chunk_segments(crystal_batch* B, uint32_t one) {
+__global__ void __launch_bounds__(kDigestThreads, 2) k_chunk_segments(crystal_batch* B, uint32_t one) {
     const uint32_t ns = B->n_sliding;
     const crystal_unit* U = units_of(B) + B->n_direct;
     const uint64_t total = B->chunk_segments;

@@ -139,7 +139,7 @@ __device__ __forceinline__ uint32_t ldg32(const uint32_t* p) { return __ldg(p); 
 
 // MD5 of len bytes at p (any alignment) in global memory; the digest words
 // (A, B, C, D) land in st.  Bytes outside [p, p + len) are read only inside
-// 4-byte-aligned words that also hold a byte of the message, and never used.
+// aligned 16-byte blocks that also hold a byte of the message, and never used.
 __device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, uint32_t (&st)[4], uint32_t one) {
     init(st);
     const uint64_t addr = reinterpret_cast<uint64_t>(p);
@@ -168,31 +168,43 @@ __device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, ui
             }
             compress(st, X, one);
         }
-    } else if ((addr & 3) == 0) {
-        const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
-        for (uint64_t blk = 0; blk < full; ++blk, q += 16) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) X[k] = ldg32(q + k);
-            compress(st, X, one);
-        }
     } else {
-        const uint32_t sh = (uint32_t)(addr & 3) * 8;
-        const uint32_t* q = reinterpret_cast<const uint32_t*>(addr & ~uint64_t(3));
-        uint32_t x[17];
+        // Any other alignment: five aligned 16-byte loads cover the block (each
+        // holds at least one byte of it), then the words are shifted into place
+        // by o = addr mod 16 bytes: whole words by a two-level select on o / 4,
+        // the rest by a funnel shift.  The next block's loads are in flight
+        // while this block compresses.
+        const uint32_t o = (uint32_t)(addr & 15);
+        const uint32_t wq = o >> 2;
+        const uint32_t sh = (o & 3) * 8;
+        const uint8_t* q = reinterpret_cast<const uint8_t*>(addr - o);
+        uint4 nx[5];
         if (full) {
 #pragma unroll
-            for (int k = 0; k < 17; ++k) x[k] = ldg32(q + k);
+            for (int v = 0; v < 5; ++v) nx[v] = ldg_stream16(q + 16 * v);
         }
         for (uint64_t blk = 0; blk < full; ++blk) {
+            uint32_t w[20];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) X[k] = __funnelshift_r(x[k], x[k + 1], sh);
-            q += 16;
-            // next block: words 1..17 of it; word 0 is this block's word 16
-            if (blk + 1 < full) {
-                x[0] = x[16];
-#pragma unroll
-                for (int k = 1; k < 17; ++k) x[k] = ldg32(q + k);
+            for (int v = 0; v < 5; ++v) {
+                w[4 * v + 0] = nx[v].x;
+                w[4 * v + 1] = nx[v].y;
+                w[4 * v + 2] = nx[v].z;
+                w[4 * v + 3] = nx[v].w;
             }
+            q += 64;
+            if (blk + 1 < full) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) nx[v] = ldg_stream16(q + 16 * v);
+            }
+            uint32_t y1[19];
+#pragma unroll
+            for (int k = 0; k < 19; ++k) y1[k] = (wq & 1) ? w[k + 1] : w[k];
+            uint32_t y[17];
+#pragma unroll
+            for (int k = 0; k < 17; ++k) y[k] = (wq & 2) ? y1[k + 2] : y1[k];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) X[k] = __funnelshift_r(y[k], y[k + 1], sh);
             compress(st, X, one);
         }
     }
