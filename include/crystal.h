@@ -258,8 +258,11 @@ typedef struct crystal_batch {
     /* crystal_unit units[n_direct + n_sliding] follow */
 } crystal_batch;
 
-/* Offsets processed by one window tile of the sliding kernel. */
-#define CRYSTAL_SLIDING_TILE 1024u
+/* Offsets processed by one window tile of the sliding kernel (256 threads x
+ * 8 windows).  The planner counts a sliding unit's work in these tiles. */
+#ifndef CRYSTAL_SLIDING_TILE
+#define CRYSTAL_SLIDING_TILE 2048u
+#endif
 
 /* Scratch bytes one unit needs: 16 * ceil(n/S) for direct; for sliding the
  * per-chunk segment table and digests for as many chunks as out_size holds.

@@ -37,7 +37,6 @@ CRYSTAL_FLAG_NO_OVERLAP = 2
 CRYSTAL_FLAG_NO_BATCH = 4
 CRYSTAL_FLAG_GRAPHS = 8
 
-CRYSTAL_SLIDING_TILE = 1024
 
 
 class crystal_config(ctypes.Structure):

@@ -34,12 +34,13 @@ std::atomic<uint64_t> g_kernel_launches{0};
 namespace {
 
 constexpr int kTile = CRYSTAL_SLIDING_TILE;  // window offsets per tile
-constexpr int kWinThreads = 256;             // 8 warps x 4 windows x 32 lanes = 1024
+constexpr int kWinThreads = 256;             // 8 warps x kWinPerThread windows x 32 lanes
 constexpr int kWinPerThread = kTile / kWinThreads;
-static_assert(kWinPerThread == 4, "window tile layout assumes 4 windows per thread");
-// Staged bytes per tile: 1024 offsets + up to 54 halo bytes + 15 alignment bytes,
-// rounded to whole 16-byte vectors, plus room for the last window's word reads.
-constexpr int kStageWords = 284;
+static_assert(kWinPerThread * kWinThreads == kTile && kWinPerThread <= 32, "tile layout");
+// Staged words per tile: the tile's offsets + up to 54 halo bytes + 15 alignment
+// bytes, rounded up to whole 16-byte vectors, plus room for the last window's
+// word reads.
+constexpr int kStageWords = 4 * ((kTile + 69 + 15) / 16) + 4;
 
 constexpr int kSegThreads = 128;
 constexpr int kChunkThreads = 512;
@@ -162,7 +163,7 @@ __device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t de
     uint32_t A[kWinPerThread];
 #pragma unroll
     for (int r = 0; r < kWinPerThread; ++r) {
-        const uint32_t rel = warp * 128 + r * 32 + lane;
+        const uint32_t rel = warp * (32 * kWinPerThread) + r * 32 + lane;
         uint32_t X[16];
         window_block<W>(sw, rel + delta, w, X);
         A[r] = md5::first_word_one_block(X, one);
@@ -170,7 +171,7 @@ __device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t de
     uint32_t mine = 0;
 #pragma unroll
     for (int r = 0; r < kWinPerThread; ++r) {
-        const uint32_t rel = warp * 128 + r * 32 + lane;
+        const uint32_t rel = warp * (32 * kWinPerThread) + r * 32 + lane;
         const bool hit = (rel + w <= lim) && ((A[r] & mask) == target);
         const uint32_t word = __ballot_sync(0xffffffffu, hit);
         if (lane == (uint32_t)r) mine = word;
@@ -185,6 +186,22 @@ __device__ __forceinline__ void cp_async16(uint32_t* smem_dst, uint64_t gmem_src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Owner of tile g >= the tiles of unit u: a short forward walk (the next
+// tile of a CTA is usually in the same unit or the next one), else a binary
+// search over the rest.
+__device__ __forceinline__ uint32_t next_owner(const crystal_unit* U, uint32_t cnt, uint32_t u, uint64_t g) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        if (u + 1 < cnt && U[u + 1].work_begin <= g) ++u;
+    }
+    if (u + 1 < cnt && U[u + 1].work_begin <= g) u = owner_of(U, cnt, g);
+    return u;
+}
+
+#ifndef CRYSTAL_WIN_FAST_OWNER
+#define CRYSTAL_WIN_FAST_OWNER 1
+#endif
 
 // Issue the copies of one tile's bytes [base, min(n, base + kTile + w - 1))
 // from their 16-byte aligned block on into smem; vectors past the unit's end
@@ -204,8 +221,8 @@ __device__ __forceinline__ void stage_tile(uint32_t* sw, const crystal_unit& X, 
 // The next tile's bytes are copied into the other half of a double buffer
 // while the current tile is hashed.
 // Resident CTAs per SM the window kernel is compiled for (sets its register
-// budget: 65536 / (256 * blocks)).  Eight (32 registers) was measured
-// fastest among 3..8 on B300.
+// budget: 65536 / (256 * blocks)).  Eight (32 registers) was measured fastest
+// on B300 with 2048-offset tiles (8 windows per thread).
 #ifndef CRYSTAL_WIN_MIN_BLOCKS
 #define CRYSTAL_WIN_MIN_BLOCKS 8
 #endif
@@ -228,7 +245,11 @@ __global__ void __launch_bounds__(kWinThreads, CRYSTAL_WIN_MIN_BLOCKS) k_sliding
         const uint64_t tn = t + gridDim.x;
         uint32_t un = 0;
         if (tn < hi) {
+#if CRYSTAL_WIN_FAST_OWNER
+            un = next_owner(U, ns, u, tn);
+#else
             un = owner_of(U, ns, tn);
+#endif
             stage_tile(sw[buf ^ 1], U[un], (tn - U[un].work_begin) * (uint64_t)kTile);
         }
         cp_async_commit();
@@ -243,7 +264,7 @@ __global__ void __launch_bounds__(kWinThreads, CRYSTAL_WIN_MIN_BLOCKS) k_sliding
         const uint32_t mine = tile_windows<W>(sw[buf], delta, lim, w, X.mask, X.target, one);
         const uint32_t lane = threadIdx.x & 31;
         if (lane < (uint32_t)kWinPerThread) {
-            const uint64_t word = (base >> 5) + (threadIdx.x >> 5) * 4 + lane;
+            const uint64_t word = (base >> 5) + (threadIdx.x >> 5) * kWinPerThread + lane;
             if (word < ((X.n + 31) >> 5)) reinterpret_cast<uint32_t*>(X.out + 8)[word] = mine;
         }
         __syncthreads();

@@ -149,13 +149,27 @@ def test_batch_plan_prefixes_and_validation(C):
     D, S = C.CRYSTAL_KIND_MD5_DIRECT, C.CRYSTAL_KIND_MD5_SLIDING
     units = [_unit(D, 0), _unit(D, 4096), _unit(D, 4097), _unit(D, 100, seg_bytes=7),
              _unit(S, 0), _unit(S, 1024), _unit(S, 1025), _unit(S, 10, window=55)]
+    tile = int(re.search(r"#define CRYSTAL_SLIDING_TILE (\d+)u", open(HEADER).read()).group(1))
     st, buf, rec = _plan(C, units, 4, 4)
     assert st == 0
-    assert rec["work_begin"].tolist() == [0, 1, 2, 4, 0, 0, 1, 3]
+    sl_tiles = [-(-n // tile) for n in (0, 1024, 1025, 10)]
+    sl_begin = [int(v) for v in np.cumsum([0] + sl_tiles[:-1])]
+    assert rec["work_begin"].tolist() == [0, 1, 2, 4] + sl_begin
     hdr = buf[:64]
     assert hdr[:8].view("<u4").tolist() == [4, 4]
-    assert hdr[8:24].view("<u8").tolist() == [4 + 15, 4]
+    assert hdr[8:24].view("<u8").tolist() == [4 + 15, sum(sl_tiles)]
     assert hdr[24:28].view("<u4")[0] == 55
+    assert hdr[32:40].view("<u8")[0] == sum(sl_tiles[:3])  # tiles of the w = 20 units
+
+
+def test_batch_plan_puts_w20_units_first(C):
+    D, S = C.CRYSTAL_KIND_MD5_DIRECT, C.CRYSTAL_KIND_MD5_SLIDING
+    units = [_unit(S, 5000, window=7, out=1 << 21), _unit(S, 3000, out=2 << 21), _unit(S, 100, window=33, out=3 << 21),
+             _unit(S, 9000, out=4 << 21)]
+    st, buf, rec = _plan(C, units, 0, 4)
+    assert st == 0
+    assert rec["window"].tolist() == [20, 20, 7, 33]
+    assert rec["out"].tolist() == [2 << 21, 4 << 21, 1 << 21, 3 << 21]  # records move whole
     bad = [
         [_unit(S, 10)] + units[1:4],               # wrong kind order
         [_unit(D, 10, seg_bytes=0)],               # zero segment
