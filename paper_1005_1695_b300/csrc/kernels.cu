@@ -168,7 +168,9 @@ __device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t de
         window_block<W>(sw, rel + delta, w, X);
         A[r] = md5::first_word_one_block(X, one);
     }
-    uint32_t mine = 0;
+    // ballots only after every window of the thread is hashed: a ballot per
+    // window was measured 9% slower (each one is a warp-wide sync point)
+    uint32_t mine = 0;  // lane r ends up holding bitmap word r of this warp
 #pragma unroll
     for (int r = 0; r < kWinPerThread; ++r) {
         const uint32_t rel = warp * (32 * kWinPerThread) + r * 32 + lane;
