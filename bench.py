@@ -53,6 +53,22 @@ OPS_PER_WINDOW_W20 = 61 * 4 + 19 + 3
 SM_COUNT_B300 = 148
 INT_LANES_PER_SM = 128  # 4 schedulers x one 32-lane instruction per clock
 
+# DRAM bytes (read + write) of the window kernel per 1 MiB sliding unit, from one
+# ncu capture of 160 units (traffic grows with the units processed), valid only
+# for the kernel sources it was taken on (checked by hash; otherwise null).
+WINDOW_TRAFFIC_PER_UNIT = (167.846656e6 + 14.420736e6) / 160
+WINDOW_TRAFFIC_SOURCES = "14be97120abb608f"
+
+
+def _kernel_sources_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "md5_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1005_1695_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -322,6 +338,9 @@ def run_ours(args, ws, rank, local):
     win_avg_s = float(np.mean(win_ms)) / 1e3
     achieved = windows * OPS_PER_WINDOW_W20 / win_avg_s / 1e12
     peaks = _peaks()
+    traffic = None
+    if _kernel_sources_hash() == WINDOW_TRAFFIC_SOURCES and N == 1 << 20:
+        traffic = round(WINDOW_TRAFFIC_PER_UNIT * U)
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak = SM_COUNT_B300 * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
     alu_bound_gbs = peak * 1e12 / OPS_PER_WINDOW_W20  # windows/s = bytes/s
@@ -340,7 +359,7 @@ def run_ours(args, ws, rank, local):
                    "graphs": bool(args.graphs)},
         "roofline": {"bound": "alu", "kernel": "k_sliding_windows", "achieved": round(achieved, 3),
                      "peak": round(peak, 3), "unit": "Tops/s (int32)", "frac": round(achieved / peak, 4),
-                     "traffic": None,
+                     "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
                      "ops_per_window": OPS_PER_WINDOW_W20, "windows_per_launch": windows,
                      "avg_launch_ms": round(win_avg_s * 1e3, 4),
                      "peak_basis": f"{SM_COUNT_B300} SMs x {INT_LANES_PER_SM} int32 lanes/clk x {sm_max:.0f} MHz"},
