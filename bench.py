@@ -150,6 +150,45 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measure_link(torch, dev, total: int, n_streams: int = 8, chunk: int = 8 << 20, reps: int = 3) -> dict:
+    """Pinned host <-> device copy bandwidth: one stream copying ``total`` bytes
+    at once, and ``n_streams`` streams copying ``chunk``-byte pieces
+    concurrently (which can use several copy engines).  Best of ``reps``."""
+    pinned = torch.empty(total, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(total, dtype=torch.uint8, device=dev)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
+
+    def timed(h2d: bool, multi: bool) -> float:
+        best = 0.0
+        for _ in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            cur = torch.cuda.current_stream()
+            a.record(cur)
+            if not multi:
+                (dbuf.copy_(pinned, non_blocking=True) if h2d else pinned.copy_(dbuf, non_blocking=True))
+            else:
+                for s in streams:
+                    s.wait_event(a)
+                for i, off in enumerate(range(0, total, chunk)):
+                    with torch.cuda.stream(streams[i % n_streams]):
+                        d, h = dbuf[off:off + chunk], pinned[off:off + chunk]
+                        (d.copy_(h, non_blocking=True) if h2d else h.copy_(d, non_blocking=True))
+                for s in streams:
+                    cur.wait_stream(s)
+            b.record(cur)
+            torch.cuda.synchronize()
+            best = max(best, total / (a.elapsed_time(b) / 1e3) / GB)
+        return best
+
+    out = {"h2d_single_gbs": timed(True, False), "h2d_multi_gbs": timed(True, True),
+           "d2h_single_gbs": timed(False, False), "d2h_multi_gbs": timed(False, True)}
+    out = {k: round(v, 2) for k, v in out.items()}
+    out["how"] = f"torch pinned copies of {total >> 20} MiB: one stream, and {n_streams} streams x {chunk >> 20} MiB"
+    del pinned, dbuf
+    return out
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -307,31 +346,22 @@ def run_ours(args, ws, rank, local):
         launches = launches_value + C.kernel_launches() - launches1
         clock_info = clocks.stop()
         e2e_value = aggregate_gbs(ws, total_bytes, args.steps, e2e_wall)
+        # the same job shapes with the dummy kernel (copies only): the transfer ceiling
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            C.check(ctx.submit_many(tasks, C.CRYSTAL_KIND_NOP, p), "submit_many")
+            for t in tasks:
+                assert t.wait(60_000_000_000) == C.CRYSTAL_OK
+        copy_only = aggregate_gbs(ws, total_bytes, args.steps, slowest(time.perf_counter() - t1))
     else:
         clock_info = clocks.stop()
-        e2e_value, lat, e2e_wall, launches = None, [0.0], None, launches_value
+        e2e_value, lat, e2e_wall, launches, copy_only = None, [0.0], None, launches_value, None
         tasks, ctx = [], None
 
     # ---- host link (pinned copies) measured on this GPU ----
-    pinned = torch.empty(total_bytes, dtype=torch.uint8).pin_memory()
-    dbuf = torch.empty(total_bytes, dtype=torch.uint8, device=dev)
-    for _ in range(2):
-        dbuf.copy_(pinned, non_blocking=True)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(3):
-        dbuf.copy_(pinned, non_blocking=True)
-    b.record()
-    torch.cuda.synchronize()
-    h2d = 3 * total_bytes / (a.elapsed_time(b) / 1e3) / GB
-    a.record()
-    for _ in range(3):
-        pinned.copy_(dbuf, non_blocking=True)
-    b.record()
-    torch.cuda.synchronize()
-    d2h = 3 * total_bytes / (a.elapsed_time(b) / 1e3) / GB
-    del pinned, dbuf
+    link = measure_link(torch, dev, total_bytes)
+    h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
+    d2h = max(link["d2h_single_gbs"], link["d2h_multi_gbs"])
 
     # ---- roofline of the window kernel ----
     windows = U * (N - 20 + 1)
@@ -368,8 +398,12 @@ def run_ours(args, ws, rank, local):
             "d2h_bytes_per_step": U * out_size * ws, "ms_per_step": round(e2e_wall * 1e3 / args.steps, 3),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                            "p99": round(float(np.percentile(lat, 99)), 3)},
-            "roofline_gbs": round(e2e_bound, 2), "frac": round(e2e_value / ws / e2e_bound, 4)},
-        "host_link": {"h2d_gbs": round(h2d, 2), "d2h_gbs": round(d2h, 2), "how": "torch pinned copy, 256 MiB"},
+            "roofline_gbs": round(e2e_bound, 2), "frac": round(e2e_value / ws / e2e_bound, 4),
+            "roofline_basis": "min(best measured H2D, best measured D2H scaled to the output bytes, "
+                              "issue-rate ALU bound of the window kernel)",
+            "copy_only_gbs": round(copy_only, 3),
+            "copy_only_note": "the same jobs with the dummy kernel: copy-in and copy-out only"},
+        "host_link": link,
         "clocks": clock_info,
         "gpu_launches": int(launches),
         "gpu_launches_split": {"value_region": int(launches_value), "e2e_region": int(launches - launches_value)},
@@ -439,6 +473,79 @@ def run_direct_value(args, ws, rank, local):
     print(json.dumps(line))
 
 
+def run_stream_modes(args, local, kind, unit_bytes, n_units, modes, subset=None):
+    """One stream of jobs per mode through the job API; digests of every mode
+    must agree.  Prints one line (these workloads are not the headline)."""
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    torch.cuda.set_device(local)
+    C.load()
+    p = C.params(segment_bytes=4096)
+    out_size = 16 if kind == C.CRYSTAL_KIND_MD5_DIRECT else C.sliding_out_bytes(unit_bytes, args.max_chunks)
+
+    def unit(i):
+        return inputs.uniform_unit(args.seed, i, unit_bytes)
+
+    results, outs = {}, {}
+    for mode in modes:
+        n = n_units if not subset or mode not in subset else min(n_units, subset[mode])
+        runs = []
+        for _ in range(max(1, args.steps)):
+            r = S.run_stream(mode, unit, n, unit_bytes, kind, p, out_size, streams=args.streams,
+                             batch_jobs=args.batch_jobs, depth=args.depth, device=local,
+                             keep=range(0, n, max(1, n // 32)))
+            assert all(st == C.CRYSTAL_OK for st in r.statuses), (mode, set(r.statuses))
+            runs.append(r)
+        best = sorted(runs, key=lambda r: r.seconds)[len(runs) // 2]  # median run
+        results[mode] = {"units": n, "GB_per_s": round(best.gbs, 3), "s": round(best.seconds, 4),
+                         "latency_ms": {"p50": round(best.latency(50), 3), "p99": round(best.latency(99), 3)}}
+        outs[mode] = best.outputs
+    ref = outs[modes[0]]
+    for mode in modes[1:]:
+        for i, o in outs[mode].items():
+            if i in ref:
+                assert o == ref[i], f"mode {mode} differs from {modes[0]} on unit {i}"
+    return results
+
+
+def run_plain(args, ws, rank, local):
+    """64 units of 64 KiB, direct hashing, 4 KiB segments: the plain
+    single-stream form against the pooled, overlapped, batched form."""
+    from paper_1005_1695_b300 import crystal as C
+
+    U, N = args.units or 64, args.unit_bytes or 65536
+    res = run_stream_modes(args, local, C.CRYSTAL_KIND_MD5_DIRECT, N, U, ["plain", "no_overlap", "pooled"])
+    print(json.dumps({"metric": "end-to-end hashed GB/s through the job API", "unit": "GB/s",
+                      "workload": f"plain direct hashing, {U} units x {N >> 10} KiB, S=4 KiB",
+                      "modes": res, "steps": args.steps, "data": "synthetic"}))
+
+
+def run_pipelined(args, ws, rank, local):
+    """Direct hashing of a long stream of 4 MiB units with pooled buffers and
+    overlap, against no-overlap and per-job allocation."""
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+
+    U, N = args.units or 4096, args.unit_bytes or (4 << 20)
+    res = run_stream_modes(args, local, C.CRYSTAL_KIND_MD5_DIRECT, N, U,
+                           ["pooled", "no_overlap", "pooled_staged", "per_job_malloc"],
+                           subset={"per_job_malloc": args.malloc_units, "pooled_staged": args.malloc_units})
+    link = measure_link(torch, torch.device("cuda", local), 256 << 20)
+    h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
+    for m in res.values():
+        m["frac_of_link"] = round(m["GB_per_s"] / h2d, 4)
+    print(json.dumps({"metric": "end-to-end hashed GB/s through the job API", "unit": "GB/s",
+                      "workload": f"pipelined direct hashing, {U} units x {N >> 20} MiB, S=4 KiB, "
+                                  f"{args.streams} streams, {args.batch_jobs} jobs per batch",
+                      "host_link": link, "modes": res, "steps": args.steps,
+                      "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -455,7 +562,9 @@ def main():
     ap.add_argument("--cpu-units", type=int, default=0, help="oracle sample units (0: 4 per core, <= 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="value,e2e", help="value (device-resident) and/or e2e (job API)")
-    ap.add_argument("--workload", default="sliding", choices=["sliding", "direct"])
+    ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined"])
+    ap.add_argument("--depth", type=int, default=24, help="jobs in flight for staged / per-job-allocation modes")
+    ap.add_argument("--malloc-units", type=int, default=512, help="units for the per-job-allocation modes")
     ap.add_argument("--segment-bytes", type=int, default=4096)
     args = ap.parse_args()
     ws, rank, local = _dist()
@@ -487,8 +596,11 @@ def main():
         print(json.dumps(line))
         return
 
-    if args.workload == "direct":
-        run_direct_value(args, ws, rank, local)
+    if args.workload in ("direct", "plain", "pipelined"):
+        if args.workload in ("plain", "pipelined") and args.units == 256 and args.unit_bytes == 1 << 20:
+            args.units, args.unit_bytes = 0, 0  # the workload's own sizes
+        {"direct": run_direct_value, "plain": run_plain, "pipelined": run_pipelined}[args.workload](
+            args, ws, rank, local)
         return
     out = run_ours(args, ws, rank, local)
     if rank == 0:

@@ -1,0 +1,149 @@
+"""Job-stream drivers over the C-ABI job runtime.
+
+These run a stream of data units through ``crystal_task_*`` the way an
+application of the paper's framework does (Section 2.2: a steady stream of
+data units, one job each; Section 5.2: a stream of jobs hashed by StoreGPU),
+in the forms the paper compares (Section 5.2, Figure 7):
+
+* ``pooled``          buffers from the pool allocated at init, several
+                      streams, outstanding jobs batched per launch; the data
+                      are produced straight into the jobs' pinned buffers
+                      (Section 2.1's advice) before the stream starts.
+* ``pooled_staged``   the same runtime, but a ring of ``depth`` jobs is
+                      refilled from pageable memory by the application thread
+                      (one host copy per job inside the timed region).
+* ``no_overlap``      pooled buffers, one stream, one job at a time: copy-in,
+                      kernel and copy-out of a job never overlap another job.
+* ``per_job_malloc``  every job allocates its pinned and device buffers when
+                      it is created and frees them when released (the
+                      allocation the pool removes), data staged from pageable
+                      memory; ``depth`` jobs in flight.
+* ``plain``           ``per_job_malloc`` with one stream and one job at a time:
+                      allocate, copy in, hash, copy out, free — job by job.
+
+All hashing runs in ``libcrystal.so``; this module only creates, fills,
+submits and waits on jobs and records host clock stamps.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import crystal as C
+
+MODES = ("pooled", "pooled_staged", "no_overlap", "per_job_malloc", "plain")
+
+_FLAGS = {
+    "pooled": 0,
+    "pooled_staged": 0,
+    "no_overlap": C.CRYSTAL_FLAG_NO_OVERLAP | C.CRYSTAL_FLAG_NO_BATCH,
+    "per_job_malloc": C.CRYSTAL_FLAG_NO_POOL,
+    "plain": C.CRYSTAL_FLAG_NO_POOL | C.CRYSTAL_FLAG_NO_OVERLAP | C.CRYSTAL_FLAG_NO_BATCH,
+}
+
+
+@dataclass
+class StreamResult:
+    mode: str
+    units: int
+    bytes: int
+    seconds: float
+    latencies_ms: List[float]
+    outputs: Dict[int, bytes] = field(default_factory=dict)
+    statuses: List[int] = field(default_factory=list)
+
+    @property
+    def gbs(self) -> float:
+        return self.bytes / self.seconds / 1e9
+
+    def latency(self, q: float) -> float:
+        return float(np.percentile(self.latencies_ms, q)) if self.latencies_ms else 0.0
+
+
+def _used(kind: int, n: int, out: np.ndarray) -> int:
+    if kind == C.CRYSTAL_KIND_MD5_DIRECT:
+        return 16
+    words = (n + 31) // 32
+    n_chunks = int(out[0:4].view(np.uint32)[0])
+    flags = int(out[4:8].view(np.uint32)[0])
+    return 8 + 4 * words + (0 if flags & 1 else 20 * n_chunks)
+
+
+def run_stream(mode: str, unit: Callable[[int], np.ndarray], n_units: int, unit_bytes: int, kind: int,
+               p: C.crystal_hash_params, out_size: int, *, streams: int = 8, batch_jobs: int = 8,
+               depth: int = 24, graphs: bool = True, device: int = 0, keep: Sequence[int] = (),
+               device_pool_bytes: Optional[int] = None, host_pool_bytes: Optional[int] = None) -> StreamResult:
+    """Hash ``n_units`` units (``unit(i)`` returns unit i's bytes) in ``mode``.
+
+    Returns wall time of the stream (first submit to last completion seen by
+    the application), per-job latencies (submit to completion, master-thread
+    stamps) and the used output bytes of the units listed in ``keep``."""
+    if mode not in MODES:
+        raise ValueError(mode)
+    flags = _FLAGS[mode] | (C.CRYSTAL_FLAG_GRAPHS if graphs and mode in ("pooled", "pooled_staged") else 0)
+    keep = set(keep)
+    scratch = C.scratch_bytes(kind, unit_bytes, out_size, p)
+    per_job_dev = unit_bytes + out_size + scratch + 3 * 256
+    resident = mode in ("pooled", "no_overlap")
+    ring = n_units if resident else (1 if mode == "plain" else min(depth, n_units))
+    dev_pool = device_pool_bytes or (ring * per_job_dev + (64 << 20))
+    host_pool = host_pool_bytes or (ring * (unit_bytes + out_size + 512) + (16 << 20))
+    ctx = C.Context(max_in_bytes=unit_bytes, max_out_bytes=out_size, device_pool_bytes=dev_pool,
+                    host_pool_bytes=host_pool, n_streams=streams, device=device, flags=flags,
+                    max_batch_jobs=batch_jobs, max_batch_bytes=batch_jobs * max(unit_bytes, 1))
+    res = StreamResult(mode, n_units, n_units * unit_bytes, 0.0, [])
+    try:
+        if resident:
+            tasks = [ctx.task_create(unit_bytes, out_size) for _ in range(n_units)]
+            for i, t in enumerate(tasks):
+                t.h_in[:] = unit(i)  # produced into the job's pinned buffer, before the stream
+            t0 = time.perf_counter()
+            C.check(ctx.submit_many(tasks, kind, p), "crystal_task_submit_many")
+            for t in tasks:
+                res.statuses.append(t.wait(600_000_000_000))
+            res.seconds = time.perf_counter() - t0
+            for i, t in enumerate(tasks):
+                s, _, d = t.timing()
+                res.latencies_ms.append((d - s) / 1e6)
+                if i in keep:
+                    res.outputs[i] = t.h_out[:_used(kind, unit_bytes, t.h_out)].tobytes()
+                t.release()
+        else:
+            src = [unit(i) for i in range(n_units)]  # pageable application memory
+            pool = None
+            if mode == "pooled_staged":
+                pool = [ctx.task_create(unit_bytes, out_size) for _ in range(ring)]
+            inflight = []  # (unit index, task)
+
+            def retire():
+                i, t = inflight.pop(0)
+                res.statuses.append(t.wait(600_000_000_000))
+                s, _, d = t.timing()
+                res.latencies_ms.append((d - s) / 1e6)
+                if i in keep:
+                    res.outputs[i] = t.h_out[:_used(kind, unit_bytes, t.h_out)].tobytes()
+                if pool is None:
+                    t.release()
+                else:
+                    pool.append(t)
+
+            t0 = time.perf_counter()
+            for i in range(n_units):
+                if len(inflight) >= ring:
+                    retire()
+                t = pool.pop(0) if pool is not None else ctx.task_create(unit_bytes, out_size)
+                t.h_in[:] = src[i]
+                C.check(t.submit(kind, p), "crystal_task_submit")
+                inflight.append((i, t))
+            while inflight:
+                retire()
+            res.seconds = time.perf_counter() - t0
+            if pool is not None:
+                for t in pool:
+                    t.release()
+    finally:
+        ctx.shutdown()
+    return res
