@@ -546,6 +546,58 @@ def run_pipelined(args, ws, rank, local):
                       "data": "synthetic"}))
 
 
+def run_serving(args, ws, rank, local):
+    """Open-loop Poisson request streams at several rates through crystal_serve:
+    lognormal sizes (median 256 KiB, sigma 1.5, cap 64 MiB), 70/30
+    direct/sliding, admission against an 8 GiB device pool."""
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    torch.cuda.set_device(local)
+    C.load()
+    src = inputs.arena(args.seed, args.arena_bytes, out=C.page_aligned(args.arena_bytes))
+    rates = [float(r) for r in args.rates.split(",")]
+    pool = args.pool_bytes
+    ctx = C.Context(max_in_bytes=64 << 20, max_out_bytes=C.sliding_out_bytes(64 << 20, 4 * 8192 + 64),
+                    device_pool_bytes=pool, host_pool_bytes=pool, n_streams=args.streams, device=local,
+                    max_batch_jobs=args.batch_jobs, max_batch_bytes=32 << 20, flags=C.CRYSTAL_FLAG_GRAPHS)
+    out = {}
+    pinned = args.source == "pinned"
+    if pinned:
+        C.host_register(src)
+    try:
+        for rate in rates:
+            n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
+            req, _ = S.make_trace(args.seed, n, rate, src.nbytes)
+            st, res, wall = ctx.serve(src, req, copy_threads=args.copy_threads, source_pinned=pinned)
+            ok = res["status"] == 0
+            lat = S.latency_ms(req, res)[ok]
+            wait = (res["admit_ns"].astype(np.float64) - req["arrival_ns"].astype(np.float64))[ok] / 1e6
+            total = int(req["size"][ok].sum())
+            span = float(req["arrival_ns"][-1]) / 1e9
+            out[f"{int(rate)}"] = {
+                "requests": n, "failed": int((~ok).sum()), "GB": round(total / 1e9, 3),
+                "offered_GB_per_s": round(float(req["size"].sum()) / max(span, 1e-9) / 1e9, 3),
+                "GB_per_s": round(total / (wall / 1e9) / 1e9, 3),
+                "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                               "p99": round(float(np.percentile(lat, 99)), 3)},
+                "admission_wait_ms_p99": round(float(np.percentile(wait, 99)), 3)}
+    finally:
+        ctx.shutdown()
+        if pinned:
+            C.host_unregister(src)
+    print(json.dumps({"metric": "served hashed GB/s and p50/p99 request latency", "unit": "GB/s",
+                      "source": "page-locked, read in place" if pinned else "pageable, staged by copy threads",
+                      "workload": "open-loop Poisson requests, lognormal sizes (median 256 KiB, sigma 1.5, "
+                                  f"cap 64 MiB), 70/30 direct/sliding, {pool >> 30} GiB device pool, "
+                                  f"{args.streams} streams, {args.batch_jobs} jobs per batch, "
+                                  f"{args.copy_threads} staging threads",
+                      "rates_per_s": out, "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,7 +614,15 @@ def main():
     ap.add_argument("--cpu-units", type=int, default=0, help="oracle sample units (0: 4 per core, <= 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="value,e2e", help="value (device-resident) and/or e2e (job API)")
-    ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined"])
+    ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined", "serving"])
+    ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000")
+    ap.add_argument("--seconds", type=float, default=2.0)
+    ap.add_argument("--min-requests", type=int, default=2000)
+    ap.add_argument("--max-requests", type=int, default=20000)
+    ap.add_argument("--arena-bytes", type=int, default=1 << 30)
+    ap.add_argument("--pool-bytes", type=int, default=8 << 30)
+    ap.add_argument("--copy-threads", type=int, default=8)
+    ap.add_argument("--source", default="pinned", choices=["pinned", "pageable"])
     ap.add_argument("--depth", type=int, default=24, help="jobs in flight for staged / per-job-allocation modes")
     ap.add_argument("--malloc-units", type=int, default=512, help="units for the per-job-allocation modes")
     ap.add_argument("--segment-bytes", type=int, default=4096)
@@ -596,6 +656,9 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.workload == "serving":
+        run_serving(args, ws, rank, local)
+        return
     if args.workload in ("direct", "plain", "pipelined"):
         if args.workload in ("plain", "pipelined") and args.units == 256 and args.unit_bytes == 1 << 20:
             args.units, args.unit_bytes = 0, 0  # the workload's own sizes

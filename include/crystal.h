@@ -128,6 +128,34 @@ int crystal_shutdown(crystal_ctx* ctx);
  * Errors: EINVAL, EAGAIN (pool full now), ENOMEM (unpooled mode), ESHUTDOWN. */
 int crystal_task_create(crystal_ctx* ctx, uint64_t in_size, uint64_t out_size, crystal_task** out);
 
+/* crystal_task_create with two extensions.
+ *  - scratch_bytes of device scratch are reserved for the job (see
+ *    crystal_scratch_bytes): a later submit whose kind needs no more than that
+ *    takes no device memory, so a job that was created can always be
+ *    submitted.  This is how a serving loop admits a request against the
+ *    device pool (admission by pool memory).  Returned at release.
+ *  - flags CRYSTAL_TASK_EXTERNAL_INPUT: the job gets no pinned input buffer of
+ *    its own (crystal_task_host_in returns NULL); its input must be bound
+ *    with crystal_task_bind_input before each submit. */
+#define CRYSTAL_TASK_EXTERNAL_INPUT 1u
+int crystal_task_create_ex(crystal_ctx* ctx, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes,
+                           uint32_t flags, crystal_task** out);
+
+/* Bind caller memory as the job's input for the next submits (Figure 2's
+ * h_input pointed at application memory): the copy-in reads size bytes from
+ * host (size <= the job's input capacity), which must stay valid and
+ * unchanged until the job completes.  For the copy to run asynchronously
+ * the memory must be page-locked (crystal_host_register, or cudaHostAlloc);
+ * Section 2.1: data in pinned memory from the beginning saves the driver's
+ * extra copy.  host = NULL returns to the job's own input buffer (EINVAL for a
+ * job created with CRYSTAL_TASK_EXTERNAL_INPUT).  Not while the job runs. */
+int crystal_task_bind_input(crystal_task* task, const void* host, uint64_t size);
+
+/* Page-lock (and unlock) caller host memory for the GPU's DMA engines
+ * (cudaHostRegister / cudaHostUnregister).  EDEVICE on failure. */
+int crystal_host_register(void* host, uint64_t bytes);
+int crystal_host_unregister(void* host);
+
 /* h_input / h_output of Figure 2.  The application writes the input before
  * submit and reads the output after completion until release; it must not
  * touch either while the job runs.  NULL for a NULL task. */
@@ -303,6 +331,56 @@ int crystal_launch_sliding_windows(const crystal_batch* batch_dev, void* stream)
 int crystal_launch_sliding_chunks(const crystal_batch* batch_dev, void* stream);
 int crystal_launch_sliding_digests(const crystal_batch* batch_dev, void* stream);
 int crystal_launch_batch(const crystal_batch* batch_dev, void* stream);
+
+/* ---- serving loop --------------------------------------------------------
+ * crystal_serve plays an open-loop stream of requests against a context
+ * (stream-processing applications, Section 2.2: data units arrive
+ * continuously and each needs low latency).  Request i arrives arrival_ns
+ * after the call starts; requests are admitted in arrival order as soon as
+ * the context's pools can hold the job's buffers and scratch
+ * (crystal_task_create_ex); copy threads stage the request's bytes from
+ * `source` into the job's pinned input (or, with CRYSTAL_SERVE_SOURCE_PINNED,
+ * bind the job's input to them) and submit it; the master thread
+ * batches whatever is outstanding (continuous batching).  On completion the
+ * used output bytes of a request with capture_offset != UINT64_MAX are copied
+ * to capture + capture_offset (if they fit), and the job is released.  A
+ * request that can never fit the pools fails with CRYSTAL_ENOMEM.
+ * Returns CRYSTAL_OK when every request finished with OK or EOVERFLOW,
+ * otherwise the last other error; per-request results are in `res`;
+ * *wall_ns receives the time of the last completion. */
+typedef struct crystal_request {
+    uint64_t arrival_ns;     /* arrival time after the start of the call (non-decreasing) */
+    uint64_t src_offset;     /* the request's bytes are source[src_offset, src_offset + size) */
+    uint64_t size;
+    uint64_t out_size;       /* output bytes reserved for the job */
+    uint64_t capture_offset; /* UINT64_MAX: output not copied out */
+    int32_t kind;            /* CRYSTAL_KIND_* */
+    uint32_t reserved;
+} crystal_request;
+
+typedef struct crystal_request_result {
+    int32_t status;
+    uint32_t reserved;
+    uint64_t admit_ns;   /* buffers obtained (after any wait for pool room) */
+    uint64_t submit_ns;  /* bytes staged, job submitted */
+    uint64_t done_ns;    /* completion seen by the master thread */
+    uint64_t used_bytes; /* output bytes that carry results */
+} crystal_request_result;
+
+#define CRYSTAL_SERVE_SOURCE_PINNED 1u
+typedef struct crystal_serve_config {
+    uint32_t copy_threads;                      /* staging threads; default 4 */
+    uint32_t flags;                             /* CRYSTAL_SERVE_SOURCE_PINNED: `source` is page-locked;
+                                                   jobs read their input from it directly
+                                                   (crystal_task_bind_input) and nothing is staged */
+    const crystal_hash_params* direct_params;   /* NULL: defaults */
+    const crystal_hash_params* sliding_params;  /* NULL: defaults */
+    void* capture;                              /* host buffer for captured outputs, or NULL */
+    uint64_t capture_bytes;
+} crystal_serve_config;
+
+int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, const crystal_request* requests,
+                  uint32_t n, const crystal_serve_config* cfg, crystal_request_result* results, uint64_t* wall_ns);
 
 /* ---- direct hashing that allocates nothing --------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot

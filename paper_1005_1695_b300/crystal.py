@@ -81,6 +81,23 @@ BATCH_HEADER_BYTES = 64
 
 crystal_callback = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
 
+REQUEST_DTYPE = np.dtype([("arrival_ns", "<u8"), ("src_offset", "<u8"), ("size", "<u8"), ("out_size", "<u8"),
+                          ("capture_offset", "<u8"), ("kind", "<i4"), ("reserved", "<u4")])
+RESULT_DTYPE = np.dtype([("status", "<i4"), ("reserved", "<u4"), ("admit_ns", "<u8"), ("submit_ns", "<u8"),
+                         ("done_ns", "<u8"), ("used_bytes", "<u8")])
+assert REQUEST_DTYPE.itemsize == 48 and RESULT_DTYPE.itemsize == 40
+NO_CAPTURE = (1 << 64) - 1
+
+
+CRYSTAL_TASK_EXTERNAL_INPUT = 1
+CRYSTAL_SERVE_SOURCE_PINNED = 1
+
+
+class crystal_serve_config(ctypes.Structure):
+    _fields_ = [("copy_threads", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("direct_params", ctypes.c_void_p), ("sliding_params", ctypes.c_void_p),
+                ("capture", ctypes.c_void_p), ("capture_bytes", ctypes.c_uint64)]
+
 _lib = None
 _u64 = ctypes.c_uint64
 _vp = ctypes.c_void_p
@@ -115,6 +132,12 @@ def load() -> ctypes.CDLL:
         "crystal_task_submit_many": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.c_int,
                                                     ctypes.POINTER(crystal_hash_params), crystal_callback, _vp]),
         "crystal_task_poll": (ctypes.c_int, [_vp]),
+        "crystal_task_create_ex": (ctypes.c_int, [_vp, _u64, _u64, _u64, ctypes.c_uint32, ctypes.POINTER(_vp)]),
+        "crystal_task_bind_input": (ctypes.c_int, [_vp, _vp, _u64]),
+        "crystal_host_register": (ctypes.c_int, [_vp, _u64]),
+        "crystal_host_unregister": (ctypes.c_int, [_vp]),
+        "crystal_serve": (ctypes.c_int, [_vp, _vp, _u64, _vp, ctypes.c_uint32, ctypes.POINTER(crystal_serve_config),
+                                         _vp, ctypes.POINTER(_u64)]),
         "crystal_task_wait": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "crystal_task_release": (ctypes.c_int, [_vp]),
         "crystal_task_timing": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64),
@@ -173,6 +196,22 @@ def kernel_launches() -> int:
     return int(load().crystal_kernel_launches())
 
 
+def page_aligned(nbytes: int) -> np.ndarray:
+    """A uint8 array whose data starts on a 4 KiB page (for host_register)."""
+    raw = np.empty(nbytes + 4096, dtype=np.uint8)
+    off = (-raw.ctypes.data) % 4096
+    return raw[off:off + nbytes]
+
+
+def host_register(arr: np.ndarray) -> None:
+    """Page-lock ``arr``'s memory (crystal_host_register)."""
+    check(load().crystal_host_register(arr.ctypes.data, arr.nbytes), "crystal_host_register")
+
+
+def host_unregister(arr: np.ndarray) -> None:
+    check(load().crystal_host_unregister(arr.ctypes.data), "crystal_host_unregister")
+
+
 # ---- job runtime ---------------------------------------------------------------
 
 class Task:
@@ -187,6 +226,16 @@ class Task:
             if hin else np.zeros(0, np.uint8)
         self.h_out = np.ctypeslib.as_array((ctypes.c_uint8 * max(out_size, 1)).from_address(hout))[:out_size] \
             if hout else np.zeros(0, np.uint8)
+
+    def bind_input(self, arr: Optional[np.ndarray]):
+        """crystal_task_bind_input: read the next submit's input from ``arr``
+        (keep it alive and unchanged until the job completes)."""
+        if arr is None:
+            check(load().crystal_task_bind_input(self.handle, None, 0), "crystal_task_bind_input")
+            return
+        self._bound = arr
+        check(load().crystal_task_bind_input(self.handle, arr.ctypes.data, arr.nbytes), "crystal_task_bind_input")
+        self.in_size = arr.nbytes
 
     def resize(self, in_size: int, out_size: int):
         check(load().crystal_task_resize(self.handle, in_size, out_size), "crystal_task_resize")
@@ -257,6 +306,26 @@ class Context:
         self._cb_keepalive = cb
         return load().crystal_task_submit_many(arr, len(tasks), kind, ctypes.byref(p) if p is not None else None,
                                                cb, user)
+
+    def serve(self, source: np.ndarray, requests: np.ndarray, direct: Optional[crystal_hash_params] = None,
+              sliding: Optional[crystal_hash_params] = None, capture: Optional[np.ndarray] = None,
+              copy_threads: int = 4, source_pinned: bool = False):
+        """crystal_serve: play ``requests`` (REQUEST_DTYPE, arrival order)
+        against this context.  Returns (status, results, wall_ns)."""
+        src = np.ascontiguousarray(source, dtype=np.uint8)
+        req = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
+        res = np.zeros(len(req), dtype=RESULT_DTYPE)
+        cfg = crystal_serve_config()
+        cfg.copy_threads = copy_threads
+        cfg.flags = CRYSTAL_SERVE_SOURCE_PINNED if source_pinned else 0
+        cfg.direct_params = ctypes.cast(ctypes.pointer(direct), ctypes.c_void_p) if direct is not None else None
+        cfg.sliding_params = ctypes.cast(ctypes.pointer(sliding), ctypes.c_void_p) if sliding is not None else None
+        if capture is not None:
+            cfg.capture, cfg.capture_bytes = capture.ctypes.data, capture.nbytes
+        wall = _u64()
+        st = load().crystal_serve(self.handle, src.ctypes.data, src.nbytes, req.ctypes.data, len(req),
+                                  ctypes.byref(cfg), res.ctypes.data, ctypes.byref(wall))
+        return st, res, wall.value
 
     def stats(self) -> crystal_stats:
         s = crystal_stats()

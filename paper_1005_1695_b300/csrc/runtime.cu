@@ -67,7 +67,11 @@ struct crystal_task {
     uint8_t* d_in = nullptr;
     uint8_t* d_out = nullptr;
     uint8_t* d_scratch = nullptr;
-    uint64_t h_in_off = 0, h_out_off = 0, d_in_off = 0, d_out_off = 0, d_scratch_off = 0;
+    uint8_t* d_reserved = nullptr;  // scratch reserved at create (crystal_task_create_ex)
+    const uint8_t* h_in_ext = nullptr;  // caller memory bound as the input (crystal_task_bind_input)
+    bool external_input = false;        // created without its own pinned input buffer
+    uint64_t h_in_off = 0, h_out_off = 0, d_in_off = 0, d_out_off = 0, d_scratch_off = 0, d_reserved_off = 0;
+    uint64_t reserved_bytes = 0;
     uint64_t in_cap = 0, out_cap = 0, in_size = 0, out_size = 0, scratch_bytes = 0;
     int kind = 0;
     crystal_hash_params params{};
@@ -158,10 +162,17 @@ void free_host(crystal_ctx* c, uint8_t* p, uint64_t off) {
     else cudaFreeHost(p);
 }
 
+// Scratch a finished job gives back (none when it used its reserved scratch).
+void free_job_scratch(crystal_ctx* c, crystal_task* t) {
+    if (t->d_scratch && t->d_scratch != t->d_reserved) free_device(c, t->d_scratch, t->d_scratch_off);
+    t->d_scratch = nullptr;
+}
+
 void free_task_buffers(crystal_task* t) {
     crystal_ctx* c = t->ctx;
-    free_device(c, t->d_scratch, t->d_scratch_off);
-    t->d_scratch = nullptr;
+    free_job_scratch(c, t);
+    free_device(c, t->d_reserved, t->d_reserved_off);
+    t->d_reserved = nullptr;
     free_device(c, t->d_in, t->d_in_off);
     free_device(c, t->d_out, t->d_out_off);
     free_host(c, t->h_in, t->h_in_off);
@@ -265,7 +276,8 @@ int capture_graph(crystal_ctx* c, Slot& s, int variant) {
 int issue(crystal_ctx* c, Slot& s) {
     cudaStream_t st = s.stream;
     for (crystal_task* t : s.tasks) {
-        if (t->in_size && cudaMemcpyAsync(t->d_in, t->h_in, t->in_size, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        const uint8_t* src = t->h_in_ext ? t->h_in_ext : t->h_in;
+        if (t->in_size && cudaMemcpyAsync(t->d_in, src, t->in_size, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return CRYSTAL_EDEVICE;
     }
     uint32_t nd = 0, ns = 0;
@@ -317,8 +329,7 @@ void finish_slot(crystal_ctx* c, Slot& s, int issue_status) {
     for (crystal_task* j : jobs) {
         j->status = issue_status != CRYSTAL_OK ? issue_status : job_status(j, dev_status);
         j->t_done = t;
-        free_device(c, j->d_scratch, j->d_scratch_off);
-        j->d_scratch = nullptr;
+        free_job_scratch(c, j);
     }
     for (crystal_task* j : jobs) {
         if (j->cb) {
@@ -388,8 +399,7 @@ void master_loop(crystal_ctx* c) {
             for (crystal_task* t : cancel) t->state = T_RUNNING;  // callbacks may release it
             lk.unlock();
             for (crystal_task* t : cancel) {
-                free_device(c, t->d_scratch, t->d_scratch_off);
-                t->d_scratch = nullptr;
+                free_job_scratch(c, t);
                 t->status = CRYSTAL_ESHUTDOWN;
                 t->t_done = now_ns();
                 if (t->cb) {
@@ -624,7 +634,13 @@ int crystal_shutdown(crystal_ctx* c) {
 }
 
 int crystal_task_create(crystal_ctx* c, uint64_t in_size, uint64_t out_size, crystal_task** out) {
+    return crystal_task_create_ex(c, in_size, out_size, 0, 0, out);
+}
+
+int crystal_task_create_ex(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes,
+                           uint32_t flags, crystal_task** out) {
     if (!c || !out) return CRYSTAL_EINVAL;
+    if (flags & ~(uint32_t)CRYSTAL_TASK_EXTERNAL_INPUT) return CRYSTAL_EINVAL;
     *out = nullptr;
     if (in_size > c->cfg.max_in_bytes || out_size > c->cfg.max_out_bytes) return CRYSTAL_EINVAL;
     {
@@ -637,10 +653,15 @@ int crystal_task_create(crystal_ctx* c, uint64_t in_size, uint64_t out_size, cry
     t->ctx = c;
     t->in_cap = t->in_size = in_size;
     t->out_cap = t->out_size = out_size;
-    int st = alloc_host(c, in_size, &t->h_in, &t->h_in_off);
+    t->external_input = flags & CRYSTAL_TASK_EXTERNAL_INPUT;
+    int st = t->external_input ? CRYSTAL_OK : alloc_host(c, in_size, &t->h_in, &t->h_in_off);
     if (st == CRYSTAL_OK) st = alloc_host(c, out_size, &t->h_out, &t->h_out_off);
     if (st == CRYSTAL_OK) st = alloc_device(c, in_size, &t->d_in, &t->d_in_off);
     if (st == CRYSTAL_OK) st = alloc_device(c, out_size, &t->d_out, &t->d_out_off);
+    if (st == CRYSTAL_OK && scratch_bytes) {
+        st = alloc_device(c, scratch_bytes, &t->d_reserved, &t->d_reserved_off);
+        if (st == CRYSTAL_OK) t->reserved_bytes = scratch_bytes;
+    }
     if (st != CRYSTAL_OK) {
         free_task_buffers(t);
         delete t;
@@ -670,6 +691,7 @@ int crystal_task_resize(crystal_task* t, uint64_t in_size, uint64_t out_size) {
 int crystal_task_submit(crystal_task* t, int kind, const crystal_hash_params* params, crystal_callback cb,
                         void* user) {
     if (!t) return CRYSTAL_EINVAL;
+    if (t->external_input && !t->h_in_ext && t->in_size) return CRYSTAL_EINVAL;
     crystal_ctx* c = t->ctx;
     crystal_hash_params p;
     int st = resolve_params(kind, params, t->in_size, t->out_size, &p);
@@ -682,7 +704,10 @@ int crystal_task_submit(crystal_task* t, int kind, const crystal_hash_params* pa
     const uint64_t scratch = crystal_scratch_bytes(kind, t->in_size, t->out_size, &p);
     uint8_t* d_scratch = nullptr;
     uint64_t d_scratch_off = 0;
-    if (scratch) {
+    if (scratch && scratch <= t->reserved_bytes) {
+        d_scratch = t->d_reserved;
+        d_scratch_off = t->d_reserved_off;
+    } else if (scratch) {
         if (!c->pooled) cudaSetDevice(c->device);
         st = alloc_device(c, scratch, &d_scratch, &d_scratch_off);
         if (st != CRYSTAL_OK) return st == CRYSTAL_ENOMEM ? CRYSTAL_ENOMEM : CRYSTAL_EAGAIN;
@@ -690,7 +715,7 @@ int crystal_task_submit(crystal_task* t, int kind, const crystal_hash_params* pa
     {
         std::lock_guard<std::mutex> lk(c->mu);
         if (!c->accepting) {
-            free_device(c, d_scratch, d_scratch_off);
+            if (d_scratch != t->d_reserved) free_device(c, d_scratch, d_scratch_off);
             return CRYSTAL_ESHUTDOWN;
         }
         t->kind = kind;
@@ -723,6 +748,7 @@ int crystal_task_submit_many(crystal_task* const* tasks, uint32_t n, int kind, c
     for (uint32_t i = 0; i < n; ++i) {
         crystal_task* t = tasks[i];
         if (!t || t->ctx != c) return CRYSTAL_EINVAL;
+        if (t->external_input && !t->h_in_ext && t->in_size) return CRYSTAL_EINVAL;
         int st = resolve_params(kind, params, t->in_size, t->out_size, &ps[i]);
         if (st != CRYSTAL_OK) return st;
         scratch[i] = crystal_scratch_bytes(kind, t->in_size, t->out_size, &ps[i]);
@@ -739,18 +765,27 @@ int crystal_task_submit_many(crystal_task* const* tasks, uint32_t n, int kind, c
     if (!c->pooled) cudaSetDevice(c->device);
     std::vector<uint8_t*> dp(n, nullptr);
     std::vector<uint64_t> doff(n, 0);
+    auto undo = [&](uint32_t upto) {
+        for (uint32_t j = 0; j < upto; ++j)
+            if (dp[j] && dp[j] != tasks[j]->d_reserved) free_device(c, dp[j], doff[j]);
+    };
     for (uint32_t i = 0; i < n; ++i) {
         if (!scratch[i]) continue;
+        if (scratch[i] <= tasks[i]->reserved_bytes) {
+            dp[i] = tasks[i]->d_reserved;
+            doff[i] = tasks[i]->d_reserved_off;
+            continue;
+        }
         int st = alloc_device(c, scratch[i], &dp[i], &doff[i]);
         if (st != CRYSTAL_OK) {
-            for (uint32_t j = 0; j < i; ++j) free_device(c, dp[j], doff[j]);
+            undo(i);
             return st == CRYSTAL_ENOMEM ? CRYSTAL_ENOMEM : CRYSTAL_EAGAIN;
         }
     }
     {
         std::lock_guard<std::mutex> lk(c->mu);
         if (!c->accepting) {
-            for (uint32_t j = 0; j < n; ++j) free_device(c, dp[j], doff[j]);
+            undo(n);
             return CRYSTAL_ESHUTDOWN;
         }
         const uint64_t now = now_ns();
@@ -773,6 +808,39 @@ int crystal_task_submit_many(crystal_task* const* tasks, uint32_t n, int kind, c
         }
     }
     c->cv_master.notify_one();
+    return CRYSTAL_OK;
+}
+
+int crystal_task_bind_input(crystal_task* t, const void* host, uint64_t size) {
+    if (!t) return CRYSTAL_EINVAL;
+    std::lock_guard<std::mutex> lk(t->ctx->mu);
+    if (t->state == T_OUTSTANDING || t->state == T_RUNNING) return CRYSTAL_EINVAL;
+    if (!host) {
+        if (t->external_input) return CRYSTAL_EINVAL;  // it has no buffer of its own to go back to
+        t->h_in_ext = nullptr;
+        return CRYSTAL_OK;
+    }
+    if (size > t->in_cap) return CRYSTAL_EINVAL;
+    t->h_in_ext = static_cast<const uint8_t*>(host);
+    t->in_size = size;
+    return CRYSTAL_OK;
+}
+
+int crystal_host_register(void* host, uint64_t bytes) {
+    if (!host || !bytes) return CRYSTAL_EINVAL;
+    if (cudaHostRegister(host, bytes, cudaHostRegisterDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return CRYSTAL_EDEVICE;
+    }
+    return CRYSTAL_OK;
+}
+
+int crystal_host_unregister(void* host) {
+    if (!host) return CRYSTAL_EINVAL;
+    if (cudaHostUnregister(host) != cudaSuccess) {
+        cudaGetLastError();
+        return CRYSTAL_EDEVICE;
+    }
     return CRYSTAL_OK;
 }
 

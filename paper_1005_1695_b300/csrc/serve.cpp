@@ -1,0 +1,236 @@
+// Serving loop: an open-loop stream of hashing requests over the job runtime.
+//
+// Section 2.2 of the CrystalGPU paper describes stream-processing
+// applications: data units arrive continuously and each must be processed
+// with low latency.  crystal_serve plays such a stream against a context:
+// requests arrive at their given times, are admitted in arrival order as
+// soon as the context's pools can hold their buffers and scratch (admission
+// by pool memory), have their bytes staged into the job's pinned buffer by
+// copy threads, and are submitted; the master thread batches whatever is
+// outstanding when a stream slot frees (continuous batching), so requests
+// that arrive while others run join the next batch and overlap on the GPU.
+// Completion callbacks record the times, optionally copy the result out,
+// and release the job, which frees room for the next admission.
+#include <stdint.h>
+#include <string.h>
+#include <time.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "crystal.h"
+
+namespace {
+
+uint64_t mono_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+struct Serve;
+
+struct Ticket {
+    Serve* s;
+    uint32_t idx;
+};
+
+struct Serve {
+    crystal_ctx* ctx = nullptr;
+    const uint8_t* src = nullptr;
+    const crystal_request* req = nullptr;
+    crystal_request_result* res = nullptr;
+    crystal_hash_params pd{}, ps{};
+    uint8_t* capture = nullptr;
+    uint64_t capture_bytes = 0;
+    uint64_t t0 = 0;
+    bool pinned_source = false;
+    std::vector<Ticket> tickets;
+
+    std::mutex mu;
+    std::condition_variable cv_done, cv_work;
+    std::deque<std::pair<uint32_t, crystal_task*>> work;
+    uint32_t finished = 0;
+    uint64_t last_done = 0;
+    bool workers_stop = false;
+
+    const crystal_hash_params* params_for(int kind) const {
+        return kind == CRYSTAL_KIND_MD5_SLIDING ? &ps : &pd;
+    }
+
+    void finish(uint32_t i, int status) {
+        const uint64_t t = mono_ns() - t0;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            res[i].status = status;
+            res[i].done_ns = t;
+            ++finished;
+            if (t > last_done) last_done = t;
+        }
+        cv_done.notify_all();
+    }
+};
+
+uint64_t used_bytes(int kind, uint64_t n, const uint8_t* out, uint64_t out_size) {
+    if (kind == CRYSTAL_KIND_MD5_DIRECT) return out_size < 16 ? 0 : 16;
+    if (kind != CRYSTAL_KIND_MD5_SLIDING) return out_size;
+    uint32_t hdr[2];
+    memcpy(hdr, out, 8);
+    const uint64_t fixed = 8 + 4 * ((n + 31) / 32);
+    return (hdr[1] & 1u) ? fixed : fixed + 20ull * hdr[0];
+}
+
+// Completion callback, on the master thread.
+void on_done(crystal_task* t, int status, void* user) {
+    Ticket* tk = static_cast<Ticket*>(user);
+    Serve* s = tk->s;
+    const uint32_t i = tk->idx;
+    const crystal_request& r = s->req[i];
+    const uint8_t* out = static_cast<const uint8_t*>(crystal_task_host_out(t));
+    const uint64_t used = used_bytes(r.kind, r.size, out, r.out_size);
+    s->res[i].used_bytes = used;
+    if (r.capture_offset != UINT64_MAX && s->capture && r.capture_offset + used <= s->capture_bytes)
+        memcpy(s->capture + r.capture_offset, out, used);
+    crystal_task_release(t);  // freed by the master once this callback returns
+    s->finish(i, status);
+}
+
+void worker(Serve* s) {
+    for (;;) {
+        std::pair<uint32_t, crystal_task*> w;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [s] { return s->workers_stop || !s->work.empty(); });
+            if (s->work.empty()) return;
+            w = s->work.front();
+            s->work.pop_front();
+        }
+        const crystal_request& r = s->req[w.first];
+        if (s->pinned_source) {
+            crystal_task_bind_input(w.second, s->src + r.src_offset, r.size);
+        } else if (r.size) {
+            memcpy(crystal_task_host_in(w.second), s->src + r.src_offset, r.size);
+        }
+        s->res[w.first].submit_ns = mono_ns() - s->t0;
+        const int st = crystal_task_submit(w.second, r.kind, s->params_for(r.kind), on_done, &s->tickets[w.first]);
+        if (st != CRYSTAL_OK) {
+            crystal_task_release(w.second);
+            s->finish(w.first, st);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, const crystal_request* req,
+                  uint32_t n, const crystal_serve_config* cfg, crystal_request_result* res, uint64_t* wall_ns) {
+    if (!ctx || !req || !res || (!source && source_bytes)) return CRYSTAL_EINVAL;
+    for (uint32_t i = 0; i < n; ++i) {
+        const crystal_request& r = req[i];
+        if (r.src_offset > source_bytes || r.size > source_bytes - r.src_offset) return CRYSTAL_EINVAL;
+        if (r.kind != CRYSTAL_KIND_MD5_DIRECT && r.kind != CRYSTAL_KIND_MD5_SLIDING && r.kind != CRYSTAL_KIND_NOP)
+            return CRYSTAL_EINVAL;
+        if (i && r.arrival_ns < req[i - 1].arrival_ns) return CRYSTAL_EINVAL;
+    }
+    Serve s;
+    s.ctx = ctx;
+    s.src = static_cast<const uint8_t*>(source);
+    s.req = req;
+    s.res = res;
+    crystal_params_default(&s.pd);
+    crystal_params_default(&s.ps);
+    uint32_t threads = 4;
+    if (cfg) {
+        if (cfg->direct_params) s.pd = *cfg->direct_params;
+        if (cfg->sliding_params) s.ps = *cfg->sliding_params;
+        s.capture = static_cast<uint8_t*>(cfg->capture);
+        s.capture_bytes = cfg->capture_bytes;
+        if (cfg->copy_threads) threads = cfg->copy_threads;
+        s.pinned_source = cfg->flags & CRYSTAL_SERVE_SOURCE_PINNED;
+    }
+    if (threads > 64) threads = 64;
+    memset(res, 0, sizeof(crystal_request_result) * n);
+    s.tickets.resize(n);
+    for (uint32_t i = 0; i < n; ++i) s.tickets[i] = Ticket{&s, i};
+    std::vector<std::thread> pool;
+    for (uint32_t k = 0; k < threads; ++k) pool.emplace_back(worker, &s);
+
+    s.t0 = mono_ns();
+    std::deque<uint32_t> fifo;  // arrived, not yet admitted (arrival order)
+    uint32_t next = 0;
+    uint32_t admitted = 0;      // admitted or refused at admission
+    for (;;) {
+        const uint64_t now = mono_ns() - s.t0;
+        while (next < n && req[next].arrival_ns <= now) fifo.push_back(next++);
+        // admission: in arrival order, while the pools can hold the head request
+        while (!fifo.empty()) {
+            const uint32_t i = fifo.front();
+            const crystal_request& r = req[i];
+            const uint64_t scratch = crystal_scratch_bytes(r.kind, r.size, r.out_size, s.params_for(r.kind));
+            crystal_task* t = nullptr;
+            int st = crystal_task_create_ex(ctx, r.size, r.out_size, scratch,
+                                            s.pinned_source ? CRYSTAL_TASK_EXTERNAL_INPUT : 0u, &t);
+            if (st == CRYSTAL_EAGAIN) {
+                uint32_t finished;
+                {
+                    std::lock_guard<std::mutex> lk(s.mu);
+                    finished = s.finished;
+                }
+                if (finished < admitted) break;  // wait for a completion to free room
+                st = CRYSTAL_ENOMEM;             // nothing in flight: it can never fit
+            }
+            fifo.pop_front();
+            ++admitted;
+            res[i].admit_ns = mono_ns() - s.t0;
+            if (st != CRYSTAL_OK) {
+                s.finish(i, st);
+                continue;
+            }
+            {
+                std::lock_guard<std::mutex> lk(s.mu);
+                s.work.emplace_back(i, t);
+            }
+            s.cv_work.notify_one();
+        }
+        std::unique_lock<std::mutex> lk(s.mu);
+        if (s.finished == n) break;
+        if (!fifo.empty()) {
+            // blocked on pool room: wake on a completion or the next arrival
+            const uint32_t before = s.finished;
+            const uint64_t wait = next < n && req[next].arrival_ns > now ? req[next].arrival_ns - now : 200000;
+            s.cv_done.wait_for(lk, std::chrono::nanoseconds(wait < 200000 ? wait : 200000),
+                               [&] { return s.finished != before; });
+        } else if (next < n) {
+            const uint64_t due = req[next].arrival_ns;
+            lk.unlock();
+            const uint64_t t = mono_ns() - s.t0;
+            if (due > t + 200000) {
+                std::this_thread::sleep_for(std::chrono::nanoseconds(due - t - 100000));
+            } else {
+                while (mono_ns() - s.t0 < due) std::this_thread::yield();
+            }
+        } else {
+            s.cv_done.wait(lk, [&] { return s.finished == n; });
+            break;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(s.mu);
+        s.workers_stop = true;
+    }
+    s.cv_work.notify_all();
+    for (auto& th : pool) th.join();
+    if (wall_ns) *wall_ns = s.last_done;
+    int worst = CRYSTAL_OK;
+    for (uint32_t i = 0; i < n; ++i)
+        if (res[i].status < 0 && res[i].status != CRYSTAL_EOVERFLOW) worst = res[i].status;
+    return worst;
+}
+
+}  // extern "C"

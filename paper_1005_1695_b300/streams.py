@@ -147,3 +147,70 @@ def run_stream(mode: str, unit: Callable[[int], np.ndarray], n_units: int, unit_
     finally:
         ctx.shutdown()
     return res
+
+
+# ---- served stream --------------------------------------------------------------
+
+def make_trace(seed: int, n: int, rate_per_s: float, source_bytes: int, *, median: int = 256 << 10,
+               sigma: float = 1.5, cap: int = 64 << 20, p_sliding: float = 0.3, window: int = 20,
+               capture_every: int = 0, chunk_room: int = 4):
+    """An open-loop request trace: Poisson arrivals at ``rate_per_s``,
+    lognormal sizes (median, sigma, capped), a ``p_sliding`` share of
+    sliding-window requests, each request a window of the source arena at a
+    seeded offset.  Sliding outputs have room for ``chunk_room`` times the
+    expected chunk count (one chunk per 8 KiB) plus 64.  Every
+    ``capture_every``-th request (0: none) has its output captured; returns
+    (requests, capture_bytes)."""
+    from . import inputs
+
+    sizes = inputs.lognormal_sizes(seed, n, median=median, sigma=sigma, cap=min(cap, source_bytes))
+    arrivals = inputs.poisson_arrivals(seed, n, rate_per_s)
+    sliding = inputs.kind_mix(seed, n, p_sliding)
+    offs = inputs.rng(seed, inputs.TAG_SIZES, 7).integers(0, 1 << 62, size=n) % (source_bytes - sizes + 1)
+    req = np.zeros(n, dtype=C.REQUEST_DTYPE)
+    req["arrival_ns"] = np.round(arrivals * 1e9).astype(np.uint64)
+    req["src_offset"] = offs
+    req["size"] = sizes
+    req["kind"] = np.where(sliding, C.CRYSTAL_KIND_MD5_SLIDING, C.CRYSTAL_KIND_MD5_DIRECT)
+    out = np.full(n, 16, dtype=np.uint64)
+    for i in np.nonzero(sliding)[0]:
+        n_i = int(sizes[i])
+        out[i] = C.sliding_out_bytes(n_i, chunk_room * (n_i // 8192) + 64)
+    req["out_size"] = out
+    req["capture_offset"] = C.NO_CAPTURE
+    cap_bytes = 0
+    if capture_every:
+        for i in range(0, n, capture_every):
+            req["capture_offset"][i] = cap_bytes
+            cap_bytes += int(out[i] + 15) // 16 * 16
+    return req, cap_bytes
+
+
+def serve_trace(req, source, *, device_pool_bytes: int, host_pool_bytes: int, streams: int = 8,
+                batch_jobs: int = 8, copy_threads: int = 8, device: int = 0, capture_bytes: int = 0,
+                graphs: bool = True, direct=None, sliding=None, source_pinned: bool = False):
+    """Run a trace through crystal_serve on a fresh context sized to the pools.
+    With ``source_pinned`` the source is page-locked for the run and jobs read
+    their input from it directly.  Returns (status, results, wall_ns, capture)."""
+    max_in = int(req["size"].max()) if len(req) else 1
+    max_out = int(req["out_size"].max()) if len(req) else 16
+    ctx = C.Context(max_in_bytes=max(max_in, 1), max_out_bytes=max(max_out, 16),
+                    device_pool_bytes=device_pool_bytes, host_pool_bytes=host_pool_bytes, n_streams=streams,
+                    device=device, max_batch_jobs=batch_jobs, max_batch_bytes=max(batch_jobs << 20, 32 << 20),
+                    flags=C.CRYSTAL_FLAG_GRAPHS if graphs else 0)
+    capture = np.zeros(max(capture_bytes, 16), dtype=np.uint8) if capture_bytes else None
+    if source_pinned:
+        C.host_register(source)
+    try:
+        st, res, wall = ctx.serve(source, req, direct=direct, sliding=sliding, capture=capture,
+                                  copy_threads=copy_threads, source_pinned=source_pinned)
+    finally:
+        ctx.shutdown()
+        if source_pinned:
+            C.host_unregister(source)
+    return st, res, wall, capture
+
+
+def latency_ms(req, res) -> np.ndarray:
+    """Request latency: completion minus arrival (admission wait included)."""
+    return (res["done_ns"].astype(np.float64) - req["arrival_ns"].astype(np.float64)) / 1e6

@@ -7,6 +7,7 @@ the same alone and in a mix.  Failure paths are driven from the host: a
 full pool, a too-small output buffer, a bounded wait that runs out, an
 allocation that cannot succeed at init, shutdown with jobs in flight.
 """
+import ctypes
 import threading
 
 import numpy as np
@@ -285,3 +286,41 @@ def test_external_device_arena(C, oracle_mod):
         base = arena.data_ptr()
         for t in tasks:
             assert base <= C.load().crystal_task_device_in(t.handle) < base + arena.numel()
+
+
+def test_bound_input_from_registered_memory(C, oracle_mod):
+    from paper_1005_1695_b300 import inputs
+
+    n = 700_001
+    src = C.page_aligned(3 * n)
+    src[:] = inputs.uniform_unit(41, 0, 3 * n)
+    C.host_register(src)
+    try:
+        with C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 20, device_pool_bytes=64 << 20,
+                       host_pool_bytes=16 << 20) as ctx:
+            h = ctypes.c_void_p()
+            st = C.load().crystal_task_create_ex(ctx.handle, n, 16, 0, C.CRYSTAL_TASK_EXTERNAL_INPUT,
+                                                ctypes.byref(h))
+            assert st == C.CRYSTAL_OK
+            t = C.Task(ctx, h.value, n, 16)
+            ctx._tasks.add(t)
+            assert C.load().crystal_task_host_in(t.handle) is None
+            assert t.submit(DIRECT) == C.CRYSTAL_EINVAL  # nothing bound yet
+            for k in range(3):
+                view = src[k * n:(k + 1) * n]
+                t.bind_input(view)
+                assert t.submit(DIRECT) == C.CRYSTAL_OK
+                assert t.wait(30 * SEC) == C.CRYSTAL_OK
+                assert t.output()[:16] == oracle_mod.direct(view, 4096)
+            assert C.load().crystal_task_bind_input(t.handle, None, 0) == C.CRYSTAL_EINVAL
+            # a job with its own buffer can also be bound, and unbound again
+            t2 = ctx.task_create(n, 16)
+            t2.h_in[:] = src[:n]
+            t2.bind_input(src[n:2 * n])
+            assert t2.submit(DIRECT) == 0 and t2.wait(30 * SEC) == 0
+            assert t2.output()[:16] == oracle_mod.direct(src[n:2 * n], 4096)
+            t2.bind_input(None)
+            assert t2.submit(DIRECT) == 0 and t2.wait(30 * SEC) == 0
+            assert t2.output()[:16] == oracle_mod.direct(src[:n], 4096)
+    finally:
+        C.host_unregister(src)

@@ -1,0 +1,83 @@
+"""The serving loop on the GPU: Poisson arrivals, lognormal sizes, mixed
+direct / sliding requests, admission against a small device pool (so
+requests wait for room), continuous batching.  Every captured output must be
+bit-exact against the oracle, and the same as the request run alone."""
+import numpy as np
+import pytest
+
+from helpers import first_difference, same_result
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    from paper_1005_1695_b300 import crystal
+
+    crystal.load()
+    return crystal
+
+
+def _outputs(req, res, capture):
+    outs = {}
+    for i in range(len(req)):
+        off = int(req["capture_offset"][i])
+        if off != (1 << 64) - 1:
+            outs[i] = capture[off:off + int(res["used_bytes"][i])].tobytes()
+    return outs
+
+
+@pytest.mark.parametrize("pinned", [False, True], ids=["staged", "pinned_source"])
+def test_served_mix_bit_exact_alone_equals_mix(C, oracle_mod, pinned):
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    src = inputs.arena(3, 64 << 20, out=C.page_aligned(64 << 20))
+    req, cap = S.make_trace(3, 240, 4000.0, src.nbytes, median=96 << 10, sigma=1.5, cap=4 << 20,
+                            capture_every=1)
+    # a device pool far smaller than the trace's total bytes: admission has to wait
+    st, res, wall, capture = S.serve_trace(req, src, device_pool_bytes=24 << 20, host_pool_bytes=24 << 20,
+                                           streams=4, batch_jobs=4, copy_threads=4, capture_bytes=cap,
+                                           source_pinned=pinned)
+    assert st == C.CRYSTAL_OK
+    assert (res["status"] == 0).all()
+    assert (res["done_ns"] >= res["submit_ns"]).all() and (res["submit_ns"] >= res["admit_ns"]).all()
+    assert (res["admit_ns"] >= req["arrival_ns"]).all()
+    assert wall > 0
+    mix = _outputs(req, res, capture)
+    for i in range(len(req)):
+        k, n, o = int(req["kind"][i]), int(req["size"][i]), int(req["src_offset"][i])
+        ost, want = oracle_mod.task(k, src[o:o + n], int(req["out_size"][i]))
+        assert ost == 0
+        assert same_result(k, n, mix[i], want), f"request {i}: " + first_difference(k, n, mix[i], want)
+    # the same requests one at a time, each alone on the GPU
+    for i in range(0, len(req), 12):
+        one = req[i:i + 1].copy()
+        one["arrival_ns"] = 0
+        one["capture_offset"] = 0
+        st1, res1, _, cap1 = S.serve_trace(one, src, device_pool_bytes=64 << 20, host_pool_bytes=64 << 20,
+                                           streams=1, batch_jobs=1, copy_threads=1,
+                                           capture_bytes=int(one["out_size"][0]) + 16)
+        assert st1 == C.CRYSTAL_OK
+        alone = cap1[:int(res1["used_bytes"][0])].tobytes()
+        assert alone == mix[i], i
+
+
+def test_request_that_never_fits_fails_cleanly(C):
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    src = inputs.arena(4, 16 << 20)
+    req, _ = S.make_trace(4, 20, 2000.0, src.nbytes, median=64 << 10, cap=1 << 20, p_sliding=0.0)
+    req["size"][5] = 12 << 20  # larger than the whole device pool below
+    req["src_offset"][5] = 0
+    st, res, wall, _ = S.serve_trace(req, src, device_pool_bytes=8 << 20, host_pool_bytes=64 << 20,
+                                     streams=2, batch_jobs=2)
+    assert res["status"][5] == C.CRYSTAL_ENOMEM
+    others = np.delete(res["status"], 5)
+    assert (others == 0).all()
+    assert st == C.CRYSTAL_ENOMEM
