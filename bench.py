@@ -598,6 +598,53 @@ def run_serving(args, ws, rank, local):
                       "rates_per_s": out, "data": "synthetic"}))
 
 
+def run_batched(args, ws, rank, local):
+    """Uneven units (log-uniform 4 KiB-16 MiB, 80/20 direct/sliding) read in
+    place from a page-locked seeded arena, all available at once, packed into
+    batches replayed as CUDA graphs with the autotuned setting; against the
+    plain single-stream form on a sample."""
+    import torch
+
+    from paper_1005_1695_b300 import autotune as A
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    torch.cuda.set_device(local)
+    C.load()
+    src = inputs.arena(args.seed, args.arena_bytes, out=C.page_aligned(args.arena_bytes))
+    U = args.units or 100_000
+    req, _ = S.make_batch(args.seed, U, src.nbytes)
+    pool = args.pool_bytes
+    C.host_register(src)
+    try:
+        sample = req[:min(U, args.tune_units)]
+        best, table = A.tune(sample, src, device_pool_bytes=pool, device=local)
+        st, res, wall = A.run_batch(req, src, best, device_pool_bytes=pool, device=local)
+        C.check(st, "crystal_serve")
+        plain_n = min(U, args.malloc_units)
+        stp, resp, wallp = A.run_batch(req[:plain_n], src, A.Setting(1, 1, 64 << 20), device_pool_bytes=pool,
+                                       device=local, submit_threads=1,
+                                       flags=C.CRYSTAL_FLAG_NO_OVERLAP | C.CRYSTAL_FLAG_NO_BATCH)
+        C.check(stp, "crystal_serve")
+    finally:
+        C.host_unregister(src)
+    link = measure_link(torch, torch.device("cuda", local), 256 << 20)
+    h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
+    total = float(req["size"].sum())
+    gbs = total / (wall / 1e9) / GB
+    print(json.dumps({"metric": "end-to-end hashed GB/s, batched uneven units", "unit": "GB/s",
+                      "workload": f"{U} units, log-uniform 4 KiB-16 MiB, 80/20 direct/sliding (w=20), "
+                                  f"inputs read in place from a {args.arena_bytes >> 30} GiB page-locked arena, "
+                                  "CUDA graphs, autotuned",
+                      "GB": round(total / GB, 2), "value": round(gbs, 3), "frac_of_link": round(gbs / h2d, 4),
+                      "host_link": link, "chosen": best.as_dict(), "tuning_table": table,
+                      "tuning_sample_units": len(sample),
+                      "plain_single_stream": {"units": plain_n,
+                                              "GB_per_s": round(float(req["size"][:plain_n].sum()) / (wallp / 1e9) / GB, 3)},
+                      "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -614,7 +661,8 @@ def main():
     ap.add_argument("--cpu-units", type=int, default=0, help="oracle sample units (0: 4 per core, <= 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="value,e2e", help="value (device-resident) and/or e2e (job API)")
-    ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined", "serving"])
+    ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined", "serving", "batched"])
+    ap.add_argument("--tune-units", type=int, default=4000)
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000")
     ap.add_argument("--seconds", type=float, default=2.0)
     ap.add_argument("--min-requests", type=int, default=2000)
@@ -658,6 +706,13 @@ def main():
 
     if args.workload == "serving":
         run_serving(args, ws, rank, local)
+        return
+    if args.workload == "batched":
+        if args.units == 256:
+            args.units = 0
+        if args.arena_bytes == 1 << 30:
+            args.arena_bytes = 8 << 30
+        run_batched(args, ws, rank, local)
         return
     if args.workload in ("direct", "plain", "pipelined"):
         if args.workload in ("plain", "pipelined") and args.units == 256 and args.unit_bytes == 1 << 20:

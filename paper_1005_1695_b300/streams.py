@@ -214,3 +214,31 @@ def serve_trace(req, source, *, device_pool_bytes: int, host_pool_bytes: int, st
 def latency_ms(req, res) -> np.ndarray:
     """Request latency: completion minus arrival (admission wait included)."""
     return (res["done_ns"].astype(np.float64) - req["arrival_ns"].astype(np.float64)) / 1e6
+
+
+def make_batch(seed: int, n: int, source_bytes: int, *, lo: int = 4096, hi: int = 16 << 20,
+               p_sliding: float = 0.2, chunk_room: int = 4, capture: bool = False):
+    """``n`` units of log-uniform size in [lo, hi], a ``p_sliding`` share of
+    them sliding-window, all available at once (arrival 0), each a window of
+    the source arena at a seeded offset.  Returns (requests, capture_bytes)."""
+    from . import inputs
+
+    sizes = inputs.loguniform_sizes(seed, n, lo=lo, hi=min(hi, source_bytes))
+    sliding = inputs.kind_mix(seed, n, p_sliding)
+    offs = inputs.rng(seed, inputs.TAG_SIZES, 9).integers(0, 1 << 62, size=n) % (source_bytes - sizes + 1)
+    req = np.zeros(n, dtype=C.REQUEST_DTYPE)
+    req["src_offset"] = offs
+    req["size"] = sizes
+    req["kind"] = np.where(sliding, C.CRYSTAL_KIND_MD5_SLIDING, C.CRYSTAL_KIND_MD5_DIRECT)
+    out = np.full(n, 16, dtype=np.uint64)
+    for i in np.nonzero(sliding)[0]:
+        n_i = int(sizes[i])
+        out[i] = C.sliding_out_bytes(n_i, chunk_room * (n_i // 8192) + 64)
+    req["out_size"] = out
+    req["capture_offset"] = C.NO_CAPTURE
+    cap_bytes = 0
+    if capture:
+        for i in range(n):
+            req["capture_offset"][i] = cap_bytes
+            cap_bytes += int(out[i] + 15) // 16 * 16
+    return req, cap_bytes
