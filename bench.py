@@ -645,6 +645,82 @@ def run_batched(args, ws, rank, local):
                       "data": "synthetic"}))
 
 
+def run_overhead(args, ws, rank, local):
+    """Framework overhead of one job (Section 5.1, Figure 5): copy in n bytes,
+    dummy kernel, copy out n bytes, issued directly vs through the job
+    runtime; the difference is the framework's own cost."""
+    import ctypes
+
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+
+    torch.cuda.set_device(local)
+    L = C.load()
+    sizes = [int(x) for x in args.sizes.split(",")]
+    reps = max(30, args.steps)
+    stream = torch.cuda.Stream()
+    out = {}
+    with C.Context(max_in_bytes=max(sizes), max_out_bytes=max(sizes), device_pool_bytes=2 * max(sizes) + (64 << 20),
+                   host_pool_bytes=2 * max(sizes) + (16 << 20), n_streams=1, device=local) as ctx:
+        for n in sizes:
+            t = ctx.task_create(n, n)
+            # the direct path moves the very same buffers: the job's pinned and device memory
+            h_in, h_out = L.crystal_task_host_in(t.handle), L.crystal_task_host_out(t.handle)
+            d_in, d_out = L.crystal_task_device_in(t.handle), L.crystal_task_device_out(t.handle)
+            raw = []
+            for i in range(reps + 5):
+                t0 = time.perf_counter()
+                C.check(L.crystal_direct_job(h_in, d_in, n, h_out, d_out, n, stream.cuda_stream),
+                        "crystal_direct_job")
+                if i >= 5:
+                    raw.append(time.perf_counter() - t0)
+            fw = []
+            for i in range(reps + 5):
+                t0 = time.perf_counter()
+                C.check(t.submit(C.CRYSTAL_KIND_NOP), "submit")
+                assert t.wait(10_000_000_000) == C.CRYSTAL_OK
+                if i >= 5:
+                    fw.append(time.perf_counter() - t0)
+            t.release()
+            r, f = float(np.median(raw)) * 1e6, float(np.median(fw)) * 1e6
+            out[str(n)] = {"direct_us": round(r, 1), "framework_us": round(f, 1), "overhead_us": round(f - r, 1),
+                           "overhead_pct": round(100 * (f - r) / f, 1)}
+    print(json.dumps({"metric": "framework overhead per job (dummy kernel, equal bytes in and out)",
+                      "unit": "us", "sizes": out, "reps": reps,
+                      "paper_context": "slightly under 70 us per job on a 9800 GX2 host (Section 5.1)"}))
+
+
+def run_streamlen(args, ws, rank, local):
+    """Streams of 1..10 jobs of 1 MiB (direct hashing, Figure 8's shape): the
+    plain form against no-overlap and pooled + overlap, per stream length."""
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    torch.cuda.set_device(local)
+    C.load()
+    N = 1 << 20
+    p = C.params()
+
+    def unit(i):
+        return inputs.uniform_unit(args.seed, i, N)
+
+    out = {}
+    for L in range(1, 11):
+        row = {}
+        for mode in ("plain", "no_overlap", "pooled"):
+            runs = [S.run_stream(mode, unit, L, N, C.CRYSTAL_KIND_MD5_DIRECT, p, 16, streams=8, batch_jobs=8,
+                                 depth=24, device=local).seconds for _ in range(max(3, args.steps))]
+            row[mode] = round(L * N / float(np.median(runs)) / GB, 3)
+        row["speedup_pooled_vs_plain"] = round(row["pooled"] / row["plain"], 2)
+        out[str(L)] = row
+    print(json.dumps({"metric": "GB/s per stream length, 1 MiB direct-hash jobs", "unit": "GB/s",
+                      "stream_lengths": out, "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -661,7 +737,9 @@ def main():
     ap.add_argument("--cpu-units", type=int, default=0, help="oracle sample units (0: 4 per core, <= 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="value,e2e", help="value (device-resident) and/or e2e (job API)")
-    ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined", "serving", "batched"])
+    ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined", "serving", "batched", "overhead",
+                             "streamlen"])
+    ap.add_argument("--sizes", default="4096,65536,1048576,16777216,67108864")
     ap.add_argument("--tune-units", type=int, default=4000)
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000")
     ap.add_argument("--seconds", type=float, default=2.0)
@@ -706,6 +784,9 @@ def main():
 
     if args.workload == "serving":
         run_serving(args, ws, rank, local)
+        return
+    if args.workload in ("overhead", "streamlen"):
+        {"overhead": run_overhead, "streamlen": run_streamlen}[args.workload](args, ws, rank, local)
         return
     if args.workload == "batched":
         if args.units == 256:

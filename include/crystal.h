@@ -48,7 +48,7 @@ enum {
 
 /* ---- job kinds (the kernel_func of Figure 2, chosen by id) -------------- */
 enum {
-    CRYSTAL_KIND_NOP = 0,         /* dummy kernel of Section 5.1: copy in, no work, copy out */
+    CRYSTAL_KIND_NOP = 0,         /* dummy kernel of Section 5.1: copy in, empty kernel, copy out */
     CRYSTAL_KIND_MD5_DIRECT = 1,  /* direct hashing (Section 5.2, Figure 6) */
     CRYSTAL_KIND_MD5_SLIDING = 2  /* sliding-window hashing (Section 2.2, content-addressable storage) */
 };
@@ -234,6 +234,15 @@ const char* crystal_strerror(int status);
  * launchers; a graph replay counts each kernel node). */
 uint64_t crystal_kernel_launches(void);
 
+/* The baseline of the overhead experiment (Section 5.1, Figure 5): one job
+ * issued without the framework -- copy in_size bytes h_in -> d_in, launch a
+ * kernel that does nothing, copy out_size bytes d_out -> h_out, all on
+ * `stream`, then wait for the stream.  Host buffers should be page-locked.
+ * CRYSTAL_KIND_NOP jobs through the runtime do the same three stages, so the
+ * difference of the two times is the framework's own cost. */
+int crystal_direct_job(const void* h_in, void* d_in, uint64_t in_size, void* h_out, const void* d_out,
+                       uint64_t out_size, void* stream);
+
 /* ---- output layouts (what the kernels write) ----------------------------
  * direct  : 16-byte digest Direct(u, S) = MD5(MD5(seg_0) || ... || MD5(seg_{m-1})),
  *           m = max(1, ceil(n / S)); the last segment may be short.
@@ -245,7 +254,7 @@ uint64_t crystal_kernel_launches(void);
  *           digest[k] = Direct(u[end_{k-1}, end_k), chunk_segment_bytes),
  *           end_{-1} = 0.  If the records do not fit in out_size, flags bit 0
  *           is set, n_chunks holds the count needed and no record is written.
- * nop     : nothing is written; out_size bytes are copied back.
+ * nop     : a kernel that does nothing runs; out_size bytes are copied back.
  */
 
 /* ---- stateless batch launchers ------------------------------------------

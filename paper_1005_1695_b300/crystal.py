@@ -147,6 +147,7 @@ def load() -> ctypes.CDLL:
         "crystal_sliding_out_bytes": (_u64, [_u64, _u64]),
         "crystal_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "crystal_kernel_launches": (_u64, []),
+        "crystal_direct_job": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _u64, _vp]),
         "crystal_scratch_bytes": (_u64, [ctypes.c_int, _u64, _u64, ctypes.POINTER(crystal_hash_params)]),
         "crystal_batch_plan": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
         "crystal_batch_bytes": (_u64, [ctypes.c_uint32]),

@@ -22,6 +22,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <thread>
 
 #include "crystal.h"
 #include "crystal_internal.h"
@@ -48,6 +49,16 @@ constexpr int kDigestThreads = 256;
 constexpr int kScanThreads = 1024;
 
 constexpr uint32_t kDevBadRecord = 1u;
+
+// Whether each kernel puts the round-function add on the FMA pipe (see
+// md5::add_on_fma): throughput-bound kernels do; the serial digest-of-digests
+// chains may prefer the lower-latency ALU add.
+#ifndef CRYSTAL_FMA_SEGMENTS
+#define CRYSTAL_FMA_SEGMENTS 1
+#endif
+#ifndef CRYSTAL_FMA_OUTER
+#define CRYSTAL_FMA_OUTER 1
+#endif
 
 __device__ __forceinline__ crystal_unit* units_of(crystal_batch* b) {
     return reinterpret_cast<crystal_unit*>(reinterpret_cast<uint8_t*>(b) + sizeof(crystal_batch));
@@ -94,7 +105,7 @@ __global__ void __launch_bounds__(kSegThreads, 5) k_direct_segments(crystal_batc
         const uint64_t off = j * X.seg_bytes;
         const uint64_t len = X.n > off ? (X.n - off < X.seg_bytes ? X.n - off : X.seg_bytes) : 0;
         uint32_t st[4];
-        md5::digest_global(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
+        md5::digest_global<CRYSTAL_FMA_SEGMENTS>(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
         store_digest16(reinterpret_cast<uint8_t*>(X.scratch) + 16 * j, st);
     }
 }
@@ -108,7 +119,7 @@ __global__ void __launch_bounds__(kDigestThreads) k_direct_outer(crystal_batch* 
         const crystal_unit X = U[u];
         const uint64_t m = num_segments(X.n, X.seg_bytes);
         uint32_t st[4];
-        md5::digest_global(reinterpret_cast<const uint8_t*>(X.scratch), 16 * m, st, one);
+        md5::digest_global<CRYSTAL_FMA_OUTER>(reinterpret_cast<const uint8_t*>(X.scratch), 16 * m, st, one);
         store_digest(reinterpret_cast<uint8_t*>(X.out), st);
     }
 }
@@ -456,7 +467,7 @@ __global__ void __launch_bounds__(kDigestThreads, 2) k_chunk_segments(crystal_ba
         const uint64_t off = start + (uint64_t)(t - seg_prefix[clo]) * S;
         const uint64_t len = end > off ? (end - off < S ? end - off : S) : 0;
         uint32_t st[4];
-        md5::digest_global(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
+        md5::digest_global<CRYSTAL_FMA_SEGMENTS>(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
         store_digest16(chunk_digest_area(X, cap) + 16ull * t, st);
     }
 }
@@ -481,11 +492,15 @@ __global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B
         for (uint32_t c = threadIdx.x; c < n_chunks; c += blockDim.x) {
             const uint32_t s0 = seg_prefix[c], s1 = seg_prefix[c + 1];
             uint32_t st[4];
-            md5::digest_global(dig + 16ull * s0, 16ull * (s1 - s0), st, one);
+            md5::digest_global<CRYSTAL_FMA_OUTER>(dig + 16ull * s0, 16ull * (s1 - s0), st, one);
             store_digest(out_dig + 16ull * c, st);
         }
     }
 }
+
+// ---- the dummy kernel of the overhead experiment ----------------------------
+
+__global__ void k_nop() {}
 
 // ---- launch geometry -----------------------------------------------------------
 
@@ -531,6 +546,11 @@ int launched(int kernels) {
 }
 
 }  // namespace
+
+int launch_nop(cudaStream_t s) {
+    k_nop<<<1, 32, 0, s>>>();
+    return launched(1);
+}
 
 int launch_direct_segments(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
@@ -710,5 +730,20 @@ int crystal_launch_batch(const crystal_batch* b, void* stream) {
 }
 
 uint64_t crystal_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
+
+int crystal_direct_job(const void* h_in, void* d_in, uint64_t in_size, void* h_out, const void* d_out,
+                       uint64_t out_size, void* stream) {
+    if ((in_size && (!h_in || !d_in)) || (out_size && (!h_out || !d_out))) return CRYSTAL_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (in_size && cudaMemcpyAsync(d_in, h_in, in_size, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return CRYSTAL_EDEVICE;
+    if (launch_nop(s) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
+    if (out_size && cudaMemcpyAsync(h_out, d_out, out_size, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CRYSTAL_EDEVICE;
+    // poll for completion, as the runtime's master thread does
+    cudaError_t e;
+    while ((e = cudaStreamQuery(s)) == cudaErrorNotReady) std::this_thread::yield();
+    return e == cudaSuccess ? CRYSTAL_OK : CRYSTAL_EDEVICE;
+}
 
 }  // extern "C"

@@ -64,7 +64,7 @@ __device__ __forceinline__ uint32_t add_on_fma(uint32_t x, uint32_t one, uint32_
 // One step: b' = b + ((a + f(b,c,d) + X[k] + T[i]) <<< s), then the register
 // names rotate (a, b, c, d) <- (d, b', b, c).  The sum not involving b is
 // formed first so the dependent chain through b is f -> add -> rotate -> add.
-template <int I>
+template <int I, bool FMA = true>
 __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d,
                                      const uint32_t (&X)[16], uint32_t one) {
     uint32_t f;
@@ -78,7 +78,12 @@ __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint
         f = c ^ (b | ~d);               // I
     }
     const uint32_t pre = a + (kT(I) + X[kWord(I)]);
-    const uint32_t t = add_on_fma(f, one, pre);
+    uint32_t t;
+    if constexpr (FMA) {
+        t = add_on_fma(f, one, pre);
+    } else {
+        t = pre + f;
+    }
     const uint32_t nb = b + rotl(t, kRot(I));
     a = d;
     d = c;
@@ -86,23 +91,27 @@ __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint
     b = nb;
 }
 
-template <int... I>
+template <bool FMA, int... I>
 __device__ __forceinline__ void steps_seq(std::integer_sequence<int, I...>, uint32_t& a, uint32_t& b,
                                           uint32_t& c, uint32_t& d, const uint32_t (&X)[16], uint32_t one) {
-    (step<I>(a, b, c, d, X, one), ...);
+    (step<I, FMA>(a, b, c, d, X, one), ...);
 }
 
-// The first N steps of the compression function.
-template <int N>
+// The first N steps of the compression function.  FMA: the round-function
+// add goes to the FMA pipe (more throughput when many chains share the ALU
+// pipe); without it every add stays on the ALU pipe (lower latency for a
+// single chain).
+template <int N, bool FMA = true>
 __device__ __forceinline__ void steps(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d,
                                       const uint32_t (&X)[16], uint32_t one) {
-    steps_seq(std::make_integer_sequence<int, N>{}, a, b, c, d, X, one);
+    steps_seq<FMA>(std::make_integer_sequence<int, N>{}, a, b, c, d, X, one);
 }
 
 // Full compression of one 16-word block into the chaining state.
+template <bool FMA = true>
 __device__ __forceinline__ void compress(uint32_t (&st)[4], const uint32_t (&X)[16], uint32_t one) {
     uint32_t a = st[0], b = st[1], c = st[2], d = st[3];
-    steps<64>(a, b, c, d, X, one);
+    steps<64, FMA>(a, b, c, d, X, one);
     st[0] += a;
     st[1] += b;
     st[2] += c;
@@ -140,6 +149,7 @@ __device__ __forceinline__ uint32_t ldg32(const uint32_t* p) { return __ldg(p); 
 // MD5 of len bytes at p (any alignment) in global memory; the digest words
 // (A, B, C, D) land in st.  Bytes outside [p, p + len) are read only inside
 // aligned 16-byte blocks that also hold a byte of the message, and never used.
+template <bool FMA = true>
 __device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, uint32_t (&st)[4], uint32_t one) {
     init(st);
     const uint64_t addr = reinterpret_cast<uint64_t>(p);
@@ -166,7 +176,7 @@ __device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, ui
 #pragma unroll
                 for (int v = 0; v < 4; ++v) nx[v] = ldg_stream16(q + 16 * v);
             }
-            compress(st, X, one);
+            compress<FMA>(st, X, one);
         }
     } else {
         // Any other alignment: five aligned 16-byte loads cover the block (each
@@ -205,7 +215,7 @@ __device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, ui
             for (int k = 0; k < 17; ++k) y[k] = (wq & 2) ? y1[k + 2] : y1[k];
 #pragma unroll
             for (int k = 0; k < 16; ++k) X[k] = __funnelshift_r(y[k], y[k + 1], sh);
-            compress(st, X, one);
+            compress<FMA>(st, X, one);
         }
     }
     // Tail: rem < 64 bytes, then 0x80, zeros, 64-bit bit length.
@@ -233,14 +243,14 @@ __device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, ui
     if (rem < 56) {
         X[14] = (uint32_t)bits;
         X[15] = (uint32_t)(bits >> 32);
-        compress(st, X, one);
+        compress<FMA>(st, X, one);
     } else {
-        compress(st, X, one);
+        compress<FMA>(st, X, one);
 #pragma unroll
         for (int k = 0; k < 14; ++k) X[k] = 0;
         X[14] = (uint32_t)bits;
         X[15] = (uint32_t)(bits >> 32);
-        compress(st, X, one);
+        compress<FMA>(st, X, one);
     }
 }
 

@@ -43,6 +43,12 @@ uint64_t now_ns() {
 
 enum TaskState : int { T_IDLE = 0, T_OUTSTANDING = 1, T_RUNNING = 2, T_DONE = 3 };
 
+// Short polling windows before a thread blocks (the master when it runs out
+// of work, a waiter before it sleeps): a thread wake-up costs tens of
+// microseconds, comparable to a small job.
+constexpr uint64_t kIdleSpinNs = 200000;
+constexpr uint64_t kWaitSpinNs = 200000;
+
 struct Slot {
     cudaStream_t stream = nullptr;
     bool own_stream = false;  // slots beyond the first n_streams share a stream
@@ -77,7 +83,7 @@ struct crystal_task {
     crystal_hash_params params{};
     crystal_callback cb = nullptr;
     void* user = nullptr;
-    int state = T_IDLE;
+    std::atomic<int> state{T_IDLE};  // written under the context lock; read lock-free by waiters
     int status = CRYSTAL_EINVAL;
     bool submitted_once = false;
     bool release_in_callback = false;
@@ -109,6 +115,7 @@ struct crystal_ctx {
     bool accepting = true;
     uint64_t seq = 0;
 
+    std::atomic<uint64_t> n_outstanding{0};  // mirrors outstanding.size() for the idle spin
     std::atomic<uint64_t> jobs_completed{0};
     std::atomic<uint64_t> batches{0};
     uint64_t n_running_jobs = 0;
@@ -299,7 +306,10 @@ int issue(crystal_ctx* c, Slot& s) {
                 return CRYSTAL_EDEVICE;
         }
     } else {
+        // only dummy jobs: the "dummy kernel with insignificant execution
+        // time" of the overhead experiment (Section 5.1)
         s.h_desc->status = 0;
+        if (launch_nop(st) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     }
     for (crystal_task* t : s.tasks) {
         if (t->out_size && cudaMemcpyAsync(t->h_out, t->d_out, t->out_size, cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -363,6 +373,7 @@ bool take_batch(crystal_ctx* c, Slot& s) {
         crystal_task* t = c->outstanding.front();
         if (!s.tasks.empty() && bytes + t->in_size > c->max_bytes) break;
         c->outstanding.pop_front();
+        c->n_outstanding.fetch_sub(1);
         bytes += t->in_size;
         t->state = T_RUNNING;
         s.tasks.push_back(t);
@@ -396,6 +407,7 @@ void master_loop(crystal_ctx* c) {
         if (c->stop && !c->outstanding.empty()) {
             std::vector<crystal_task*> cancel(c->outstanding.begin(), c->outstanding.end());
             c->outstanding.clear();
+            c->n_outstanding.store(0);
             for (crystal_task* t : cancel) t->state = T_RUNNING;  // callbacks may release it
             lk.unlock();
             for (crystal_task* t : cancel) {
@@ -457,7 +469,14 @@ void master_loop(crystal_ctx* c) {
         if (c->stop && c->running.empty() && c->outstanding.empty()) break;
         if (progressed) continue;
         if (c->running.empty()) {
-            c->cv_master.wait(lk);
+            // idle: poll for new jobs for a short while before sleeping, so a
+            // job submitted soon after is dispatched without a thread wake-up
+            lk.unlock();
+            const uint64_t t0 = now_ns();
+            while (c->n_outstanding.load(std::memory_order_relaxed) == 0 && now_ns() - t0 < kIdleSpinNs)
+                std::this_thread::yield();
+            lk.lock();
+            if (c->outstanding.empty() && c->running.empty() && !c->stop) c->cv_master.wait(lk);
         } else {
             // poll the running slots (Section 4.1: completion is found by polling)
             lk.unlock();
@@ -732,6 +751,7 @@ int crystal_task_submit(crystal_task* t, int kind, const crystal_hash_params* pa
         t->t_submit = now_ns();
         t->t_dispatch = t->t_done = 0;
         c->outstanding.push_back(t);
+        c->n_outstanding.fetch_add(1);
     }
     c->cv_master.notify_one();
     return CRYSTAL_OK;
@@ -806,6 +826,7 @@ int crystal_task_submit_many(crystal_task* const* tasks, uint32_t n, int kind, c
             t->t_dispatch = t->t_done = 0;
             c->outstanding.push_back(t);
         }
+        c->n_outstanding.fetch_add(n);
     }
     c->cv_master.notify_one();
     return CRYSTAL_OK;
@@ -856,6 +877,11 @@ int crystal_task_wait(crystal_task* t, int64_t timeout_ns) {
     if (!t) return CRYSTAL_EINVAL;
     crystal_ctx* c = t->ctx;
     if (tl_callback_ctx == c) return CRYSTAL_EINVAL;
+    {
+        const uint64_t spin = timeout_ns >= 0 && (uint64_t)timeout_ns < kWaitSpinNs ? (uint64_t)timeout_ns : kWaitSpinNs;
+        const uint64_t t0 = now_ns();
+        while (t->state.load() != T_DONE && now_ns() - t0 < spin) std::this_thread::yield();
+    }
     std::unique_lock<std::mutex> lk(c->mu);
     if (!t->submitted_once) return CRYSTAL_EINVAL;
     auto done = [t] { return t->state == T_DONE; };
