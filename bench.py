@@ -675,17 +675,23 @@ def run_overhead(args, ws, rank, local):
                         "crystal_direct_job")
                 if i >= 5:
                     raw.append(time.perf_counter() - t0)
-            fw = []
+            fw, disp, run, ret = [], [], [], []
             for i in range(reps + 5):
                 t0 = time.perf_counter()
                 C.check(t.submit(C.CRYSTAL_KIND_NOP), "submit")
                 assert t.wait(10_000_000_000) == C.CRYSTAL_OK
+                t1 = time.perf_counter()
                 if i >= 5:
-                    fw.append(time.perf_counter() - t0)
+                    fw.append(t1 - t0)
+                    s_ns, d_ns, e_ns = t.timing()
+                    disp.append((d_ns - s_ns) / 1e3)
+                    run.append((e_ns - d_ns) / 1e3)
             t.release()
             r, f = float(np.median(raw)) * 1e6, float(np.median(fw)) * 1e6
             out[str(n)] = {"direct_us": round(r, 1), "framework_us": round(f, 1), "overhead_us": round(f - r, 1),
-                           "overhead_pct": round(100 * (f - r) / f, 1)}
+                           "overhead_pct": round(100 * (f - r) / f, 1),
+                           "submit_to_dispatch_us": round(float(np.median(disp)), 1),
+                           "dispatch_to_done_us": round(float(np.median(run)), 1)}
     print(json.dumps({"metric": "framework overhead per job (dummy kernel, equal bytes in and out)",
                       "unit": "us", "sizes": out, "reps": reps,
                       "paper_context": "slightly under 70 us per job on a 9800 GX2 host (Section 5.1)"}))

@@ -188,6 +188,14 @@ int crystal_task_submit(crystal_task* task, int kind, const crystal_hash_params*
 int crystal_task_submit_many(crystal_task* const* tasks, uint32_t n, int kind,
                              const crystal_hash_params* params, crystal_callback cb, void* user);
 
+/* Priority of the job's next submits (default 0).  The master thread takes
+ * outstanding jobs highest priority first and in submission order within a
+ * priority (all jobs at 0: the paper's FIFO, Section 4.2; priority-based
+ * scheduling is the extension its Section 7 names).  A deadline scheduler
+ * maps earlier deadlines to higher priorities.  Not while the job is queued
+ * or running. */
+int crystal_task_set_priority(crystal_task* task, int priority);
+
 /* job_query(), Figure 3: CRYSTAL_PENDING while queued or running, otherwise
  * the job's final status (CRYSTAL_OK, CRYSTAL_EOVERFLOW, CRYSTAL_EDEVICE,
  * CRYSTAL_ESHUTDOWN).  EINVAL for a job never submitted. */

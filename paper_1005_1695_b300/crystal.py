@@ -132,6 +132,7 @@ def load() -> ctypes.CDLL:
         "crystal_task_submit_many": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.c_int,
                                                     ctypes.POINTER(crystal_hash_params), crystal_callback, _vp]),
         "crystal_task_poll": (ctypes.c_int, [_vp]),
+        "crystal_task_set_priority": (ctypes.c_int, [_vp, ctypes.c_int]),
         "crystal_task_create_ex": (ctypes.c_int, [_vp, _u64, _u64, _u64, ctypes.c_uint32, ctypes.POINTER(_vp)]),
         "crystal_task_bind_input": (ctypes.c_int, [_vp, _vp, _u64]),
         "crystal_host_register": (ctypes.c_int, [_vp, _u64]),
@@ -246,6 +247,9 @@ class Task:
         cb = callback if callback is not None else crystal_callback()
         self._cb_keepalive = cb
         return load().crystal_task_submit(self.handle, kind, ctypes.byref(p) if p is not None else None, cb, user)
+
+    def set_priority(self, priority: int) -> int:
+        return load().crystal_task_set_priority(self.handle, priority)
 
     def poll(self) -> int:
         return load().crystal_task_poll(self.handle)

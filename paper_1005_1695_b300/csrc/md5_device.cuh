@@ -54,7 +54,8 @@ __device__ __forceinline__ uint32_t rotl(uint32_t x, int s) { return __funnelshi
 // integer ALU pipe.  On sm_103a the ALU pipe takes one warp instruction every
 // two cycles per scheduler and bounds this hash; moving the add that joins
 // the round function into the running sum to the FMA pipe was measured
-// faster (moving the other adds, or the rotate, was measured slower).
+// faster (moving the other adds, or the rotate, was measured slower in the
+// window kernel).
 __device__ __forceinline__ uint32_t add_on_fma(uint32_t x, uint32_t one, uint32_t y) {
     uint32_t d;
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(y));
@@ -77,11 +78,12 @@ __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint
     } else {
         f = c ^ (b | ~d);               // I
     }
-    const uint32_t pre = a + (kT(I) + X[kWord(I)]);
     uint32_t t;
     if constexpr (FMA) {
+        const uint32_t pre = a + (kT(I) + X[kWord(I)]);
         t = add_on_fma(f, one, pre);
     } else {
+        const uint32_t pre = a + (kT(I) + X[kWord(I)]);
         t = pre + f;
     }
     const uint32_t nb = b + rotl(t, kRot(I));

@@ -22,6 +22,8 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <functional>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -84,11 +86,46 @@ struct crystal_task {
     crystal_callback cb = nullptr;
     void* user = nullptr;
     std::atomic<int> state{T_IDLE};  // written under the context lock; read lock-free by waiters
+    int priority = 0;                 // higher is dispatched first (crystal_task_set_priority)
     int status = CRYSTAL_EINVAL;
     bool submitted_once = false;
     bool release_in_callback = false;
     uint64_t t_submit = 0, t_dispatch = 0, t_done = 0;
 };
+
+namespace {
+
+// The outstanding queue (Section 4.2): FIFO within a priority, higher
+// priorities first.  With every job at priority 0 it is the paper's FIFO.
+class OutstandingQueue {
+  public:
+    bool empty() const { return n_ == 0; }
+    size_t size() const { return n_; }
+    crystal_task* front() const { return q_.begin()->second.front(); }
+    void pop_front() {
+        auto it = q_.begin();
+        it->second.pop_front();
+        if (it->second.empty()) q_.erase(it);
+        --n_;
+    }
+    void push_back(crystal_task* t, int priority) {
+        q_[priority].push_back(t);
+        ++n_;
+    }
+    std::vector<crystal_task*> drain() {
+        std::vector<crystal_task*> all;
+        for (auto& kv : q_) all.insert(all.end(), kv.second.begin(), kv.second.end());
+        q_.clear();
+        n_ = 0;
+        return all;
+    }
+
+  private:
+    std::map<int, std::deque<crystal_task*>, std::greater<int>> q_;
+    size_t n_ = 0;
+};
+
+}  // namespace
 
 struct crystal_ctx {
     crystal_config cfg{};
@@ -107,7 +144,7 @@ struct crystal_ctx {
     std::mutex mu;
     std::condition_variable cv_master;
     std::condition_variable cv_done;
-    std::deque<crystal_task*> outstanding;
+    OutstandingQueue outstanding;
     std::deque<uint32_t> running;  // slot indices in dispatch order
     std::unordered_set<crystal_task*> tasks;
     std::thread master;
@@ -405,8 +442,7 @@ void master_loop(crystal_ctx* c) {
         }
         // cancellation on shutdown
         if (c->stop && !c->outstanding.empty()) {
-            std::vector<crystal_task*> cancel(c->outstanding.begin(), c->outstanding.end());
-            c->outstanding.clear();
+            std::vector<crystal_task*> cancel = c->outstanding.drain();
             c->n_outstanding.store(0);
             for (crystal_task* t : cancel) t->state = T_RUNNING;  // callbacks may release it
             lk.unlock();
@@ -432,7 +468,7 @@ void master_loop(crystal_ctx* c) {
             lk.lock();
             progressed = true;
         }
-        // dispatch: FIFO from the outstanding queue into free slots
+        // dispatch: from the outstanding queue (priority, then FIFO) into free slots
         while (!c->outstanding.empty()) {
             const uint32_t ns = (uint32_t)c->slots.size();
             uint32_t pick = ns;
@@ -750,7 +786,7 @@ int crystal_task_submit(crystal_task* t, int kind, const crystal_hash_params* pa
         t->release_in_callback = false;
         t->t_submit = now_ns();
         t->t_dispatch = t->t_done = 0;
-        c->outstanding.push_back(t);
+        c->outstanding.push_back(t, t->priority);
         c->n_outstanding.fetch_add(1);
     }
     c->cv_master.notify_one();
@@ -824,7 +860,7 @@ int crystal_task_submit_many(crystal_task* const* tasks, uint32_t n, int kind, c
             t->release_in_callback = false;
             t->t_submit = now;
             t->t_dispatch = t->t_done = 0;
-            c->outstanding.push_back(t);
+            c->outstanding.push_back(t, t->priority);
         }
         c->n_outstanding.fetch_add(n);
     }
@@ -862,6 +898,14 @@ int crystal_host_unregister(void* host) {
         cudaGetLastError();
         return CRYSTAL_EDEVICE;
     }
+    return CRYSTAL_OK;
+}
+
+int crystal_task_set_priority(crystal_task* t, int priority) {
+    if (!t) return CRYSTAL_EINVAL;
+    std::lock_guard<std::mutex> lk(t->ctx->mu);
+    if (t->state == T_OUTSTANDING || t->state == T_RUNNING) return CRYSTAL_EINVAL;
+    t->priority = priority;
     return CRYSTAL_OK;
 }
 

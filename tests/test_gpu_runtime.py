@@ -324,3 +324,36 @@ def test_bound_input_from_registered_memory(C, oracle_mod):
             assert t2.output()[:16] == oracle_mod.direct(src[:n], 4096)
     finally:
         C.host_unregister(src)
+
+
+def test_priority_jobs_overtake_queued_fifo_jobs(C):
+    """Sequential mode: while a long job runs, five low-priority jobs and then one
+    high-priority job are queued; the high one is dispatched next, the low
+    ones after it in submission order."""
+    with C.Context(max_in_bytes=64 << 20, max_out_bytes=8 << 20, device_pool_bytes=512 << 20,
+                   host_pool_bytes=256 << 20, flags=C.CRYSTAL_FLAG_NO_OVERLAP) as ctx:
+        n = 48 << 20
+        big = ctx.task_create(n, C.sliding_out_bytes(n, 1 << 14))
+        big.h_in[:] = 9
+        low = [ctx.task_create(4096, 16) for _ in range(5)]
+        high = ctx.task_create(4096, 16)
+        for t in low + [high]:
+            t.h_in[:] = 1
+        assert high.set_priority(5) == 0
+        assert big.submit(SLIDING) == 0
+        import time
+
+        deadline = time.time() + 5
+        while big.timing()[1] == 0 and time.time() < deadline:  # wait until the long job is dispatched
+            time.sleep(1e-5)
+        assert big.timing()[1] > 0
+        for t in low:
+            assert t.submit(DIRECT) == 0
+        assert high.submit(DIRECT) == 0
+        for t in [big, high] + low:
+            assert t.wait(60 * SEC) == 0
+        d_high = high.timing()[1]
+        d_low = [t.timing()[1] for t in low]
+        assert big.timing()[1] < d_high < min(d_low)
+        assert d_low == sorted(d_low)
+        assert high.set_priority(0) == 0
