@@ -8,6 +8,8 @@ sequential FIFO job loop.
 What each function restates:
 
 * :func:`md5` -- MD5 per RFC 1321 (padding, length, four rounds).
+* :func:`sha1` -- SHA-1 per FIPS 180-4 (the hash of the paper's experiments,
+  Section 5.2); kinds 3 and 4 are the SHA-1 forms of direct and sliding.
 * :func:`direct` -- direct hashing: MD5 over the concatenated per-segment MD5
   digests (StoreGPU's direct hashing, used in Section 5.2 of the paper).
 * :func:`sliding_bitmap`, :func:`chunk_ends`, :func:`task` -- sliding-window
@@ -35,6 +37,10 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 KIND_NOP = 0
 KIND_MD5_DIRECT = 1
 KIND_MD5_SLIDING = 2
+KIND_SHA1_DIRECT = 3
+KIND_SHA1_SLIDING = 4
+HASH_MD5 = 0
+HASH_SHA1 = 1
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -80,6 +86,18 @@ def _load():
             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
         ]
         lib.oracle_task.restype = ctypes.c_int
+        lib.oracle_sha1.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+        lib.oracle_sha1.restype = None
+        lib.oracle_direct_hash.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_void_p]
+        lib.oracle_direct_hash.restype = ctypes.c_int
+        lib.oracle_sliding_bitmap_hash.argtypes = [
+            ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+            ctypes.c_void_p,
+        ]
+        lib.oracle_sliding_bitmap_hash.restype = None
+        lib.oracle_digest_bytes.argtypes = [ctypes.c_int]
+        lib.oracle_digest_bytes.restype = ctypes.c_uint32
         _lib = lib
     return _lib
 
@@ -98,6 +116,22 @@ def md5(data) -> bytes:
     return bytes(out)
 
 
+def sha1(data) -> bytes:
+    """SHA-1 digest (20 bytes) of ``data`` (FIPS 180-4)."""
+    arr, p = _buf(data)
+    out = (ctypes.c_uint8 * 20)()
+    _load().oracle_sha1(p, arr.size, out)
+    return bytes(out)
+
+
+def digest_bytes(kind: int) -> int:
+    return 20 if kind in (KIND_SHA1_DIRECT, KIND_SHA1_SLIDING) else 16
+
+
+def hash_of(kind: int) -> int:
+    return HASH_SHA1 if kind in (KIND_SHA1_DIRECT, KIND_SHA1_SLIDING) else HASH_MD5
+
+
 def md5_table() -> List[int]:
     """The oracle's 64 sine-derived constants, for the closed-form pin."""
     out = (ctypes.c_uint32 * 64)()
@@ -109,21 +143,23 @@ def num_segments(n: int, seg_bytes: int) -> int:
     return int(_load().oracle_num_segments(n, seg_bytes))
 
 
-def direct(data, seg_bytes: int = 4096) -> bytes:
-    """Direct hash: MD5 over the concatenated MD5s of ``seg_bytes`` segments."""
+def direct(data, seg_bytes: int = 4096, hash: int = HASH_MD5) -> bytes:
+    """Direct hash: H over the concatenated H digests of ``seg_bytes``
+    segments (H = MD5 or SHA-1)."""
     arr, p = _buf(data)
-    out = (ctypes.c_uint8 * 16)()
-    if _load().oracle_direct(p, arr.size, seg_bytes, out) != 0:
+    out = (ctypes.c_uint8 * 20)()
+    if _load().oracle_direct_hash(hash, p, arr.size, seg_bytes, out) != 0:
         raise ValueError("oracle_direct failed")
-    return bytes(out)
+    return bytes(out)[:20 if hash == HASH_SHA1 else 16]
 
 
-def sliding_bitmap(data, window: int = 20, mask: int = 0x1FFF, target: int = 0x1FFF) -> np.ndarray:
+def sliding_bitmap(data, window: int = 20, mask: int = 0x1FFF, target: int = 0x1FFF,
+                   hash: int = HASH_MD5) -> np.ndarray:
     """Boundary bitmap, ``ceil(n/32)`` little-endian uint32 words."""
     arr, p = _buf(data)
     words = (arr.size + 31) // 32
     bm = np.zeros(max(words, 1), dtype=np.uint32)
-    _load().oracle_sliding_bitmap(p, arr.size, window, mask, target, bm.ctypes.data)
+    _load().oracle_sliding_bitmap_hash(hash, p, arr.size, window, mask, target, bm.ctypes.data)
     return bm[:words]
 
 
@@ -139,9 +175,10 @@ def chunk_ends(bitmap: np.ndarray, n: int, window: int) -> np.ndarray:
     return ends
 
 
-def sliding_out_bytes(n: int, max_chunks: int) -> int:
-    """Output-buffer bytes for a sliding job that can hold ``max_chunks`` records."""
-    return 8 + 4 * ((n + 31) // 32) + 20 * max_chunks
+def sliding_out_bytes(n: int, max_chunks: int, digest: int = 16) -> int:
+    """Output-buffer bytes for a sliding job that can hold ``max_chunks`` records
+    (``digest`` = 16 for MD5, 20 for SHA-1)."""
+    return 8 + 4 * ((n + 31) // 32) + (4 + digest) * max_chunks
 
 
 def task(kind: int, data, out_size: int, seg_bytes: int = 4096, window: int = 20,
@@ -157,7 +194,7 @@ def task(kind: int, data, out_size: int, seg_bytes: int = 4096, window: int = 20
     return int(st), out[:out_size].tobytes()
 
 
-def parse_sliding(out: bytes, n: int):
+def parse_sliding(out: bytes, n: int, digest: int = 16):
     """Split a sliding output buffer into (n_chunks, flags, bitmap, ends, digests)."""
     hdr = np.frombuffer(out[:8], dtype=np.uint32)
     n_chunks, flags = int(hdr[0]), int(hdr[1])
@@ -168,7 +205,7 @@ def parse_sliding(out: bytes, n: int):
     off = 8 + 4 * words
     ends = np.frombuffer(out[off:off + 4 * n_chunks], dtype=np.uint32)
     off += 4 * n_chunks
-    dig = np.frombuffer(out[off:off + 16 * n_chunks], dtype=np.uint8).reshape(n_chunks, 16)
+    dig = np.frombuffer(out[off:off + digest * n_chunks], dtype=np.uint8).reshape(n_chunks, digest)
     return n_chunks, flags, bm, ends, dig
 
 

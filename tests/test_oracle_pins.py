@@ -229,3 +229,72 @@ def test_run_tasks_fifo_and_pure(oracle_mod):
     assert res == list(reversed(res_rev))
     assert res[0][1] == direct_closed_form(jobs[0][1], 256)
     assert oracle_mod.run_tasks_parallel(jobs, 3) == res
+
+
+# ---- SHA-1 (the hash of the paper's own experiments) ------------------------
+
+@pytest.mark.parametrize("n", list(range(0, 201)))
+def test_sha1_every_length_to_200(oracle_mod, n):
+    x = _bytes(n + 5000, n)
+    assert oracle_mod.sha1(x) == hashlib.sha1(x).digest()
+
+
+@pytest.mark.parametrize("fill", [0x00, 0xFF])
+@pytest.mark.parametrize("n", [55, 56, 63, 64, 119, 120, 4096])
+def test_sha1_constant_bytes(oracle_mod, fill, n):
+    x = bytes([fill]) * n
+    assert oracle_mod.sha1(x) == hashlib.sha1(x).digest()
+
+
+def test_sha1_random_lengths(oracle_mod):
+    g = np.random.default_rng(77)
+    for k in range(4):
+        x = _bytes(600 + k, int(g.integers(1, 1 << 20)))
+        assert oracle_mod.sha1(x) == hashlib.sha1(x).digest()
+
+
+def sha1_direct_closed_form(x: bytes, S: int) -> bytes:
+    m = max(1, -(-len(x) // S))
+    return hashlib.sha1(b"".join(hashlib.sha1(x[i * S:(i + 1) * S]).digest() for i in range(m))).digest()
+
+
+@pytest.mark.parametrize("S", [64, 100, 4096])
+def test_sha1_direct_special_sizes(oracle_mod, S):
+    for n in [0, 1, S - 1, S, S + 1, 3 * S - 7, 16 * S]:
+        x = _bytes(n + 7 * S, n)
+        assert oracle_mod.direct(x, S, hash=oracle_mod.HASH_SHA1) == sha1_direct_closed_form(x, S), (n, S)
+
+
+@pytest.mark.parametrize("w", [1, 3, 20])
+@pytest.mark.parametrize("mask,target", [(0x0, 0x0), (0x3, 0x1), (0x1FFF, 0x1FFF)])
+def test_sha1_sliding_bruteforce_tiny(oracle_mod, w, mask, target):
+    for n in range(0, 49):
+        x = _bytes(3000 + n, n)
+        bits = [i for i in range(0, n - w + 1)
+                if (struct.unpack("<I", hashlib.sha1(x[i:i + w]).digest()[:4])[0] & mask) == target]
+        bm = oracle_mod.sliding_bitmap(x, w, mask, target, hash=oracle_mod.HASH_SHA1)
+        assert np.array_equal(bm, words_from_bits(bits, n)), (n, w, mask)
+
+
+def test_sha1_sliding_task_layout(oracle_mod):
+    n, w, mask, S = 4000, 20, 0x3F, 100
+    x = _bytes(21, n)
+    bits = [i for i in range(0, n - w + 1)
+            if (struct.unpack("<I", hashlib.sha1(x[i:i + w]).digest()[:4])[0] & mask) == mask]
+    ends = brute_ends(bits, n, w)
+    out_size = oracle_mod.sliding_out_bytes(n, len(ends), digest=20)
+    st, out = oracle_mod.task(oracle_mod.KIND_SHA1_SLIDING, x, out_size, window=w, mask=mask, target=mask,
+                              chunk_seg_bytes=S)
+    assert st == 0
+    cnt, flags, bm, e, dig = oracle_mod.parse_sliding(out, n, digest=20)
+    assert cnt == len(ends) and list(e) == ends and flags == 0
+    start = 0
+    for k, end in enumerate(ends):
+        assert dig[k].tobytes() == sha1_direct_closed_form(x[start:end], S)
+        start = end
+    st, out = oracle_mod.task(oracle_mod.KIND_SHA1_DIRECT, x, 20, seg_bytes=256)
+    assert st == 0 and out == sha1_direct_closed_form(x, 256)
+    # one record short: 24-byte records (4-byte end + 20-byte digest) must not fit
+    st, out = oracle_mod.task(oracle_mod.KIND_SHA1_SLIDING, x, oracle_mod.sliding_out_bytes(n, len(ends) - 1, 20),
+                              window=w, mask=mask, target=mask, chunk_seg_bytes=S)
+    assert st == 1 and oracle_mod.parse_sliding(out, n, digest=20)[:2] == (len(ends), 1)
