@@ -50,6 +50,12 @@ GB = 1e9
 # add; 19 of the 61 steps use one of the 5 data words.  Then the
 # feed-forward add, the mask and the compare.
 OPS_PER_WINDOW_W20 = 61 * 4 + 19 + 3
+# SHA-1 window (w = 20, one block, the first digest word needs all 80 steps):
+# per step a rotate of a, the 3-input round function, two 3-input adds (a<<<5,
+# f, e, constant, schedule word) and the rotate of b; from step 16 on the
+# schedule word costs two 3-input XORs and a rotate; then the feed-forward
+# add, the mask and the compare.
+OPS_PER_WINDOW_SHA1_W20 = 80 * 5 + 64 * 3 + 3
 SM_COUNT_B300 = 148
 INT_LANES_PER_SM = 128  # 4 schedulers x one 32-lane instruction per clock
 
@@ -255,14 +261,15 @@ def run_ours(args, ws, rank, local):
 
     U, N = args.units, args.unit_bytes
     p = C.params(window_bytes=20, mask=0x1FFF, target=0x1FFF, chunk_segment_bytes=4096)
-    out_size = C.sliding_out_bytes(N, args.max_chunks)
+    KIND = C.CRYSTAL_KIND_SHA1_SLIDING if args.hash == "sha1" else C.CRYSTAL_KIND_MD5_SLIDING
+    ops_per_window = OPS_PER_WINDOW_SHA1_W20 if args.hash == "sha1" else OPS_PER_WINDOW_W20
+    out_size = C.sliding_out_bytes(N, args.max_chunks, KIND)
     host = sliding_workload(rank_seed(args.seed, rank), U, N)
     total_bytes = U * N
 
     # ---- value: inputs resident in HBM, kernel chain through the C ABI ----
     d_in = torch.from_numpy(host).to(dev)
-    batch = C.DeviceBatch(d_in, [u * N for u in range(U)], [N] * U, [C.CRYSTAL_KIND_MD5_SLIDING] * U, p,
-                          out_sizes=[out_size] * U)
+    batch = C.DeviceBatch(d_in, [u * N for u in range(U)], [N] * U, [KIND] * U, p, out_sizes=[out_size] * U)
     desc_host = torch.from_numpy(batch.host_desc).pin_memory()
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(device=dev)
@@ -308,7 +315,7 @@ def run_ours(args, ws, rank, local):
 
     # ---- e2e: job API, pinned host buffers, copies inside the timed region ----
     if "e2e" in args.legs:
-        pool_dev = int(total_bytes + U * (out_size + C.scratch_bytes(2, N, out_size, p) + 4096) + (64 << 20))
+        pool_dev = int(total_bytes + U * (out_size + C.scratch_bytes(KIND, N, out_size, p) + 4096) + (64 << 20))
         pool_host = int(total_bytes + U * (out_size + 4096) + (16 << 20))
         ctx = C.Context(max_in_bytes=N, max_out_bytes=out_size, device_pool_bytes=pool_dev,
                         host_pool_bytes=pool_host, n_streams=args.streams, max_batch_jobs=args.batch_jobs,
@@ -319,7 +326,7 @@ def run_ours(args, ws, rank, local):
             t.h_in[:] = host[u * N:(u + 1) * N]
 
         def e2e_step():
-            st = ctx.submit_many(tasks, C.CRYSTAL_KIND_MD5_SLIDING, p)
+            st = ctx.submit_many(tasks, KIND, p)
             assert st == C.CRYSTAL_OK, st
             for t in tasks:
                 s = t.wait(60_000_000_000)
@@ -332,7 +339,7 @@ def run_ours(args, ws, rank, local):
         got_dev = batch.outputs()
         for u in range(0, U, max(1, U // 16)):
             n_chunks = int.from_bytes(got_dev[u][:4], "little")
-            used = 8 + 4 * (N // 32) + 20 * n_chunks
+            used = 8 + 4 * (N // 32) + (4 + C.digest_size(KIND)) * n_chunks
             assert tasks[u].output()[:used] == got_dev[u][:used], "job output differs from device batch output"
         lat = []
         launches1 = C.kernel_launches()
@@ -366,21 +373,21 @@ def run_ours(args, ws, rank, local):
     # ---- roofline of the window kernel ----
     windows = U * (N - 20 + 1)
     win_avg_s = float(np.mean(win_ms)) / 1e3
-    achieved = windows * OPS_PER_WINDOW_W20 / win_avg_s / 1e12
+    achieved = windows * ops_per_window / win_avg_s / 1e12
     peaks = _peaks()
     traffic = None
-    if _kernel_sources_hash() == WINDOW_TRAFFIC_SOURCES and N == 1 << 20:
+    if _kernel_sources_hash() == WINDOW_TRAFFIC_SOURCES and N == 1 << 20 and args.hash == "md5":
         traffic = round(WINDOW_TRAFFIC_PER_UNIT * U)
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak = SM_COUNT_B300 * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
-    alu_bound_gbs = peak * 1e12 / OPS_PER_WINDOW_W20  # windows/s = bytes/s
+    alu_bound_gbs = peak * 1e12 / ops_per_window  # windows/s = bytes/s
     e2e_bound = min(h2d * GB, alu_bound_gbs, d2h * GB * total_bytes / (U * out_size)) / GB
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"sliding-window MD5, {U} units x {N // 1024} KiB, w=20, "
+        "config": {"workload": f"sliding-window {args.hash.upper()}, {U} units x {N // 1024} KiB, w=20, "
                                "mask=target=0x1FFF, chunk direct hash S=4 KiB",
                    "units_per_gpu": U, "unit_bytes": N, "window": 20, "mask": 0x1FFF, "target": 0x1FFF,
                    "chunk_segment_bytes": 4096, "content": "50% repeated 8 KiB blocks from a pool of 64",
@@ -390,7 +397,7 @@ def run_ours(args, ws, rank, local):
         "roofline": {"bound": "alu", "kernel": "k_sliding_windows", "achieved": round(achieved, 3),
                      "peak": round(peak, 3), "unit": "Tops/s (int32)", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
-                     "ops_per_window": OPS_PER_WINDOW_W20, "windows_per_launch": windows,
+                     "ops_per_window": ops_per_window, "windows_per_launch": windows,
                      "avg_launch_ms": round(win_avg_s * 1e3, 4),
                      "peak_basis": f"{SM_COUNT_B300} SMs x {INT_LANES_PER_SM} int32 lanes/clk x {sm_max:.0f} MHz"},
         "e2e": None if e2e_value is None else {
@@ -743,6 +750,8 @@ def main():
     ap.add_argument("--cpu-units", type=int, default=0, help="oracle sample units (0: 4 per core, <= 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="value,e2e", help="value (device-resident) and/or e2e (job API)")
+    ap.add_argument("--hash", default="md5", choices=["md5", "sha1"],
+                    help="hash of the sliding workload (the headline is MD5)")
     ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined", "serving", "batched", "overhead",
                              "streamlen"])
     ap.add_argument("--sizes", default="4096,65536,1048576,16777216,67108864")

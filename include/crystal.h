@@ -48,9 +48,11 @@ enum {
 
 /* ---- job kinds (the kernel_func of Figure 2, chosen by id) -------------- */
 enum {
-    CRYSTAL_KIND_NOP = 0,         /* dummy kernel of Section 5.1: copy in, empty kernel, copy out */
-    CRYSTAL_KIND_MD5_DIRECT = 1,  /* direct hashing (Section 5.2, Figure 6) */
-    CRYSTAL_KIND_MD5_SLIDING = 2  /* sliding-window hashing (Section 2.2, content-addressable storage) */
+    CRYSTAL_KIND_NOP = 0,          /* dummy kernel of Section 5.1: copy in, empty kernel, copy out */
+    CRYSTAL_KIND_MD5_DIRECT = 1,   /* direct hashing (Section 5.2, Figure 6) */
+    CRYSTAL_KIND_MD5_SLIDING = 2,  /* sliding-window hashing (Section 2.2, content-addressable storage) */
+    CRYSTAL_KIND_SHA1_DIRECT = 3,  /* the same with SHA-1 (FIPS 180-4), the hash of Section 5.2's runs */
+    CRYSTAL_KIND_SHA1_SLIDING = 4
 };
 
 /* ---- context flags ------------------------------------------------------ */
@@ -227,13 +229,17 @@ typedef struct crystal_stats {
 } crystal_stats;
 int crystal_get_stats(crystal_ctx* ctx, crystal_stats* out);
 
-/* Worst-case output size of a job: 16 for direct; for sliding the header,
- * the bitmap and one record per possible chunk (n - w + 2 of them, the
- * case mask = 0).  in_size for NOP.  0 on a bad kind. */
+/* Worst-case output size of a job: the digest size (16 MD5, 20 SHA-1) for
+ * direct; for sliding the header, the bitmap and one record per possible
+ * chunk (n - w + 2 of them, the case mask = 0).  in_size for NOP.  0 on a
+ * bad kind. */
 uint64_t crystal_out_bytes(int kind, uint64_t in_size, const crystal_hash_params* params);
 
-/* Output size of a sliding job with room for max_chunks chunk records. */
+/* Output size of an MD5 sliding job with room for max_chunks chunk records
+ * (20 bytes each), and of a sliding job of any kind (4 + digest bytes each;
+ * 0 for a kind that is not sliding). */
 uint64_t crystal_sliding_out_bytes(uint64_t in_size, uint64_t max_chunks);
+uint64_t crystal_out_bytes_for_chunks(int kind, uint64_t in_size, uint64_t max_chunks);
 
 /* Static text for a status code. */
 const char* crystal_strerror(int status);
@@ -252,12 +258,13 @@ int crystal_direct_job(const void* h_in, void* d_in, uint64_t in_size, void* h_o
                        uint64_t out_size, void* stream);
 
 /* ---- output layouts (what the kernels write) ----------------------------
- * direct  : 16-byte digest Direct(u, S) = MD5(MD5(seg_0) || ... || MD5(seg_{m-1})),
- *           m = max(1, ceil(n / S)); the last segment may be short.
+ * direct  : digest Direct(u, S) = H(H(seg_0) || ... || H(seg_{m-1})) of D bytes,
+ *           m = max(1, ceil(n / S)); the last segment may be short.  H is
+ *           MD5 (D = 16) or SHA-1 (D = 20) by kind.
  * sliding : u32 n_chunks | u32 flags | u32 bitmap[ceil(n/32)] |
- *           u32 chunk_end[n_chunks] | u8 digest[n_chunks][16]
+ *           u32 chunk_end[n_chunks] | u8 digest[n_chunks][D]
  *           bit i of the bitmap (word i/32, bit i%32) is set iff
- *           i <= n - w and (LE32(MD5(u[i, i+w))[0..3]) & mask) == target;
+ *           i <= n - w and (LE32(H(u[i, i+w))[0..3]) & mask) == target;
  *           chunk ends are the sorted set {i + w : bit i} U {n};
  *           digest[k] = Direct(u[end_{k-1}, end_k), chunk_segment_bytes),
  *           end_{-1} = 0.  If the records do not fit in out_size, flags bit 0
@@ -282,7 +289,7 @@ typedef struct crystal_unit {
     uint32_t out_cap;    /* output bytes available */
     uint32_t seg_bytes;  /* direct: S; sliding: chunk S */
     uint16_t window;     /* sliding: w */
-    uint16_t kind;       /* CRYSTAL_KIND_MD5_DIRECT or CRYSTAL_KIND_MD5_SLIDING */
+    uint16_t kind;       /* a direct or a sliding CRYSTAL_KIND_* (MD5 or SHA-1) */
     uint32_t mask, target;
     uint32_t seg_base;   /* sliding: written by the kernels (first chunk segment of
                             this unit among the batch's chunk segments) */
@@ -299,7 +306,10 @@ typedef struct crystal_batch {
     uint64_t sliding_tiles_w20; /* tiles of the sliding units with w = 20, which the
                                    planner places first */
     uint64_t chunk_segments;    /* written by the kernels: chunk segments of the batch */
-    uint64_t reserved[2];       /* header is 64 bytes */
+    uint64_t sliding_tiles_md5; /* tiles of the MD5 sliding units (w = 20 first, then other
+                                   windows); the SHA-1 sliding units follow */
+    uint64_t direct_segments_md5; /* segments of the MD5 direct units, which come before the
+                                     SHA-1 direct units (header is 64 bytes) */
     /* crystal_unit units[n_direct + n_sliding] follow */
 } crystal_batch;
 
@@ -317,10 +327,10 @@ uint64_t crystal_scratch_bytes(int kind, uint64_t n, uint64_t out_size, const cr
 /* Host-side planning of a batch in host memory (the header followed by the
  * unit records, units filled by the caller except work_begin and seg_base):
  * checks every unit (kinds in order, sizes, windows 1..55, out_cap large
- * enough, 16-byte aligned scratch), moves the sliding units with w = 20 in
- * front of the other sliding units (stable; each record keeps its own
- * pointers, so results do not depend on the order), fills work_begin and the
- * header's totals.  The buffer is then copied to the device as is.  Returns
+ * enough, 16-byte aligned scratch), orders the units (stable; each record
+ * keeps its own pointers, so results do not depend on the order): MD5 direct
+ * before SHA-1 direct; MD5 sliding with w = 20, other MD5 sliding, SHA-1
+ * sliding; fills work_begin and the header's totals.  The buffer is then copied to the device as is.  Returns
  * CRYSTAL_OK or CRYSTAL_EINVAL. */
 int crystal_batch_plan(crystal_batch* batch_host, uint32_t n_direct, uint32_t n_sliding);
 

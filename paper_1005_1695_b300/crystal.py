@@ -31,6 +31,14 @@ CRYSTAL_EDEVICE = -7
 CRYSTAL_KIND_NOP = 0
 CRYSTAL_KIND_MD5_DIRECT = 1
 CRYSTAL_KIND_MD5_SLIDING = 2
+CRYSTAL_KIND_SHA1_DIRECT = 3
+CRYSTAL_KIND_SHA1_SLIDING = 4
+DIRECT_KINDS = (CRYSTAL_KIND_MD5_DIRECT, CRYSTAL_KIND_SHA1_DIRECT)
+SLIDING_KINDS = (CRYSTAL_KIND_MD5_SLIDING, CRYSTAL_KIND_SHA1_SLIDING)
+
+
+def digest_size(kind: int) -> int:
+    return 20 if kind in (CRYSTAL_KIND_SHA1_DIRECT, CRYSTAL_KIND_SHA1_SLIDING) else 16
 
 CRYSTAL_FLAG_NO_POOL = 1
 CRYSTAL_FLAG_NO_OVERLAP = 2
@@ -146,6 +154,7 @@ def load() -> ctypes.CDLL:
         "crystal_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(crystal_stats)]),
         "crystal_out_bytes": (_u64, [ctypes.c_int, _u64, ctypes.POINTER(crystal_hash_params)]),
         "crystal_sliding_out_bytes": (_u64, [_u64, _u64]),
+        "crystal_out_bytes_for_chunks": (_u64, [ctypes.c_int, _u64, _u64]),
         "crystal_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "crystal_kernel_launches": (_u64, []),
         "crystal_direct_job": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _u64, _vp]),
@@ -186,8 +195,8 @@ def out_bytes(kind: int, in_size: int, p: Optional[crystal_hash_params] = None) 
     return int(load().crystal_out_bytes(kind, in_size, ctypes.byref(p) if p is not None else None))
 
 
-def sliding_out_bytes(in_size: int, max_chunks: int) -> int:
-    return int(load().crystal_sliding_out_bytes(in_size, max_chunks))
+def sliding_out_bytes(in_size: int, max_chunks: int, kind: int = CRYSTAL_KIND_MD5_SLIDING) -> int:
+    return int(load().crystal_out_bytes_for_chunks(kind, in_size, max_chunks))
 
 
 def scratch_bytes(kind: int, n: int, out_size: int, p: Optional[crystal_hash_params] = None) -> int:
@@ -383,12 +392,12 @@ class DeviceBatch:
         self.device = d_input.device
         self.kinds = list(kinds)
         self.sizes = [int(s) for s in sizes]
-        order = [i for i in range(n_units) if kinds[i] == CRYSTAL_KIND_MD5_DIRECT] + \
-                [i for i in range(n_units) if kinds[i] == CRYSTAL_KIND_MD5_SLIDING]
+        order = [i for i in range(n_units) if kinds[i] in DIRECT_KINDS] + \
+                [i for i in range(n_units) if kinds[i] in SLIDING_KINDS]
         if len(order) != n_units:
             raise ValueError("kinds must be direct or sliding")
         self.order = order
-        self.n_direct = sum(1 for k in kinds if k == CRYSTAL_KIND_MD5_DIRECT)
+        self.n_direct = sum(1 for k in kinds if k in DIRECT_KINDS)
         self.n_sliding = n_units - self.n_direct
         plist = per_unit_params or [p if p is not None else params()] * n_units
         self.params = plist
@@ -399,8 +408,8 @@ class DeviceBatch:
             pi = plist[i]
             if out_sizes is not None:
                 osz = int(out_sizes[i])
-            elif kinds[i] == CRYSTAL_KIND_MD5_DIRECT:
-                osz = 16
+            elif kinds[i] in DIRECT_KINDS:
+                osz = digest_size(kinds[i])
             else:
                 osz = L.crystal_out_bytes(kinds[i], self.sizes[i], ctypes.byref(pi))
             self.out_off[i], self.out_size[i] = o, osz
@@ -423,7 +432,7 @@ class DeviceBatch:
             u["out"] = base_out + self.out_off[i]
             u["scratch"] = base_scr + self.scr_off[i]
             u["out_cap"] = self.out_size[i]
-            direct = kinds[i] == CRYSTAL_KIND_MD5_DIRECT
+            direct = kinds[i] in DIRECT_KINDS
             u["seg_bytes"] = (pi.segment_bytes if direct else pi.chunk_segment_bytes) or 4096
             u["window"] = pi.window_bytes or 20
             u["mask"], u["target"], u["kind"] = pi.mask, pi.target, kinds[i]

@@ -26,6 +26,11 @@ inline crystal_unit* batch_units(crystal_batch* b) {
 
 constexpr uint32_t kMaxWindow = 55;  // a window message fits one MD5 block
 
+inline bool kind_is_direct(int k) { return k == CRYSTAL_KIND_MD5_DIRECT || k == CRYSTAL_KIND_SHA1_DIRECT; }
+inline bool kind_is_sliding(int k) { return k == CRYSTAL_KIND_MD5_SLIDING || k == CRYSTAL_KIND_SHA1_SLIDING; }
+inline bool kind_is_sha1(int k) { return k == CRYSTAL_KIND_SHA1_DIRECT || k == CRYSTAL_KIND_SHA1_SLIDING; }
+inline uint64_t digest_bytes_of(int k) { return kind_is_sha1(k) ? 20 : 16; }
+
 inline uint64_t segments_of(uint64_t n, uint64_t S) { return n == 0 ? 1 : (n + S - 1) / S; }
 inline uint64_t bitmap_words(uint64_t n) { return (n + 31) / 32; }
 inline uint64_t sliding_fixed_bytes(uint64_t n) { return 8 + 4 * bitmap_words(n); }

@@ -2,8 +2,8 @@
 //
 //   k_direct_segments  K1  one MD5 per segment of every direct unit
 //   k_direct_outer     K2  MD5 over each unit's concatenated segment digests
-//   k_sliding_windows  K3  MD5 of every w-byte window, boundary bitmap
-//                          (one instance for w = 20, one for any w in 1..55)
+//   k_sliding_windows  K3  digest of every w-byte window, boundary bitmap
+//                          (MD5 with w = 20, MD5 with any w in 1..55, SHA-1)
 //   k_sliding_chunks   K4  chunk ends from the bitmap, per-chunk segment table
 //   k_chunk_seg_scan   K4b where each unit's chunk segments start in the batch
 //   k_chunk_segments   K5a one MD5 per segment of every chunk
@@ -26,7 +26,9 @@
 
 #include "crystal.h"
 #include "crystal_internal.h"
+#include "digest_device.cuh"
 #include "md5_device.cuh"
+#include "sha1_device.cuh"
 
 namespace crystal {
 
@@ -75,16 +77,26 @@ __device__ __forceinline__ uint32_t owner_of(const crystal_unit* U, uint32_t cnt
     return lo;
 }
 
-__device__ __forceinline__ void store_digest(uint8_t* dst, const uint32_t (&st)[4]) {
-    uint32_t* d = reinterpret_cast<uint32_t*>(dst);  // 4-byte aligned by contract
-    d[0] = st[0];
-    d[1] = st[1];
-    d[2] = st[2];
-    d[3] = st[3];
+__device__ __forceinline__ bool is_sha1(const crystal_unit& X) {
+    return X.kind == CRYSTAL_KIND_SHA1_DIRECT || X.kind == CRYSTAL_KIND_SHA1_SLIDING;
 }
 
-__device__ __forceinline__ void store_digest16(uint8_t* dst, const uint32_t (&st)[4]) {
-    *reinterpret_cast<uint4*>(dst) = make_uint4(st[0], st[1], st[2], st[3]);
+// Digest bytes of a unit's hash, and bytes per chunk record (u32 end + digest).
+__device__ __forceinline__ uint32_t digest_bytes(const crystal_unit& X) { return is_sha1(X) ? 20u : 16u; }
+__device__ __forceinline__ uint32_t record_bytes(const crystal_unit& X) { return 4u + digest_bytes(X); }
+
+// Digest of [p, p + len) with the unit's hash, stored at dst (4-byte aligned).
+template <bool FMA>
+__device__ __forceinline__ void digest_to(const crystal_unit& X, const uint8_t* p, uint64_t len, uint8_t* dst,
+                                          uint32_t one) {
+    uint32_t st[5];
+    if (is_sha1(X)) {
+        digest_global<SHA1Hash, FMA>(p, len, st, one);
+        store_digest<SHA1Hash>(dst, st);
+    } else {
+        digest_global<MD5Hash, FMA>(p, len, st, one);
+        store_digest<MD5Hash>(dst, st);
+    }
 }
 
 __device__ __forceinline__ uint64_t num_segments(uint64_t n, uint32_t S) {
@@ -93,20 +105,25 @@ __device__ __forceinline__ uint64_t num_segments(uint64_t n, uint32_t S) {
 
 // ---- K1: segment digests of direct units ------------------------------------
 
+// One instance per hash: MD5 units are [0, direct_segments_md5) of the
+// segment space (the planner puts them first), SHA-1 units the rest.
+template <class H>
 __global__ void __launch_bounds__(kSegThreads, 5) k_direct_segments(crystal_batch* B, uint32_t one) {
     const uint32_t nd = B->n_direct;
-    const uint64_t total = B->direct_segments;
+    const bool sha = H::kWords == 5;
+    const uint64_t lo = sha ? B->direct_segments_md5 : 0;
+    const uint64_t hi = sha ? B->direct_segments : B->direct_segments_md5;
     const crystal_unit* U = units_of(B);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    for (uint64_t g = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < hi; g += stride) {
         const uint32_t u = owner_of(U, nd, g);
         const crystal_unit X = U[u];
         const uint64_t j = g - X.work_begin;
         const uint64_t off = j * X.seg_bytes;
         const uint64_t len = X.n > off ? (X.n - off < X.seg_bytes ? X.n - off : X.seg_bytes) : 0;
-        uint32_t st[4];
-        md5::digest_global<CRYSTAL_FMA_SEGMENTS>(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
-        store_digest16(reinterpret_cast<uint8_t*>(X.scratch) + 16 * j, st);
+        uint32_t st[5];
+        digest_global<H, CRYSTAL_FMA_SEGMENTS>(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
+        store_digest<H>(reinterpret_cast<uint8_t*>(X.scratch) + (uint64_t)H::kBytes * j, st);
     }
 }
 
@@ -118,9 +135,8 @@ __global__ void __launch_bounds__(kDigestThreads) k_direct_outer(crystal_batch* 
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nd; u += gridDim.x * blockDim.x) {
         const crystal_unit X = U[u];
         const uint64_t m = num_segments(X.n, X.seg_bytes);
-        uint32_t st[4];
-        md5::digest_global<CRYSTAL_FMA_OUTER>(reinterpret_cast<const uint8_t*>(X.scratch), 16 * m, st, one);
-        store_digest(reinterpret_cast<uint8_t*>(X.out), st);
+        digest_to<CRYSTAL_FMA_OUTER>(X, reinterpret_cast<const uint8_t*>(X.scratch), digest_bytes(X) * m,
+                                     reinterpret_cast<uint8_t*>(X.out), one);
     }
 }
 
@@ -166,7 +182,23 @@ __device__ __forceinline__ void window_block(const uint32_t* sw, uint32_t p, uin
     }
 }
 
-template <int W>
+// LE32 of digest bytes 0..3 of the one-block message X (MD5 layout: little-
+// endian words, bit length in word 14).  For SHA-1 the words are turned
+// big-endian and the length moved to word 15 first.
+template <class H>
+__device__ __forceinline__ uint32_t window_first_word(uint32_t (&X)[16], uint32_t w, uint32_t one) {
+    if constexpr (H::kWords == 5) {
+#pragma unroll
+        for (int k = 0; k < 14; ++k) X[k] = sha1::bswap(X[k]);
+        X[14] = 0;
+        X[15] = 8u * w;
+        return sha1::bswap(sha1::first_word_one_block(X));
+    } else {
+        return md5::first_word_one_block(X, one);
+    }
+}
+
+template <int W, class H>
 __device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t delta, uint32_t lim, uint32_t w,
                                                  uint32_t mask, uint32_t target, uint32_t one) {
     const uint32_t lane = threadIdx.x & 31;
@@ -177,7 +209,7 @@ __device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t de
         const uint32_t rel = warp * (32 * kWinPerThread) + r * 32 + lane;
         uint32_t X[16];
         window_block<W>(sw, rel + delta, w, X);
-        A[r] = md5::first_word_one_block(X, one);
+        A[r] = window_first_word<H>(X, w, one);
     }
     // ballots only after every window of the thread is hashed: a ballot per
     // window was measured 9% slower (each one is a warp-wide sync point)
@@ -229,8 +261,10 @@ __device__ __forceinline__ void stage_tile(uint32_t* sw, const crystal_unit& X, 
     for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) cp_async16(sw + 4 * v, a0 + 16ull * v);
 }
 
-// W = 20: tiles [0, sliding_tiles_w20), whose units all have w = 20 (the
-// planner puts them first); W = 0: the remaining tiles, any w in 1..55.
+// Instances (the planner orders the sliding units this way):
+//   <20, MD5>: tiles [0, sliding_tiles_w20), MD5 units with w = 20;
+//   <0, MD5>:  tiles [sliding_tiles_w20, sliding_tiles_md5), other MD5 units;
+//   <0, SHA1>: tiles [sliding_tiles_md5, sliding_tiles), SHA-1 units, any w.
 // The next tile's bytes are copied into the other half of a double buffer
 // while the current tile is hashed.
 // Resident CTAs per SM the window kernel is compiled for (sets its register
@@ -240,14 +274,14 @@ __device__ __forceinline__ void stage_tile(uint32_t* sw, const crystal_unit& X, 
 #define CRYSTAL_WIN_MIN_BLOCKS 8
 #endif
 
-template <int W>
-__global__ void __launch_bounds__(kWinThreads, CRYSTAL_WIN_MIN_BLOCKS) k_sliding_windows(crystal_batch* B,
-                                                                                          uint32_t one) {
+template <int W, class H, int MINB>
+__global__ void __launch_bounds__(kWinThreads, MINB) k_sliding_windows(crystal_batch* B, uint32_t one) {
     __shared__ __align__(16) uint32_t sw[2][kStageWords];
     const uint32_t ns = B->n_sliding;
     const crystal_unit* U = units_of(B) + B->n_direct;
-    const uint64_t lo = W == 20 ? 0 : B->sliding_tiles_w20;
-    const uint64_t hi = W == 20 ? B->sliding_tiles_w20 : B->sliding_tiles;
+    const bool sha = H::kWords == 5;
+    const uint64_t lo = sha ? B->sliding_tiles_md5 : (W == 20 ? 0 : B->sliding_tiles_w20);
+    const uint64_t hi = sha ? B->sliding_tiles : (W == 20 ? B->sliding_tiles_w20 : B->sliding_tiles_md5);
     uint64_t t = lo + blockIdx.x;
     if (t >= hi) return;
     uint32_t u = owner_of(U, ns, t);
@@ -274,7 +308,13 @@ __global__ void __launch_bounds__(kWinThreads, CRYSTAL_WIN_MIN_BLOCKS) k_sliding
         const uint64_t left = X.n - base;
         const uint32_t lim = left < (uint64_t)(2 * kTile) ? (uint32_t)left : (uint32_t)(2 * kTile);
         const uint32_t w = W > 0 ? (uint32_t)W : (uint32_t)X.window;
-        const uint32_t mine = tile_windows<W>(sw[buf], delta, lim, w, X.mask, X.target, one);
+        uint32_t mine;
+        if (W == 0 && H::kWords == 5 && w == 20) {
+            // SHA-1 units with the common window: padding words fold at compile time
+            mine = tile_windows<20, H>(sw[buf], delta, lim, 20u, X.mask, X.target, one);
+        } else {
+            mine = tile_windows<W, H>(sw[buf], delta, lim, w, X.mask, X.target, one);
+        }
         const uint32_t lane = threadIdx.x & 31;
         if (lane < (uint32_t)kWinPerThread) {
             const uint64_t word = (base >> 5) + (threadIdx.x >> 5) * kWinPerThread + lane;
@@ -336,7 +376,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch*
             }
             continue;
         }
-        const uint64_t cap = (X.out_cap - fixed) / 20;
+        const uint64_t cap = (X.out_cap - fixed) / record_bytes(X);
         // pass 1: boundary count per contiguous word range
         const uint64_t per = (words + kChunkThreads - 1) / kChunkThreads;
         const uint64_t lo = threadIdx.x * per;
@@ -453,7 +493,7 @@ __global__ void __launch_bounds__(kDigestThreads, 2) k_chunk_segments(crystal_ba
         const uint64_t fixed = 8 + 4 * words;
         const uint32_t* hdr = reinterpret_cast<const uint32_t*>(X.out);
         const uint32_t n_chunks = hdr[0];
-        const uint64_t cap = (X.out_cap - fixed) / 20;
+        const uint64_t cap = (X.out_cap - fixed) / record_bytes(X);
         const uint32_t* ends = hdr + 2 + words;
         const uint32_t* seg_prefix = reinterpret_cast<const uint32_t*>(X.scratch);
         uint32_t clo = 0, chi = n_chunks;  // chunk: last with seg_prefix[c] <= t
@@ -466,9 +506,8 @@ __global__ void __launch_bounds__(kDigestThreads, 2) k_chunk_segments(crystal_ba
         const uint64_t end = ends[clo];
         const uint64_t off = start + (uint64_t)(t - seg_prefix[clo]) * S;
         const uint64_t len = end > off ? (end - off < S ? end - off : S) : 0;
-        uint32_t st[4];
-        md5::digest_global<CRYSTAL_FMA_SEGMENTS>(reinterpret_cast<const uint8_t*>(X.in) + off, len, st, one);
-        store_digest16(chunk_digest_area(X, cap) + 16ull * t, st);
+        digest_to<CRYSTAL_FMA_SEGMENTS>(X, reinterpret_cast<const uint8_t*>(X.in) + off, len,
+                                        chunk_digest_area(X, cap) + (uint64_t)digest_bytes(X) * t, one);
     }
 }
 
@@ -485,15 +524,14 @@ __global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B
         uint32_t* hdr = reinterpret_cast<uint32_t*>(X.out);
         if (hdr[1] & 1u) continue;
         const uint32_t n_chunks = hdr[0];
-        const uint64_t cap = (X.out_cap - fixed) / 20;
+        const uint64_t cap = (X.out_cap - fixed) / record_bytes(X);
         const uint32_t* seg_prefix = reinterpret_cast<const uint32_t*>(X.scratch);
         const uint8_t* dig = chunk_digest_area(X, cap);
         uint8_t* out_dig = reinterpret_cast<uint8_t*>(hdr + 2 + words + n_chunks);
+        const uint64_t D = digest_bytes(X);
         for (uint32_t c = threadIdx.x; c < n_chunks; c += blockDim.x) {
             const uint32_t s0 = seg_prefix[c], s1 = seg_prefix[c + 1];
-            uint32_t st[4];
-            md5::digest_global<CRYSTAL_FMA_OUTER>(dig + 16ull * s0, 16ull * (s1 - s0), st, one);
-            store_digest(out_dig + 16ull * c, st);
+            digest_to<CRYSTAL_FMA_OUTER>(X, dig + D * s0, D * (s1 - s0), out_dig + D * c, one);
         }
     }
 }
@@ -504,9 +542,19 @@ __global__ void k_nop() {}
 
 // ---- launch geometry -----------------------------------------------------------
 
+// The three window-kernel instances (SHA-1 needs more registers for its
+// 16-word schedule: four CTAs per SM).
+constexpr auto kWin20 = k_sliding_windows<20, MD5Hash, CRYSTAL_WIN_MIN_BLOCKS>;
+constexpr auto kWinAny = k_sliding_windows<0, MD5Hash, CRYSTAL_WIN_MIN_BLOCKS>;
+#ifndef CRYSTAL_SHA1_WIN_MIN_BLOCKS
+#define CRYSTAL_SHA1_WIN_MIN_BLOCKS 4
+#endif
+constexpr auto kWinSha1 = k_sliding_windows<0, SHA1Hash, CRYSTAL_SHA1_WIN_MIN_BLOCKS>;
+
 struct Geometry {
     int sms = 0;
-    int seg_blocks = 0, outer_blocks = 0, win20_blocks = 0, win_blocks = 0, unit_blocks = 0, digest_blocks = 0;
+    int seg_blocks = 0, seg_sha1_blocks = 0, outer_blocks = 0, win20_blocks = 0, win_blocks = 0, win_sha1_blocks = 0, unit_blocks = 0,
+        digest_blocks = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -525,9 +573,11 @@ const Geometry* geometry() {
     std::call_once(g_geom_once[dev], [dev] {
         Geometry g;
         cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev);
-        g.seg_blocks = g.sms * resident((const void*)k_direct_segments, kSegThreads);
-        g.win20_blocks = g.sms * resident((const void*)k_sliding_windows<20>, kWinThreads);
-        g.win_blocks = g.sms * resident((const void*)k_sliding_windows<0>, kWinThreads);
+        g.seg_blocks = g.sms * resident((const void*)k_direct_segments<MD5Hash>, kSegThreads);
+        g.seg_sha1_blocks = g.sms * resident((const void*)k_direct_segments<SHA1Hash>, kSegThreads);
+        g.win20_blocks = g.sms * resident((const void*)kWin20, kWinThreads);
+        g.win_blocks = g.sms * resident((const void*)kWinAny, kWinThreads);
+        g.win_sha1_blocks = g.sms * resident((const void*)kWinSha1, kWinThreads);
         g.digest_blocks = g.sms * resident((const void*)k_chunk_segments, kDigestThreads);
         g.outer_blocks = g.sms * 2;
         g.unit_blocks = g.sms * 2;
@@ -555,8 +605,9 @@ int launch_nop(cudaStream_t s) {
 int launch_direct_segments(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
     if (!g) return CRYSTAL_EDEVICE;
-    k_direct_segments<<<g->seg_blocks, kSegThreads, 0, s>>>(b, g_one);
-    return launched(1);
+    k_direct_segments<MD5Hash><<<g->seg_blocks, kSegThreads, 0, s>>>(b, g_one);
+    k_direct_segments<SHA1Hash><<<g->seg_sha1_blocks, kSegThreads, 0, s>>>(b, g_one);
+    return launched(2);
 }
 
 int launch_direct_outer(crystal_batch* b, cudaStream_t s) {
@@ -569,9 +620,10 @@ int launch_direct_outer(crystal_batch* b, cudaStream_t s) {
 int launch_sliding_windows(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
     if (!g) return CRYSTAL_EDEVICE;
-    k_sliding_windows<20><<<g->win20_blocks, kWinThreads, 0, s>>>(b, g_one);
-    k_sliding_windows<0><<<g->win_blocks, kWinThreads, 0, s>>>(b, g_one);
-    return launched(2);
+    kWin20<<<g->win20_blocks, kWinThreads, 0, s>>>(b, g_one);
+    kWinAny<<<g->win_blocks, kWinThreads, 0, s>>>(b, g_one);
+    kWinSha1<<<g->win_sha1_blocks, kWinThreads, 0, s>>>(b, g_one);
+    return launched(3);
 }
 
 int launch_sliding_chunks(crystal_batch* b, cudaStream_t s) {
@@ -636,12 +688,13 @@ __global__ void k_noalloc_describe(crystal_batch* B, uint64_t in, uint64_t unit_
         B->n_direct = n_units;
         B->n_sliding = 0;
         B->direct_segments = m * n_units;
+        B->direct_segments_md5 = m * n_units;
         B->sliding_tiles = 0;
         B->window_max = 0;
         B->status = 0;
         B->sliding_tiles_w20 = 0;
         B->chunk_segments = 0;
-        B->reserved[0] = B->reserved[1] = 0;
+        B->sliding_tiles_md5 = 0;
     }
 }
 
@@ -680,7 +733,7 @@ int crystal_md5_direct_noalloc(const void* d_in, uint64_t unit_bytes, uint32_t n
     const int blocks = (int)((n_units + threads - 1) / threads < 1024 ? (n_units + threads - 1) / threads : 1024);
     k_noalloc_describe<<<blocks, threads, 0, s>>>(B, reinterpret_cast<uint64_t>(d_in), unit_bytes, n_units,
                                                    segment_bytes, reinterpret_cast<uint64_t>(d_digests), digests);
-    k_direct_segments<<<g->seg_blocks, kSegThreads, 0, s>>>(B, g_one);
+    k_direct_segments<MD5Hash><<<g->seg_blocks, kSegThreads, 0, s>>>(B, g_one);
     k_direct_outer<<<g->outer_blocks, kDigestThreads, 0, s>>>(B, g_one);
     return launched(3);
 }

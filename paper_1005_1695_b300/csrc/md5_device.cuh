@@ -148,113 +148,5 @@ __device__ __forceinline__ uint4 ldg_stream16(const void* p) {
 
 __device__ __forceinline__ uint32_t ldg32(const uint32_t* p) { return __ldg(p); }
 
-// MD5 of len bytes at p (any alignment) in global memory; the digest words
-// (A, B, C, D) land in st.  Bytes outside [p, p + len) are read only inside
-// aligned 16-byte blocks that also hold a byte of the message, and never used.
-template <bool FMA = true>
-__device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, uint32_t (&st)[4], uint32_t one) {
-    init(st);
-    const uint64_t addr = reinterpret_cast<uint64_t>(p);
-    const uint64_t full = len >> 6;
-    uint32_t X[16];
-    if ((addr & 15) == 0) {
-        // the next block's loads are in flight while this block compresses
-        const uint8_t* q = p;
-        uint4 nx[4];
-        if (full) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) nx[v] = ldg_stream16(q + 16 * v);
-        }
-        for (uint64_t blk = 0; blk < full; ++blk) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                X[4 * v + 0] = nx[v].x;
-                X[4 * v + 1] = nx[v].y;
-                X[4 * v + 2] = nx[v].z;
-                X[4 * v + 3] = nx[v].w;
-            }
-            q += 64;
-            if (blk + 1 < full) {
-#pragma unroll
-                for (int v = 0; v < 4; ++v) nx[v] = ldg_stream16(q + 16 * v);
-            }
-            compress<FMA>(st, X, one);
-        }
-    } else {
-        // Any other alignment: five aligned 16-byte loads cover the block (each
-        // holds at least one byte of it), then the words are shifted into place
-        // by o = addr mod 16 bytes: whole words by a two-level select on o / 4,
-        // the rest by a funnel shift.  The next block's loads are in flight
-        // while this block compresses.
-        const uint32_t o = (uint32_t)(addr & 15);
-        const uint32_t wq = o >> 2;
-        const uint32_t sh = (o & 3) * 8;
-        const uint8_t* q = reinterpret_cast<const uint8_t*>(addr - o);
-        uint4 nx[5];
-        if (full) {
-#pragma unroll
-            for (int v = 0; v < 5; ++v) nx[v] = ldg_stream16(q + 16 * v);
-        }
-        for (uint64_t blk = 0; blk < full; ++blk) {
-            uint32_t w[20];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) {
-                w[4 * v + 0] = nx[v].x;
-                w[4 * v + 1] = nx[v].y;
-                w[4 * v + 2] = nx[v].z;
-                w[4 * v + 3] = nx[v].w;
-            }
-            q += 64;
-            if (blk + 1 < full) {
-#pragma unroll
-                for (int v = 0; v < 5; ++v) nx[v] = ldg_stream16(q + 16 * v);
-            }
-            uint32_t y1[19];
-#pragma unroll
-            for (int k = 0; k < 19; ++k) y1[k] = (wq & 1) ? w[k + 1] : w[k];
-            uint32_t y[17];
-#pragma unroll
-            for (int k = 0; k < 17; ++k) y[k] = (wq & 2) ? y1[k + 2] : y1[k];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) X[k] = __funnelshift_r(y[k], y[k + 1], sh);
-            compress<FMA>(st, X, one);
-        }
-    }
-    // Tail: rem < 64 bytes, then 0x80, zeros, 64-bit bit length.
-    const uint32_t rem = (uint32_t)(len & 63);
-    const uint64_t ta = addr + (full << 6);
-    const uint32_t sh = (uint32_t)(ta & 3) * 8;
-    const uint32_t* q = reinterpret_cast<const uint32_t*>(ta & ~uint64_t(3));
-    const uint32_t nwords = ((uint32_t)(ta & 3) + rem + 3) >> 2;  // aligned words holding tail bytes
-    uint32_t x[17];
-#pragma unroll
-    for (int k = 0; k < 17; ++k) x[k] = (uint32_t)k < nwords ? ldg32(q + k) : 0u;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        uint32_t w = __funnelshift_r(x[k], x[k + 1], sh);
-        const int have = (int)rem - 4 * k;  // message bytes in this word
-        if (have <= 0) {
-            w = 0;
-        } else if (have < 4) {
-            w &= (1u << (8 * have)) - 1u;
-        }
-        if (have >= 0 && have < 4) w |= 0x80u << (8 * have);
-        X[k] = w;
-    }
-    const uint64_t bits = len << 3;
-    if (rem < 56) {
-        X[14] = (uint32_t)bits;
-        X[15] = (uint32_t)(bits >> 32);
-        compress<FMA>(st, X, one);
-    } else {
-        compress<FMA>(st, X, one);
-#pragma unroll
-        for (int k = 0; k < 14; ++k) X[k] = 0;
-        X[14] = (uint32_t)bits;
-        X[15] = (uint32_t)(bits >> 32);
-        compress<FMA>(st, X, one);
-    }
-}
-
 }  // namespace md5
 }  // namespace crystal

@@ -125,21 +125,24 @@ uint64_t crystal_sliding_out_bytes(uint64_t in_size, uint64_t max_chunks) {
     return sliding_fixed_bytes(in_size) + 20 * max_chunks;
 }
 
+uint64_t crystal_out_bytes_for_chunks(int kind, uint64_t in_size, uint64_t max_chunks) {
+    if (!kind_is_sliding(kind)) return 0;
+    return sliding_fixed_bytes(in_size) + (4 + digest_bytes_of(kind)) * max_chunks;
+}
+
 uint64_t crystal_out_bytes(int kind, uint64_t in_size, const crystal_hash_params* params) {
     crystal_hash_params p;
     crystal_params_default(&p);
     if (params) {
         if (params->window_bytes) p.window_bytes = params->window_bytes;
     }
-    switch (kind) {
-    case CRYSTAL_KIND_NOP: return in_size;
-    case CRYSTAL_KIND_MD5_DIRECT: return 16;
-    case CRYSTAL_KIND_MD5_SLIDING: {
+    if (kind == CRYSTAL_KIND_NOP) return in_size;
+    if (kind_is_direct(kind)) return digest_bytes_of(kind);
+    if (kind_is_sliding(kind)) {
         const uint64_t windows = in_size >= p.window_bytes ? in_size - p.window_bytes + 1 : 0;
-        return crystal_sliding_out_bytes(in_size, windows + 1);
+        return crystal_out_bytes_for_chunks(kind, in_size, windows + 1);
     }
-    default: return 0;
-    }
+    return 0;
 }
 
 uint64_t crystal_scratch_bytes(int kind, uint64_t n, uint64_t out_size, const crystal_hash_params* params) {
@@ -149,14 +152,15 @@ uint64_t crystal_scratch_bytes(int kind, uint64_t n, uint64_t out_size, const cr
         if (params->segment_bytes) p.segment_bytes = params->segment_bytes;
         if (params->chunk_segment_bytes) p.chunk_segment_bytes = params->chunk_segment_bytes;
     }
-    if (kind == CRYSTAL_KIND_MD5_DIRECT) return 16 * segments_of(n, p.segment_bytes);
-    if (kind == CRYSTAL_KIND_MD5_SLIDING) {
+    const uint64_t D = digest_bytes_of(kind);
+    if (kind_is_direct(kind)) return D * segments_of(n, p.segment_bytes);
+    if (kind_is_sliding(kind)) {
         const uint64_t fixed = sliding_fixed_bytes(n);
         if (out_size < fixed) return 0;
-        const uint64_t cap = (out_size - fixed) / 20;
+        const uint64_t cap = (out_size - fixed) / (4 + D);
         const uint64_t table = align_up(4 * (cap + 1), 16);
         const uint64_t chunk_segments = cap + (n + p.chunk_segment_bytes - 1) / p.chunk_segment_bytes + 1;
-        return table + 16 * chunk_segments;
+        return table + D * chunk_segments;
     }
     return 0;
 }
@@ -171,32 +175,45 @@ int crystal_batch_plan(crystal_batch* b, uint32_t n_direct, uint32_t n_sliding) 
     uint64_t segs = 0, tiles = 0;
     uint32_t wmax = 0;
     for (uint32_t i = 0; i < n_direct; ++i) {
-        crystal_unit& x = U[i];
-        if (x.kind != CRYSTAL_KIND_MD5_DIRECT || x.seg_bytes == 0 || x.out_cap < 16) return CRYSTAL_EINVAL;
+        const crystal_unit& x = U[i];
+        if (!kind_is_direct(x.kind) || x.seg_bytes == 0 || x.out_cap < digest_bytes_of(x.kind)) return CRYSTAL_EINVAL;
         if ((x.scratch & 15) || (x.out & 3) || !x.scratch || !x.out || (!x.in && x.n)) return CRYSTAL_EINVAL;
+    }
+    // MD5 direct units first (stable): one segment kernel instance per hash
+    std::stable_partition(U, U + n_direct, [](const crystal_unit& x) { return !kind_is_sha1(x.kind); });
+    uint64_t segs_md5 = 0;
+    for (uint32_t i = 0; i < n_direct; ++i) {
+        crystal_unit& x = U[i];
         x.work_begin = segs;
         segs += segments_of(x.n, x.seg_bytes);
+        if (!kind_is_sha1(x.kind)) segs_md5 = segs;
     }
     crystal_unit* S = U + n_direct;
     for (uint32_t i = 0; i < n_sliding; ++i) {
         const crystal_unit& x = S[i];
-        if (x.kind != CRYSTAL_KIND_MD5_SLIDING || x.seg_bytes == 0) return CRYSTAL_EINVAL;
+        if (!kind_is_sliding(x.kind) || x.seg_bytes == 0) return CRYSTAL_EINVAL;
         if (x.window == 0 || x.window > kMaxWindow || x.n >= (1ull << 32)) return CRYSTAL_EINVAL;
         if (x.out_cap < sliding_fixed_bytes(x.n)) return CRYSTAL_EINVAL;
         if ((x.scratch & 15) || (x.out & 3) || !x.scratch || !x.out || (!x.in && x.n)) return CRYSTAL_EINVAL;
     }
-    // w = 20 units first (stable): the window kernel has a specialised
-    // instance for them and one for every other window length
-    std::stable_partition(S, S + n_sliding, [](const crystal_unit& x) { return x.window == 20; });
-    uint64_t tiles_w20 = 0;
+    // order (stable): MD5 with w = 20, other MD5, SHA-1 -- the window kernel
+    // has one instance for each group
+    auto group = [](const crystal_unit& x) {
+        return kind_is_sha1(x.kind) ? 2 : (x.window == 20 ? 0 : 1);
+    };
+    std::stable_sort(S, S + n_sliding,
+                     [&](const crystal_unit& a, const crystal_unit& b) { return group(a) < group(b); });
+    uint64_t tiles_w20 = 0, tiles_md5 = 0;
     for (uint32_t i = 0; i < n_sliding; ++i) {
         crystal_unit& x = S[i];
         x.work_begin = tiles;
         x.seg_base = 0;
         tiles += (x.n + CRYSTAL_SLIDING_TILE - 1) / CRYSTAL_SLIDING_TILE;
-        if (x.window == 20) tiles_w20 = tiles;
+        if (group(x) == 0) tiles_w20 = tiles;
+        if (group(x) <= 1) tiles_md5 = tiles;
         if (x.window > wmax) wmax = x.window;
     }
+    if (tiles_md5 < tiles_w20) tiles_md5 = tiles_w20;
     b->n_direct = n_direct;
     b->n_sliding = n_sliding;
     b->direct_segments = segs;
@@ -204,8 +221,9 @@ int crystal_batch_plan(crystal_batch* b, uint32_t n_direct, uint32_t n_sliding) 
     b->window_max = wmax;
     b->status = 0;
     b->sliding_tiles_w20 = tiles_w20;
+    b->sliding_tiles_md5 = tiles_md5;
+    b->direct_segments_md5 = segs_md5;
     b->chunk_segments = 0;
-    memset(b->reserved, 0, sizeof b->reserved);
     return CRYSTAL_OK;
 }
 

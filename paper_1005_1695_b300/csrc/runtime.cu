@@ -237,15 +237,14 @@ int resolve_params(int kind, const crystal_hash_params* in, uint64_t n, uint64_t
         p->mask = in->mask;
         p->target = in->target;
     }
-    switch (kind) {
-    case CRYSTAL_KIND_NOP: return CRYSTAL_OK;
-    case CRYSTAL_KIND_MD5_DIRECT: return out_size >= 16 ? CRYSTAL_OK : CRYSTAL_EINVAL;
-    case CRYSTAL_KIND_MD5_SLIDING:
+    if (kind == CRYSTAL_KIND_NOP) return CRYSTAL_OK;
+    if (kind_is_direct(kind)) return out_size >= digest_bytes_of(kind) ? CRYSTAL_OK : CRYSTAL_EINVAL;
+    if (kind_is_sliding(kind)) {
         if (p->window_bytes > kMaxWindow || n >= (1ull << 32)) return CRYSTAL_EINVAL;
         if (out_size < sliding_fixed_bytes(n) || out_size >= (1ull << 32)) return CRYSTAL_EINVAL;
         return CRYSTAL_OK;
-    default: return CRYSTAL_EINVAL;
     }
+    return CRYSTAL_EINVAL;
 }
 
 // ---- issuing a batch --------------------------------------------------------------
@@ -255,9 +254,8 @@ void build_descriptor(Slot& s, uint32_t* nd_out, uint32_t* ns_out) {
     crystal_unit* U = batch_units(s.h_desc);
     uint32_t k = 0;
     for (int pass = 0; pass < 2; ++pass) {
-        const int want = pass == 0 ? CRYSTAL_KIND_MD5_DIRECT : CRYSTAL_KIND_MD5_SLIDING;
         for (crystal_task* t : s.tasks) {
-            if (t->kind != want) continue;
+            if (pass == 0 ? !kind_is_direct(t->kind) : !kind_is_sliding(t->kind)) continue;
             crystal_unit& x = U[k++];
             x.in = (uint64_t)t->d_in;
             x.n = t->in_size;
@@ -265,12 +263,11 @@ void build_descriptor(Slot& s, uint32_t* nd_out, uint32_t* ns_out) {
             x.scratch = (uint64_t)t->d_scratch;
             x.work_begin = 0;
             x.out_cap = (uint32_t)std::min<uint64_t>(t->out_size, 0xFFFFFFFFull);
-            x.seg_bytes = want == CRYSTAL_KIND_MD5_DIRECT ? t->params.segment_bytes
-                                                          : t->params.chunk_segment_bytes;
+            x.seg_bytes = pass == 0 ? t->params.segment_bytes : t->params.chunk_segment_bytes;
             x.window = (uint16_t)t->params.window_bytes;
             x.mask = t->params.mask;
             x.target = t->params.target;
-            x.kind = (uint16_t)want;
+            x.kind = (uint16_t)t->kind;
             x.seg_base = 0;
         }
         if (pass == 0) *nd_out = k;
@@ -292,7 +289,7 @@ int launch_chain(crystal_batch* d, cudaStream_t st, bool direct, bool sliding) {
     return r;
 }
 
-int kernels_in_chain(bool direct, bool sliding) { return (direct ? 2 : 0) + (sliding ? 6 : 0); }
+int kernels_in_chain(bool direct, bool sliding) { return (direct ? 3 : 0) + (sliding ? 7 : 0); }
 
 // Capture descriptor upload + kernel chain of one slot as a graph.
 int capture_graph(crystal_ctx* c, Slot& s, int variant) {
@@ -358,7 +355,7 @@ int issue(crystal_ctx* c, Slot& s) {
 
 int job_status(crystal_task* t, uint32_t dev_status) {
     if (dev_status) return CRYSTAL_EDEVICE;
-    if (t->kind == CRYSTAL_KIND_MD5_SLIDING) {
+    if (kind_is_sliding(t->kind)) {
         uint32_t flags;
         memcpy(&flags, t->h_out + 4, 4);
         if (flags & 1u) return CRYSTAL_EOVERFLOW;

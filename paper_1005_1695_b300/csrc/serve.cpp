@@ -59,7 +59,7 @@ struct Serve {
     bool workers_stop = false;
 
     const crystal_hash_params* params_for(int kind) const {
-        return kind == CRYSTAL_KIND_MD5_SLIDING ? &ps : &pd;
+        return kind == CRYSTAL_KIND_MD5_SLIDING || kind == CRYSTAL_KIND_SHA1_SLIDING ? &ps : &pd;
     }
 
     void finish(uint32_t i, int status) {
@@ -76,12 +76,14 @@ struct Serve {
 };
 
 uint64_t used_bytes(int kind, uint64_t n, const uint8_t* out, uint64_t out_size) {
-    if (kind == CRYSTAL_KIND_MD5_DIRECT) return out_size < 16 ? 0 : 16;
-    if (kind != CRYSTAL_KIND_MD5_SLIDING) return out_size;
+    const bool sha = kind == CRYSTAL_KIND_SHA1_DIRECT || kind == CRYSTAL_KIND_SHA1_SLIDING;
+    const uint64_t D = sha ? 20 : 16;
+    if (kind == CRYSTAL_KIND_MD5_DIRECT || kind == CRYSTAL_KIND_SHA1_DIRECT) return out_size < D ? 0 : D;
+    if (kind != CRYSTAL_KIND_MD5_SLIDING && kind != CRYSTAL_KIND_SHA1_SLIDING) return out_size;
     uint32_t hdr[2];
     memcpy(hdr, out, 8);
     const uint64_t fixed = 8 + 4 * ((n + 31) / 32);
-    return (hdr[1] & 1u) ? fixed : fixed + 20ull * hdr[0];
+    return (hdr[1] & 1u) ? fixed : fixed + (4 + D) * hdr[0];
 }
 
 // Completion callback, on the master thread.
@@ -134,8 +136,7 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
     for (uint32_t i = 0; i < n; ++i) {
         const crystal_request& r = req[i];
         if (r.src_offset > source_bytes || r.size > source_bytes - r.src_offset) return CRYSTAL_EINVAL;
-        if (r.kind != CRYSTAL_KIND_MD5_DIRECT && r.kind != CRYSTAL_KIND_MD5_SLIDING && r.kind != CRYSTAL_KIND_NOP)
-            return CRYSTAL_EINVAL;
+        if (r.kind < CRYSTAL_KIND_NOP || r.kind > CRYSTAL_KIND_SHA1_SLIDING) return CRYSTAL_EINVAL;
         if (i && r.arrival_ns < req[i - 1].arrival_ns) return CRYSTAL_EINVAL;
     }
     Serve s;

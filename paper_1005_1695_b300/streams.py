@@ -64,12 +64,12 @@ class StreamResult:
 
 
 def _used(kind: int, n: int, out: np.ndarray) -> int:
-    if kind == C.CRYSTAL_KIND_MD5_DIRECT:
-        return 16
+    if kind in C.DIRECT_KINDS:
+        return C.digest_size(kind)
     words = (n + 31) // 32
     n_chunks = int(out[0:4].view(np.uint32)[0])
     flags = int(out[4:8].view(np.uint32)[0])
-    return 8 + 4 * words + (0 if flags & 1 else 20 * n_chunks)
+    return 8 + 4 * words + (0 if flags & 1 else (4 + C.digest_size(kind)) * n_chunks)
 
 
 def run_stream(mode: str, unit: Callable[[int], np.ndarray], n_units: int, unit_bytes: int, kind: int,

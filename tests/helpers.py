@@ -4,14 +4,15 @@ import numpy as np
 
 def used_bytes(kind: int, n: int, out: bytes) -> int:
     """Bytes of an output buffer that carry results (the rest is capacity)."""
-    if kind == 1:
-        return 16
+    digest = 20 if kind in (3, 4) else 16
+    if kind in (1, 3):
+        return digest
     if kind == 0:
         return 0
     words = (n + 31) // 32
     n_chunks = int.from_bytes(out[0:4], "little")
     flags = int.from_bytes(out[4:8], "little")
-    return 8 + 4 * words + (0 if flags & 1 else 20 * n_chunks)
+    return 8 + 4 * words + (0 if flags & 1 else (4 + digest) * n_chunks)
 
 
 def same_result(kind: int, n: int, got: bytes, want: bytes) -> bool:

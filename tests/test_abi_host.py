@@ -181,3 +181,30 @@ def test_batch_plan_puts_w20_units_first(C):
     for b in ([_unit(S, 10, window=56)], [_unit(S, 10, window=0)], [_unit(S, 4096, out_cap=100)],
               [_unit(S, 1 << 32)]):
         assert _plan(C, b, 0, 1)[0] == C.CRYSTAL_EINVAL
+
+
+def test_batch_plan_orders_hashes(C):
+    D5, S5, D1, S1 = (C.CRYSTAL_KIND_MD5_DIRECT, C.CRYSTAL_KIND_MD5_SLIDING, C.CRYSTAL_KIND_SHA1_DIRECT,
+                      C.CRYSTAL_KIND_SHA1_SLIDING)
+    units = [_unit(D1, 5000, out=1 << 21), _unit(D5, 4096, out=2 << 21), _unit(D1, 100, out=3 << 21),
+             _unit(S1, 3000, out=4 << 21), _unit(S5, 9000, window=7, out=5 << 21), _unit(S5, 5000, out=6 << 21)]
+    st, buf, rec = _plan(C, units, 3, 3)
+    assert st == 0
+    assert rec["kind"].tolist() == [D5, D1, D1, S5, S5, S1]
+    assert rec["window"].tolist()[3:] == [20, 7, 20]
+    hdr = buf[:64]
+    tile = int(re.search(r"#define CRYSTAL_SLIDING_TILE (\d+)u", open(HEADER).read()).group(1))
+    t = [-(-n // tile) for n in (5000, 9000, 3000)]
+    assert hdr[32:40].view("<u8")[0] == t[0]                 # MD5 w = 20 tiles
+    assert hdr[48:56].view("<u8")[0] == t[0] + t[1]          # all MD5 sliding tiles
+    assert hdr[56:64].view("<u8")[0] == 1                    # MD5 direct segments (one 4096-byte unit)
+    assert hdr[8:16].view("<u8")[0] == 1 + 2 + 1             # all direct segments
+    bad = [_unit(D1, 10, out_cap=19)]                        # SHA-1 digest needs 20 bytes
+    assert _plan(C, bad, 1, 0)[0] == C.CRYSTAL_EINVAL
+
+
+def test_sha1_sizes(C):
+    n = 1 << 20
+    assert C.out_bytes(C.CRYSTAL_KIND_SHA1_DIRECT, n) == 20
+    assert C.sliding_out_bytes(n, 10, C.CRYSTAL_KIND_SHA1_SLIDING) == 8 + 4 * (n // 32) + 24 * 10
+    assert C.scratch_bytes(C.CRYSTAL_KIND_SHA1_DIRECT, 65536, 20) == 20 * 16

@@ -66,6 +66,9 @@ def _run(torch, C, units, kinds, plist, out_sizes=None, align=None, mode="batch"
     return b.outputs()
 
 
+SHA1_DIRECT, SHA1_SLIDING = 3, 4
+
+
 def _oracle_all(oracle_mod, units, kinds, plist, out_sizes):
     def one(i):
         p = plist[i]
@@ -216,3 +219,46 @@ def test_sliding_config_256x1mib_sampled(torch_cuda, C, oracle_mod):
     units = [host[u * n:(u + 1) * n] for u in sample]
     want = _oracle_all(oracle_mod, units, [SLIDING] * len(units), [p] * len(units), [out_size] * len(units))
     _compare(units, [SLIDING] * len(units), [got[u] for u in sample], want)
+
+
+# ---- SHA-1 kinds ------------------------------------------------------------------
+
+@pytest.mark.parametrize("S", [4096, 100, 1])
+def test_sha1_direct_sizes_alignments(torch_cuda, C, oracle_mod, S):
+    units = [_rand(7000 + i, n) for i, n in enumerate(DIRECT_SIZES)]
+    kinds = [SHA1_DIRECT] * len(units)
+    plist = [C.params(segment_bytes=S)] * len(units)
+    got = _run(torch_cuda, C, units, kinds, plist, align=[0, 1, 2, 3, 5, 16, 4, 8])
+    want = _oracle_all(oracle_mod, units, kinds, plist, [20] * len(units))
+    _compare(units, kinds, got, want)
+
+
+@pytest.mark.parametrize("w", [1, 3, 20, 55])
+@pytest.mark.parametrize("mask,target", [(0x0, 0x0), (0x3, 0x1), (0x1FFF, 0x1FFF)])
+def test_sha1_sliding_tiny_every_length(torch_cuda, C, oracle_mod, w, mask, target):
+    units = [_rand(8000 + n, n) for n in range(0, 65)]
+    kinds = [SHA1_SLIDING] * len(units)
+    plist = [C.params(window_bytes=w, mask=mask, target=target, chunk_segment_bytes=16)] * len(units)
+    outs = [C.out_bytes(SHA1_SLIDING, len(u), plist[0]) for u in units]
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 3, 1, 2])
+    want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    _compare(units, kinds, got, want)
+
+
+def test_md5_and_sha1_mixed_batch(torch_cuda, C, oracle_mod):
+    units, kinds, plist, outs = [], [], [], []
+    for i in range(32):
+        n = [0, 33, 4097, 70001, 1 << 20, 3000][i % 6] + i
+        units.append(_rand(9000 + i, n))
+        k = [C.CRYSTAL_KIND_MD5_DIRECT, SHA1_DIRECT, C.CRYSTAL_KIND_MD5_SLIDING, SHA1_SLIDING][i % 4]
+        kinds.append(k)
+        if k in (2, 4):
+            plist.append(C.params(window_bytes=[20, 9][i % 2 if k == 2 else 0], mask=0xFF, target=i & 0xFF,
+                                  chunk_segment_bytes=[4096, 700][i % 2]))
+            outs.append(C.sliding_out_bytes(n, n // 64 + 4, k))
+        else:
+            plist.append(C.params(segment_bytes=[4096, 999][i % 2]))
+            outs.append(C.digest_size(k))
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 1, 16, 3])
+    want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    _compare(units, kinds, got, want)

@@ -357,3 +357,23 @@ def test_priority_jobs_overtake_queued_fifo_jobs(C):
         assert big.timing()[1] < d_high < min(d_low)
         assert d_low == sorted(d_low)
         assert high.set_priority(0) == 0
+
+
+def test_sha1_jobs_through_runtime(C, oracle_mod):
+    from paper_1005_1695_b300 import inputs
+
+    jobs = []
+    for i in range(10):
+        n = [65536, 300001, 0, 1 << 20, 77][i % 5]
+        if i % 2:
+            data = inputs.dedup_unit(29, i, n)
+            jobs.append((C.CRYSTAL_KIND_SHA1_SLIDING, data, C.sliding_out_bytes(n, n // 256 + 16, 4),
+                         C.params(mask=0x3FF, target=0x3FF)))
+        else:
+            data = inputs.uniform_unit(29, i, n)
+            jobs.append((C.CRYSTAL_KIND_SHA1_DIRECT, data, 20, C.params(segment_bytes=2048)))
+    want = _want(oracle_mod, jobs)
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=128 << 20,
+                   host_pool_bytes=64 << 20, n_streams=3, flags=C.CRYSTAL_FLAG_GRAPHS, max_batch_jobs=4) as ctx:
+        tasks = _submit_all(C, ctx, jobs)
+        _check(C, tasks, jobs, want)
