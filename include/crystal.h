@@ -445,10 +445,18 @@ int crystal_md5_direct_noalloc(const void* d_in, uint64_t unit_bytes, uint32_t n
                                void* d_digests, void* stream);
 
 /* Host-side arena allocator the pools use (exposed for tests; no GPU
- * needed).  Offsets are relative to 0; alignment is a power of two. */
+ * needed).  Offsets are relative to 0; alignment is a power of two; the
+ * arena's size is rounded down to a multiple of it. */
 typedef struct crystal_arena crystal_arena;
 int crystal_arena_create(uint64_t bytes, uint64_t alignment, crystal_arena** out);
-int crystal_arena_alloc(crystal_arena* a, uint64_t bytes, uint64_t* offset);
+int crystal_arena_alloc(crystal_arena* a, uint64_t bytes, uint64_t* offset);  /* best fit */
+/* Placement-controlled allocation: best fit, the lowest-addressed free block
+ * that fits (from its bottom), or the highest-addressed one (from its top).
+ * The job runtime takes inputs from the bottom and outputs and scratch from
+ * the top, so jobs created one after another get adjacent inputs and adjacent
+ * outputs and a batch's copies can be merged. */
+enum { CRYSTAL_ARENA_BEST_FIT = 0, CRYSTAL_ARENA_LOWEST = 1, CRYSTAL_ARENA_HIGHEST = 2 };
+int crystal_arena_alloc_at(crystal_arena* a, uint64_t bytes, int placement, uint64_t* offset);
 int crystal_arena_free(crystal_arena* a, uint64_t offset);
 uint64_t crystal_arena_used(crystal_arena* a);
 uint64_t crystal_arena_largest_free(crystal_arena* a);

@@ -43,6 +43,8 @@ extern "C" {
 
 int crystal_arena_create(uint64_t bytes, uint64_t alignment, crystal_arena** out) {
     if (!out || bytes == 0 || alignment == 0 || (alignment & (alignment - 1))) return CRYSTAL_EINVAL;
+    bytes &= ~(alignment - 1);  // whole aligned blocks only, so blocks taken from the top stay aligned
+    if (bytes == 0) return CRYSTAL_EINVAL;
     crystal_arena* a = new (std::nothrow) crystal_arena;
     if (!a) return CRYSTAL_ENOMEM;
     a->size = bytes;
@@ -52,21 +54,48 @@ int crystal_arena_create(uint64_t bytes, uint64_t alignment, crystal_arena** out
     return CRYSTAL_OK;
 }
 
-int crystal_arena_alloc(crystal_arena* a, uint64_t bytes, uint64_t* offset) {
-    if (!a || !offset) return CRYSTAL_EINVAL;
+int crystal_arena_alloc_at(crystal_arena* a, uint64_t bytes, int placement, uint64_t* offset) {
+    if (!a || !offset || placement < CRYSTAL_ARENA_BEST_FIT || placement > CRYSTAL_ARENA_HIGHEST)
+        return CRYSTAL_EINVAL;
     const uint64_t want = align_up(bytes ? bytes : 1, a->align);
     if (want < bytes) return CRYSTAL_EAGAIN;  // overflow
     std::lock_guard<std::mutex> lk(a->mu);
-    auto it = a->free_by_len.lower_bound({want, 0});
-    if (it == a->free_by_len.end()) return CRYSTAL_EAGAIN;
-    const uint64_t len = it->first, off = it->second;
-    a->free_by_len.erase(it);
+    uint64_t off = 0, len = 0;
+    if (placement == CRYSTAL_ARENA_BEST_FIT) {
+        auto it = a->free_by_len.lower_bound({want, 0});
+        if (it == a->free_by_len.end()) return CRYSTAL_EAGAIN;
+        len = it->first;
+        off = it->second;
+    } else if (placement == CRYSTAL_ARENA_LOWEST) {
+        auto it = a->free_by_off.begin();
+        while (it != a->free_by_off.end() && it->second < want) ++it;
+        if (it == a->free_by_off.end()) return CRYSTAL_EAGAIN;
+        off = it->first;
+        len = it->second;
+    } else {
+        auto it = a->free_by_off.rbegin();
+        while (it != a->free_by_off.rend() && it->second < want) ++it;
+        if (it == a->free_by_off.rend()) return CRYSTAL_EAGAIN;
+        off = it->first;
+        len = it->second;
+    }
+    a->free_by_len.erase({len, off});
     a->free_by_off.erase(off);
-    if (len > want) a->insert_free(off + want, len - want);
-    a->live.emplace(off, want);
+    uint64_t at = off;
+    if (placement == CRYSTAL_ARENA_HIGHEST) {
+        at = off + len - want;  // top of the block; the rest stays free below it
+        if (len > want) a->insert_free(off, len - want);
+    } else if (len > want) {
+        a->insert_free(off + want, len - want);
+    }
+    a->live.emplace(at, want);
     a->used += want;
-    *offset = off;
+    *offset = at;
     return CRYSTAL_OK;
+}
+
+int crystal_arena_alloc(crystal_arena* a, uint64_t bytes, uint64_t* offset) {
+    return crystal_arena_alloc_at(a, bytes, CRYSTAL_ARENA_BEST_FIT, offset);
 }
 
 int crystal_arena_free(crystal_arena* a, uint64_t offset) {

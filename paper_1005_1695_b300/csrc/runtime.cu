@@ -162,9 +162,9 @@ namespace {
 
 // ---- buffers ------------------------------------------------------------------
 
-int alloc_device(crystal_ctx* c, uint64_t bytes, uint8_t** p, uint64_t* off) {
+int alloc_device(crystal_ctx* c, uint64_t bytes, uint8_t** p, uint64_t* off, int placement = CRYSTAL_ARENA_HIGHEST) {
     if (c->pooled) {
-        int st = crystal_arena_alloc(c->d_arena, bytes, off);
+        int st = crystal_arena_alloc_at(c->d_arena, bytes, placement, off);
         if (st != CRYSTAL_OK) return st;
         *p = c->d_base + *off;
         return CRYSTAL_OK;
@@ -184,9 +184,9 @@ void free_device(crystal_ctx* c, uint8_t* p, uint64_t off) {
     else cudaFree(p);
 }
 
-int alloc_host(crystal_ctx* c, uint64_t bytes, uint8_t** p, uint64_t* off) {
+int alloc_host(crystal_ctx* c, uint64_t bytes, uint8_t** p, uint64_t* off, int placement = CRYSTAL_ARENA_HIGHEST) {
     if (c->pooled) {
-        int st = crystal_arena_alloc(c->h_arena, bytes, off);
+        int st = crystal_arena_alloc_at(c->h_arena, bytes, placement, off);
         if (st != CRYSTAL_OK) return st;
         *p = c->h_base + *off;
         return CRYSTAL_OK;
@@ -314,12 +314,69 @@ int capture_graph(crystal_ctx* c, Slot& s, int variant) {
 }
 
 // Issue copy-in, kernels and copy-out of the slot's jobs on its stream.
+// Copies of several jobs merged into one when their host ranges and their
+// device ranges are both contiguous blocks at the same host-to-device offset
+// (fewer, larger DMA transfers).  A job's block is its whole allocation, so a
+// merged copy only ever covers memory of the merged jobs.
+class CopyMerger {
+  public:
+    CopyMerger(cudaStream_t s, cudaMemcpyKind kind) : s_(s), kind_(kind) {}
+    // host/dev: the job's buffers; used: bytes that matter; block: allocated bytes
+    bool add(const uint8_t* host, uint8_t* dev, uint64_t used, uint64_t block, bool mergeable) {
+        if (!used) return true;
+        const int64_t delta = (int64_t)((uint64_t)dev - (uint64_t)host);
+        if (open_ && mergeable && delta == delta_) {
+            if (host == hi_) {  // just above the run
+                hi_ = host + block;
+                end_ = host + used;
+                return true;
+            }
+            if (host + block == lo_) {  // just below the run
+                lo_ = host;
+                return true;
+            }
+        }
+        if (!flush()) return false;
+        if (!mergeable) return copy(host, dev, used);
+        open_ = true;
+        lo_ = host;
+        hi_ = host + block;
+        end_ = host + used;
+        delta_ = delta;
+        return true;
+    }
+    bool flush() {
+        if (!open_) return true;
+        open_ = false;
+        return copy(lo_, reinterpret_cast<uint8_t*>((uint64_t)lo_ + (uint64_t)delta_), (uint64_t)(end_ - lo_));
+    }
+
+  private:
+    bool copy(const uint8_t* host, uint8_t* dev, uint64_t n) {
+        if (kind_ == cudaMemcpyHostToDevice)
+            return cudaMemcpyAsync(dev, host, n, kind_, s_) == cudaSuccess;
+        return cudaMemcpyAsync(const_cast<uint8_t*>(host), dev, n, kind_, s_) == cudaSuccess;
+    }
+    cudaStream_t s_;
+    cudaMemcpyKind kind_;
+    bool open_ = false;
+    const uint8_t* lo_ = nullptr;
+    const uint8_t* hi_ = nullptr;   // end of the highest block in the run
+    const uint8_t* end_ = nullptr;  // end of the bytes to copy (in the highest block)
+    int64_t delta_ = 0;
+};
+
 int issue(crystal_ctx* c, Slot& s) {
     cudaStream_t st = s.stream;
-    for (crystal_task* t : s.tasks) {
-        const uint8_t* src = t->h_in_ext ? t->h_in_ext : t->h_in;
-        if (t->in_size && cudaMemcpyAsync(t->d_in, src, t->in_size, cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return CRYSTAL_EDEVICE;
+    {
+        CopyMerger in(st, cudaMemcpyHostToDevice);
+        for (crystal_task* t : s.tasks) {
+            const bool own = !t->h_in_ext;
+            const uint8_t* src = own ? t->h_in : t->h_in_ext;
+            if (!in.add(src, t->d_in, t->in_size, align_up(t->in_cap ? t->in_cap : 1, 256), own && c->pooled))
+                return CRYSTAL_EDEVICE;
+        }
+        if (!in.flush()) return CRYSTAL_EDEVICE;
     }
     uint32_t nd = 0, ns = 0;
     build_descriptor(s, &nd, &ns);
@@ -345,9 +402,13 @@ int issue(crystal_ctx* c, Slot& s) {
         s.h_desc->status = 0;
         if (launch_nop(st) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     }
-    for (crystal_task* t : s.tasks) {
-        if (t->out_size && cudaMemcpyAsync(t->h_out, t->d_out, t->out_size, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-            return CRYSTAL_EDEVICE;
+    {
+        CopyMerger out(st, cudaMemcpyDeviceToHost);
+        for (crystal_task* t : s.tasks) {
+            if (!out.add(t->h_out, t->d_out, t->out_size, align_up(t->out_cap ? t->out_cap : 1, 256), c->pooled))
+                return CRYSTAL_EDEVICE;
+        }
+        if (!out.flush()) return CRYSTAL_EDEVICE;
     }
     if (cudaEventRecord(s.done, st) != cudaSuccess) return CRYSTAL_EDEVICE;
     return CRYSTAL_OK;
@@ -706,10 +767,11 @@ int crystal_task_create_ex(crystal_ctx* c, uint64_t in_size, uint64_t out_size, 
     t->in_cap = t->in_size = in_size;
     t->out_cap = t->out_size = out_size;
     t->external_input = flags & CRYSTAL_TASK_EXTERNAL_INPUT;
-    int st = t->external_input ? CRYSTAL_OK : alloc_host(c, in_size, &t->h_in, &t->h_in_off);
-    if (st == CRYSTAL_OK) st = alloc_host(c, out_size, &t->h_out, &t->h_out_off);
-    if (st == CRYSTAL_OK) st = alloc_device(c, in_size, &t->d_in, &t->d_in_off);
-    if (st == CRYSTAL_OK) st = alloc_device(c, out_size, &t->d_out, &t->d_out_off);
+    // inputs from the bottom of the arenas, outputs and scratch from the top
+    int st = t->external_input ? CRYSTAL_OK : alloc_host(c, in_size, &t->h_in, &t->h_in_off, CRYSTAL_ARENA_LOWEST);
+    if (st == CRYSTAL_OK) st = alloc_host(c, out_size, &t->h_out, &t->h_out_off, CRYSTAL_ARENA_HIGHEST);
+    if (st == CRYSTAL_OK) st = alloc_device(c, in_size, &t->d_in, &t->d_in_off, CRYSTAL_ARENA_LOWEST);
+    if (st == CRYSTAL_OK) st = alloc_device(c, out_size, &t->d_out, &t->d_out_off, CRYSTAL_ARENA_HIGHEST);
     if (st == CRYSTAL_OK && scratch_bytes) {
         st = alloc_device(c, scratch_bytes, &t->d_reserved, &t->d_reserved_off);
         if (st == CRYSTAL_OK) t->reserved_bytes = scratch_bytes;

@@ -208,3 +208,31 @@ def test_sha1_sizes(C):
     assert C.out_bytes(C.CRYSTAL_KIND_SHA1_DIRECT, n) == 20
     assert C.sliding_out_bytes(n, 10, C.CRYSTAL_KIND_SHA1_SLIDING) == 8 + 4 * (n // 32) + 24 * 10
     assert C.scratch_bytes(C.CRYSTAL_KIND_SHA1_DIRECT, 65536, 20) == 20 * 16
+
+
+def test_arena_two_ended_placement(C):
+    L, h = _arena(C, 1 << 20)
+    off = ctypes.c_uint64()
+    lows, highs = [], []
+    for i in range(6):
+        assert L.crystal_arena_alloc_at(h, 1000, 1, ctypes.byref(off)) == 0
+        lows.append(off.value)
+        assert L.crystal_arena_alloc_at(h, 3000, 2, ctypes.byref(off)) == 0
+        highs.append(off.value)
+    assert lows == [1024 * i for i in range(6)]                        # ascending, adjacent
+    assert highs == [(1 << 20) - 3072 * (i + 1) for i in range(6)]      # descending, adjacent
+    assert L.crystal_arena_alloc_at(h, 10, 3, ctypes.byref(off)) == C.CRYSTAL_EINVAL
+    for o in lows + highs:
+        assert L.crystal_arena_free(h, o) == 0
+    assert L.crystal_arena_largest_free(h) == 1 << 20
+    assert L.crystal_arena_alloc_at(h, 2 << 20, 2, ctypes.byref(off)) == C.CRYSTAL_EAGAIN
+    L.crystal_arena_destroy(h)
+
+
+def test_arena_top_blocks_aligned_for_any_size(C):
+    L, h = _arena(C, (1 << 20) + 1000)  # not a multiple of the alignment
+    off = ctypes.c_uint64()
+    for _ in range(5):
+        assert L.crystal_arena_alloc_at(h, 777, 2, ctypes.byref(off)) == 0
+        assert off.value % 256 == 0
+    L.crystal_arena_destroy(h)
