@@ -379,11 +379,14 @@ class DeviceBatch:
     tensor), with outputs, scratch and the descriptor in torch-owned device
     memory.  ``offsets``/``sizes`` locate each unit in ``d_input``; units are
     reordered direct-first as the descriptor requires, and results come back
-    in the caller's order."""
+    in the caller's order.  ``out_misalign`` (multiples of 4, cycled over the
+    units) places each output that many bytes past a 256-byte boundary; the
+    C ABI only asks for 4-byte aligned outputs."""
 
     def __init__(self, d_input, offsets: Sequence[int], sizes: Sequence[int], kinds: Sequence[int],
                  p: Optional[crystal_hash_params] = None, out_sizes: Optional[Sequence[int]] = None,
-                 per_unit_params: Optional[Sequence[crystal_hash_params]] = None):
+                 per_unit_params: Optional[Sequence[crystal_hash_params]] = None,
+                 out_misalign: Optional[Sequence[int]] = None):
         import torch
 
         L = load()
@@ -413,8 +416,11 @@ class DeviceBatch:
                 osz = digest_size(kinds[i])
             else:
                 osz = L.crystal_out_bytes(kinds[i], self.sizes[i], ctypes.byref(pi))
-            self.out_off[i], self.out_size[i] = o, osz
-            o = _align(o + osz, 256)
+            mis = int(out_misalign[i % len(out_misalign)]) if out_misalign else 0
+            if mis % 4:
+                raise ValueError("outputs must stay 4-byte aligned")
+            self.out_off[i], self.out_size[i] = o + mis, osz
+            o = _align(o + mis + osz, 256)
             sb = L.crystal_scratch_bytes(kinds[i], self.sizes[i], osz, ctypes.byref(pi))
             self.scr_off[i] = s
             s = _align(s + max(sb, 16), 256)

@@ -16,6 +16,15 @@
 
 namespace crystal {
 
+// 16-byte asynchronous global -> shared copy (L2 only), its commit and wait.
+__device__ __forceinline__ void cp_async16(void* smem_dst, uint64_t gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 struct MD5Hash {
     static constexpr int kWords = 4;
     static constexpr int kBytes = 16;
@@ -65,6 +74,43 @@ struct SHA1Hash {
     }
     __device__ static uint32_t out_word(uint32_t s) { return sha1::bswap(s); }
 };
+
+// Tail of a message of len bytes whose last len mod 64 bytes start at ta:
+// those bytes, then 0x80, zeros and the 64-bit bit length.
+template <class H, bool FMA>
+__device__ __forceinline__ void digest_tail(uint64_t ta, uint64_t len, uint32_t (&st)[5], uint32_t (&X)[16],
+                                            uint32_t one) {
+    const uint32_t rem = (uint32_t)(len & 63);
+    const uint32_t sh = (uint32_t)(ta & 3) * 8;
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(ta & ~uint64_t(3));
+    const uint32_t nwords = ((uint32_t)(ta & 3) + rem + 3) >> 2;  // aligned words holding tail bytes
+    uint32_t x[17];
+#pragma unroll
+    for (int k = 0; k < 17; ++k) x[k] = (uint32_t)k < nwords ? md5::ldg32(q + k) : 0u;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        uint32_t w = __funnelshift_r(x[k], x[k + 1], sh);
+        const int have = (int)rem - 4 * k;  // message bytes in this word
+        if (have <= 0) {
+            w = 0;
+        } else if (have < 4) {
+            w &= (1u << (8 * have)) - 1u;
+        }
+        if (have >= 0 && have < 4) w |= 0x80u << (8 * have);
+        X[k] = H::word(w);
+    }
+    const uint64_t bits = len << 3;
+    if (rem < 56) {
+        H::length(X, bits);
+        H::template compress<FMA>(st, X, one);
+    } else {
+        H::template compress<FMA>(st, X, one);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) X[k] = 0;
+        H::length(X, bits);
+        H::template compress<FMA>(st, X, one);
+    }
+}
 
 // Digest of len bytes at p (any alignment) in global memory into st[0..kWords).
 // Bytes outside [p, p + len) are read only inside aligned 16-byte blocks that
@@ -135,38 +181,57 @@ __device__ __forceinline__ void digest_global(const uint8_t* p, uint64_t len, ui
             H::template compress<FMA>(st, X, one);
         }
     }
-    // Tail: rem < 64 bytes, then 0x80, zeros, 64-bit bit length.
-    const uint32_t rem = (uint32_t)(len & 63);
-    const uint64_t ta = addr + (full << 6);
-    const uint32_t sh = (uint32_t)(ta & 3) * 8;
-    const uint32_t* q = reinterpret_cast<const uint32_t*>(ta & ~uint64_t(3));
-    const uint32_t nwords = ((uint32_t)(ta & 3) + rem + 3) >> 2;  // aligned words holding tail bytes
-    uint32_t x[17];
+    digest_tail<H, FMA>(addr + (full << 6), len, st, X, one);
+}
+
+// digest_global for messages that mostly start off a 16-byte boundary (chunk
+// segments start wherever a content-defined cut fell): one code path for
+// every alignment, so the lanes of a warp never split between an aligned and
+// an unaligned loop.  Each block is assembled from five aligned 16-byte
+// vectors (the fifth is loaded only when the start is unaligned, so no vector
+// without a message byte is read).
+template <class H, bool FMA = true>
+__device__ __forceinline__ void digest_global_any(const uint8_t* p, uint64_t len, uint32_t (&st)[5], uint32_t one) {
+    H::init(st);
+    const uint64_t addr = reinterpret_cast<uint64_t>(p);
+    const uint64_t full = len >> 6;
+    const uint32_t o = (uint32_t)(addr & 15);
+    const uint32_t wq = o >> 2;
+    const uint32_t sh = (o & 3) * 8;
+    const uint8_t* q = reinterpret_cast<const uint8_t*>(addr - o);
+    uint32_t X[16];
+    uint4 nx[5];
+    if (full) {
 #pragma unroll
-    for (int k = 0; k < 17; ++k) x[k] = (uint32_t)k < nwords ? md5::ldg32(q + k) : 0u;
+        for (int v = 0; v < 4; ++v) nx[v] = md5::ldg_stream16(q + 16 * v);
+        nx[4] = o ? md5::ldg_stream16(q + 64) : make_uint4(0, 0, 0, 0);
+    }
+    for (uint64_t blk = 0; blk < full; ++blk) {
+        uint32_t w[20];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        uint32_t w = __funnelshift_r(x[k], x[k + 1], sh);
-        const int have = (int)rem - 4 * k;  // message bytes in this word
-        if (have <= 0) {
-            w = 0;
-        } else if (have < 4) {
-            w &= (1u << (8 * have)) - 1u;
+        for (int v = 0; v < 5; ++v) {
+            w[4 * v + 0] = nx[v].x;
+            w[4 * v + 1] = nx[v].y;
+            w[4 * v + 2] = nx[v].z;
+            w[4 * v + 3] = nx[v].w;
         }
-        if (have >= 0 && have < 4) w |= 0x80u << (8 * have);
-        X[k] = H::word(w);
-    }
-    const uint64_t bits = len << 3;
-    if (rem < 56) {
-        H::length(X, bits);
-        H::template compress<FMA>(st, X, one);
-    } else {
-        H::template compress<FMA>(st, X, one);
+        q += 64;
+        if (blk + 1 < full) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) X[k] = 0;
-        H::length(X, bits);
+            for (int v = 0; v < 4; ++v) nx[v] = md5::ldg_stream16(q + 16 * v);
+            nx[4] = o ? md5::ldg_stream16(q + 64) : make_uint4(0, 0, 0, 0);
+        }
+        uint32_t y1[19];
+#pragma unroll
+        for (int k = 0; k < 19; ++k) y1[k] = (wq & 1) ? w[k + 1] : w[k];
+        uint32_t y[17];
+#pragma unroll
+        for (int k = 0; k < 17; ++k) y[k] = (wq & 2) ? y1[k + 2] : y1[k];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) X[k] = H::word(__funnelshift_r(y[k], y[k + 1], sh));
         H::template compress<FMA>(st, X, one);
     }
+    digest_tail<H, FMA>(addr + (full << 6), len, st, X, one);
 }
 
 // Store a digest (memory byte order) at a 4-byte aligned address.

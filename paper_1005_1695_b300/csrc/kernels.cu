@@ -48,6 +48,7 @@ constexpr int kStageWords = 4 * ((kTile + 69 + 15) / 16) + 4;
 constexpr int kSegThreads = 128;
 constexpr int kChunkThreads = 512;
 constexpr int kDigestThreads = 256;
+constexpr int kChunkSegThreads = 128;  // K5a: 5 CTAs per SM at <= 102 registers
 constexpr int kScanThreads = 1024;
 
 constexpr uint32_t kDevBadRecord = 1u;
@@ -86,15 +87,18 @@ __device__ __forceinline__ uint32_t digest_bytes(const crystal_unit& X) { return
 __device__ __forceinline__ uint32_t record_bytes(const crystal_unit& X) { return 4u + digest_bytes(X); }
 
 // Digest of [p, p + len) with the unit's hash, stored at dst (4-byte aligned).
-template <bool FMA>
+// ANY: the single-path loader for messages that rarely start 16-byte aligned.
+template <bool FMA, bool ANY = false>
 __device__ __forceinline__ void digest_to(const crystal_unit& X, const uint8_t* p, uint64_t len, uint8_t* dst,
                                           uint32_t one) {
     uint32_t st[5];
     if (is_sha1(X)) {
-        digest_global<SHA1Hash, FMA>(p, len, st, one);
+        if constexpr (ANY) digest_global_any<SHA1Hash, FMA>(p, len, st, one);
+        else digest_global<SHA1Hash, FMA>(p, len, st, one);
         store_digest<SHA1Hash>(dst, st);
     } else {
-        digest_global<MD5Hash, FMA>(p, len, st, one);
+        if constexpr (ANY) digest_global_any<MD5Hash, FMA>(p, len, st, one);
+        else digest_global<MD5Hash, FMA>(p, len, st, one);
         store_digest<MD5Hash>(dst, st);
     }
 }
@@ -224,13 +228,57 @@ __device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t de
     return mine;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t* smem_dst, uint64_t gmem_src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+// The tile with the common 20-byte window.  Lane (g, s) = (lane / 4, lane % 4)
+// of a warp hashes the windows at offsets 32 g + s + 4 j, j = 0..7, of the
+// warp's 256: consecutive windows of a thread are one word apart, so they
+// share the byte phase and all but one message word, and the thread shifts
+// 12 words into place for its 8 windows instead of 40.  Each hit becomes bit
+// s + 4 j of the thread's mask; the four lanes of a group then OR their masks
+// into bitmap word g, which is moved to lane g (the layout of tile_windows).
+template <class H>
+__device__ __forceinline__ uint32_t tile_windows20(const uint32_t* sw, uint32_t delta, uint32_t lim, uint32_t mask,
+                                                   uint32_t target, uint32_t one) {
+    static_assert(kWinPerThread == 8 && kWinThreads == 256, "lane layout assumes 8 warps x 8 windows");
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t sub = lane & 3;
+    const uint32_t rel0 = warp * 256 + (lane >> 2) * 32 + sub;
+    const uint32_t p = rel0 + delta;
+    const uint32_t* s = sw + (p >> 2);
+    const uint32_t sh = (p & 3) * 8;
+    uint32_t M[5];  // message words 0..4 of the current window
+    uint32_t raw = s[0];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const uint32_t nxt = s[k + 1];
+        M[k] = __funnelshift_r(raw, nxt, sh);
+        raw = nxt;
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t X[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) X[k] = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) X[k] = M[k];
+        X[5] = 0x80u;
+        X[14] = 8u * 20;
+        const uint32_t A = window_first_word<H>(X, 20u, one);
+        const bool hit = (rel0 + 4 * j + 20 <= lim) && ((A & mask) == target);
+        m |= (uint32_t)hit << (sub + 4 * j);
+        if (j < 7) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) M[k] = M[k + 1];
+            const uint32_t nxt = s[j + 6];
+            M[4] = __funnelshift_r(raw, nxt, sh);
+            raw = nxt;
+        }
+    }
+    m |= __shfl_xor_sync(0xffffffffu, m, 1);
+    m |= __shfl_xor_sync(0xffffffffu, m, 2);
+    return __shfl_sync(0xffffffffu, m, (lane & 7) * 4);
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Owner of tile g >= the tiles of unit u: a short forward walk (the next
 // tile of a CTA is usually in the same unit or the next one), else a binary
@@ -309,9 +357,11 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_sliding_windows(crystal_b
         const uint32_t lim = left < (uint64_t)(2 * kTile) ? (uint32_t)left : (uint32_t)(2 * kTile);
         const uint32_t w = W > 0 ? (uint32_t)W : (uint32_t)X.window;
         uint32_t mine;
-        if (W == 0 && H::kWords == 5 && w == 20) {
+        if constexpr (W == 20) {
+            mine = tile_windows20<H>(sw[buf], delta, lim, X.mask, X.target, one);
+        } else if (H::kWords == 5 && w == 20) {
             // SHA-1 units with the common window: padding words fold at compile time
-            mine = tile_windows<20, H>(sw[buf], delta, lim, 20u, X.mask, X.target, one);
+            mine = tile_windows20<H>(sw[buf], delta, lim, X.mask, X.target, one);
         } else {
             mine = tile_windows<W, H>(sw[buf], delta, lim, w, X.mask, X.target, one);
         }
@@ -357,9 +407,81 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* s
     return before;
 }
 
+__device__ __forceinline__ uint64_t warp_sum(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_inclusive_scan(uint64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per warp over the block's warps: returns this
+// warp's start; total receives the block's sum.  sh holds NT/32 + 1 entries.
+template <int NT>
+__device__ __forceinline__ uint64_t warp_starts(uint64_t warp_total, uint64_t* sh, uint64_t& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    if (lane == 0) sh[warp] = warp_total;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t v = lane < NW ? sh[lane] : 0;
+        const uint64_t x = warp_inclusive_scan(v);
+        if (lane < NW) sh[lane] = x - v;
+        if (lane == NW - 1) sh[NW] = x;
+    }
+    __syncthreads();
+    const uint64_t start = sh[warp];
+    total = sh[NW];
+    __syncthreads();
+    return start;
+}
+
+// Bitmap words a warp reads per pass iteration: each lane loads four 16-byte
+// vectors, vector r of the warp covering words [128 r, 128 r + 128).
+constexpr uint32_t kChunkWarpWords = 512;
+
+// Words [j, j + 4) of the bitmap, zero past `words`; j is a multiple of 4, so
+// every such group has the alignment `al` (address mod 16) of the bitmap,
+// which picks the widest load allowed (the output buffer is only 4-byte
+// aligned in general).
+__device__ __forceinline__ uint4 bitmap_vec(const uint32_t* bm, uint64_t j, uint64_t words, uint32_t al) {
+    if (j + 4 <= words) {
+        if (al == 0) return *reinterpret_cast<const uint4*>(bm + j);
+        if ((al & 7) == 0) {
+            const uint2 a = *reinterpret_cast<const uint2*>(bm + j);
+            const uint2 b = *reinterpret_cast<const uint2*>(bm + j + 2);
+            return make_uint4(a.x, a.y, b.x, b.y);
+        }
+        return make_uint4(bm[j], bm[j + 1], bm[j + 2], bm[j + 3]);
+    }
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (j < words) v.x = bm[j];
+    if (j + 1 < words) v.y = bm[j + 1];
+    if (j + 2 < words) v.z = bm[j + 2];
+    return v;
+}
+
+__device__ __forceinline__ uint32_t popc4(uint4 v) {
+    return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+}
+
+// One CTA per sliding unit.  Each warp owns a contiguous range of bitmap words
+// (then of chunks) and reads it kChunkWarpWords words per iteration with
+// vector loads (coalesced, four in flight per lane); prefix counts inside a
+// warp come from shuffles, across warps from one scan of the warp totals.
 __global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch* B) {
-    __shared__ uint64_t scan_sh[kChunkThreads / 32 + 1];
+    __shared__ uint64_t sh[kChunkThreads / 32 + 1];
+    constexpr uint32_t NW = kChunkThreads / 32;
     const uint32_t ns = B->n_sliding;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     crystal_unit* U = units_of(B) + B->n_direct;
     for (uint32_t u = blockIdx.x; u < ns; u += gridDim.x) {
         const crystal_unit X = U[u];
@@ -368,6 +490,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch*
         const uint64_t fixed = 8 + 4 * words;
         uint32_t* hdr = reinterpret_cast<uint32_t*>(X.out);
         const uint32_t* bm = hdr + 2;
+        const uint32_t al = (uint32_t)(reinterpret_cast<uint64_t>(bm) & 15);
         uint32_t* seg_prefix = reinterpret_cast<uint32_t*>(X.scratch);
         if (X.out_cap < fixed) {
             if (threadIdx.x == 0) {
@@ -377,14 +500,20 @@ __global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch*
             continue;
         }
         const uint64_t cap = (X.out_cap - fixed) / record_bytes(X);
-        // pass 1: boundary count per contiguous word range
-        const uint64_t per = (words + kChunkThreads - 1) / kChunkThreads;
-        const uint64_t lo = threadIdx.x * per;
-        const uint64_t hi = lo + per < words ? lo + per : words;
-        uint64_t cnt = 0;
-        for (uint64_t j = lo; j < hi; ++j) cnt += __popc(bm[j]);
+        // pass 1: boundaries per warp range (ranges are whole iterations)
+        const uint64_t iters = (words + NW * kChunkWarpWords - 1) / (NW * kChunkWarpWords);
+        const uint64_t w0 = (uint64_t)warp * iters * kChunkWarpWords;
+        const uint64_t w1 = min(words, w0 + iters * kChunkWarpWords);
+        uint32_t cnt = 0;
+        for (uint64_t j0 = w0; j0 < w1; j0 += kChunkWarpWords) {
+            uint4 v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[r] = bitmap_vec(bm, j0 + 128 * r + 4 * lane, w1, al);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) cnt += popc4(v[r]);
+        }
         uint64_t pop;
-        uint64_t k = block_exclusive_scan<kChunkThreads>(cnt, scan_sh, pop);
+        uint64_t k = warp_starts<kChunkThreads>(warp_sum(cnt), sh, pop);
         bool last_set = false;
         if (n >= X.window) {
             const uint64_t i = n - X.window;
@@ -404,33 +533,56 @@ __global__ void __launch_bounds__(kChunkThreads) k_sliding_chunks(crystal_batch*
             __syncthreads();
             continue;
         }
+        // pass 2: chunk ends, in bit order
         uint32_t* ends = hdr + 2 + words;
-        for (uint64_t j = lo; j < hi; ++j) {
-            uint32_t x = bm[j];
-            while (x) {
-                const int b = __ffs(x) - 1;
-                x &= x - 1;
-                ends[k++] = (uint32_t)(32 * j + b + X.window);
+        for (uint64_t j0 = w0; j0 < w1; j0 += kChunkWarpWords) {
+            uint4 v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[r] = bitmap_vec(bm, j0 + 128 * r + 4 * lane, w1, al);
+            // per-vector counts fit 16 bits even summed over the warp (<= 4096)
+            const uint32_t c01 = popc4(v[0]) | (popc4(v[1]) << 16);
+            const uint32_t c23 = popc4(v[2]) | (popc4(v[3]) << 16);
+            const uint32_t i01 = (uint32_t)warp_inclusive_scan(c01);
+            const uint32_t i23 = (uint32_t)warp_inclusive_scan(c23);
+            const uint32_t t01 = __shfl_sync(0xffffffffu, i01, 31), t23 = __shfl_sync(0xffffffffu, i23, 31);
+            const uint32_t tot[4] = {t01 & 0xffffu, t01 >> 16, t23 & 0xffffu, t23 >> 16};
+            const uint32_t exc[4] = {(i01 - c01) & 0xffffu, (i01 - c01) >> 16, (i23 - c23) & 0xffffu,
+                                     (i23 - c23) >> 16};
+            uint64_t before = k;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                uint64_t pos = before + exc[r];
+                const uint32_t x4[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    uint32_t x = x4[e];
+                    const uint64_t j = j0 + 128 * r + 4 * lane + e;
+                    while (x) {
+                        const int b = __ffs(x) - 1;
+                        x &= x - 1;
+                        ends[pos++] = (uint32_t)(32 * j + b + X.window);
+                    }
+                }
+                before += tot[r];
             }
+            k = before;
         }
         if (threadIdx.x == 0 && !last_set) ends[n_chunks - 1] = (uint32_t)n;
         __syncthreads();
-        // pass 2: segments per chunk, exclusive prefix into the scratch table
-        const uint64_t cper = (n_chunks + kChunkThreads - 1) / kChunkThreads;
-        const uint64_t clo = threadIdx.x * cper;
-        const uint64_t chi = clo + cper < n_chunks ? clo + cper : n_chunks;
+        // pass 3: segments per chunk, exclusive prefix into the scratch table
         const uint32_t S = X.seg_bytes;
+        const uint64_t cper = (((n_chunks + NW - 1) / NW) + 31) & ~uint64_t(31);
+        const uint64_t c0 = min(n_chunks, (uint64_t)warp * cper), c1 = min(n_chunks, c0 + cper);
         uint64_t segs = 0;
-        for (uint64_t c = clo; c < chi; ++c) {
-            const uint64_t start = c == 0 ? 0 : ends[c - 1];
-            segs += num_segments(ends[c] - start, S);
-        }
+        for (uint64_t c = c0 + lane; c < c1; c += 32) segs += num_segments(ends[c] - (c ? ends[c - 1] : 0u), S);
         uint64_t total_segs;
-        uint64_t run = block_exclusive_scan<kChunkThreads>(segs, scan_sh, total_segs);
-        for (uint64_t c = clo; c < chi; ++c) {
-            seg_prefix[c] = (uint32_t)run;
-            const uint64_t start = c == 0 ? 0 : ends[c - 1];
-            run += num_segments(ends[c] - start, S);
+        uint64_t run = warp_starts<kChunkThreads>(warp_sum(segs), sh, total_segs);
+        for (uint64_t b0 = c0; b0 < c1; b0 += 32) {
+            const uint64_t c = b0 + lane;
+            const uint64_t m = c < c1 ? num_segments(ends[c] - (c ? ends[c - 1] : 0u), S) : 0;
+            const uint64_t incl = warp_inclusive_scan(m);
+            if (c < c1) seg_prefix[c] = (uint32_t)(run + incl - m);
+            run += __shfl_sync(0xffffffffu, incl, 31);
         }
         if (threadIdx.x == 0) {
             seg_prefix[n_chunks] = (uint32_t)total_segs;
@@ -475,8 +627,17 @@ __device__ __forceinline__ uint8_t* chunk_digest_area(const crystal_unit& X, uin
 // ---- K5a: chunk segment digests ---------------------------------------------
 
 // One thread per chunk segment of the whole batch: the unit comes from the
-// starts K4b wrote, the chunk from the unit's segment table.
-__global__ void __launch_bounds__(kDigestThreads, 2) k_chunk_segments(crystal_batch* B, uint32_t one) {
+// starts K4b wrote, the chunk from the unit's segment table.  Neighbouring
+// lanes hash neighbouring segments, which keeps the DRAM streams of a warp
+// close together (dealing segments round-robin over CTAs was measured twice as
+// slow).  Chunks start at arbitrary byte offsets, hence the single-path
+// loader; the kernel is bound by the integer ALU pipe (staging its blocks
+// through shared memory to have more in flight was measured slower).
+#ifndef CRYSTAL_DIGEST_MIN_BLOCKS
+#define CRYSTAL_DIGEST_MIN_BLOCKS 5
+#endif
+__global__ void __launch_bounds__(kChunkSegThreads, CRYSTAL_DIGEST_MIN_BLOCKS) k_chunk_segments(crystal_batch* B,
+                                                                                          uint32_t one) {
     const uint32_t ns = B->n_sliding;
     const crystal_unit* U = units_of(B) + B->n_direct;
     const uint64_t total = B->chunk_segments;
@@ -506,8 +667,8 @@ __global__ void __launch_bounds__(kDigestThreads, 2) k_chunk_segments(crystal_ba
         const uint64_t end = ends[clo];
         const uint64_t off = start + (uint64_t)(t - seg_prefix[clo]) * S;
         const uint64_t len = end > off ? (end - off < S ? end - off : S) : 0;
-        digest_to<CRYSTAL_FMA_SEGMENTS>(X, reinterpret_cast<const uint8_t*>(X.in) + off, len,
-                                        chunk_digest_area(X, cap) + (uint64_t)digest_bytes(X) * t, one);
+        digest_to<CRYSTAL_FMA_SEGMENTS, true>(X, reinterpret_cast<const uint8_t*>(X.in) + off, len,
+                                              chunk_digest_area(X, cap) + (uint64_t)digest_bytes(X) * t, one);
     }
 }
 
@@ -578,7 +739,7 @@ const Geometry* geometry() {
         g.win20_blocks = g.sms * resident((const void*)kWin20, kWinThreads);
         g.win_blocks = g.sms * resident((const void*)kWinAny, kWinThreads);
         g.win_sha1_blocks = g.sms * resident((const void*)kWinSha1, kWinThreads);
-        g.digest_blocks = g.sms * resident((const void*)k_chunk_segments, kDigestThreads);
+        g.digest_blocks = g.sms * resident((const void*)k_chunk_segments, kChunkSegThreads);
         g.outer_blocks = g.sms * 2;
         g.unit_blocks = g.sms * 2;
         g_geom[dev] = g;
@@ -637,7 +798,7 @@ int launch_sliding_chunks(crystal_batch* b, cudaStream_t s) {
 int launch_sliding_digests(crystal_batch* b, cudaStream_t s) {
     const Geometry* g = geometry();
     if (!g) return CRYSTAL_EDEVICE;
-    k_chunk_segments<<<g->digest_blocks, kDigestThreads, 0, s>>>(b, g_one);
+    k_chunk_segments<<<g->digest_blocks, kChunkSegThreads, 0, s>>>(b, g_one);
     k_chunk_outer<<<g->unit_blocks, kDigestThreads, 0, s>>>(b, g_one);
     return launched(2);
 }

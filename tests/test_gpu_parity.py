@@ -50,9 +50,10 @@ def _pack(torch, units, align_offsets=None):
     return torch.from_numpy(host).cuda(), offs
 
 
-def _run(torch, C, units, kinds, plist, out_sizes=None, align=None, mode="batch"):
+def _run(torch, C, units, kinds, plist, out_sizes=None, align=None, mode="batch", out_misalign=None):
     d_in, offs = _pack(torch, units, align)
-    b = C.DeviceBatch(d_in, offs, [len(u) for u in units], kinds, out_sizes=out_sizes, per_unit_params=plist)
+    b = C.DeviceBatch(d_in, offs, [len(u) for u in units], kinds, out_sizes=out_sizes, per_unit_params=plist,
+                      out_misalign=out_misalign)
     if mode == "batch":
         b.launch()
     else:
@@ -144,6 +145,23 @@ def test_sliding_ragged_tiles(torch_cuda, C, oracle_mod, w, S):
     outs = [C.sliding_out_bytes(n, n // 16 + 8) for n in sizes]
     got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 1, 2, 3, 7, 13])
     want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    _compare(units, kinds, got, want)
+
+
+@pytest.mark.parametrize("hash_kind", [SLIDING, 4])
+def test_sliding_output_alignments_dense_cuts(torch_cuda, C, oracle_mod, hash_kind):
+    # outputs at every 4-byte alignment mod 16 (the bitmap scan picks its load
+    # width from it); units long enough that each of the chunk kernel's warps
+    # walks several iterations of bitmap words, and a mask with many cuts per
+    # bitmap word so cut positions interleave across lanes and vectors
+    sizes = [300000, 262144 + 4096 * 3 + 5, 1 << 20, 40000, 17]
+    units = [_rand(7000 + i, n) for i, n in enumerate(sizes)]
+    kinds = [hash_kind] * len(units)
+    plist = [C.params(window_bytes=20, mask=0x3F, target=0x2A, chunk_segment_bytes=1000)] * len(units)
+    outs = [C.sliding_out_bytes(n, n // 32 + 8, hash_kind) for n in sizes]
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 5, 11, 2, 8], out_misalign=[4, 8, 12, 0])
+    want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    assert all(st == 0 for st, _ in want)
     _compare(units, kinds, got, want)
 
 
