@@ -62,8 +62,8 @@ INT_LANES_PER_SM = 128  # 4 schedulers x one 32-lane instruction per clock
 # DRAM bytes (read + write) of the window kernel per 1 MiB sliding unit, from one
 # ncu capture of 160 units (traffic grows with the units processed), valid only
 # for the kernel sources it was taken on (checked by hash; otherwise null).
-WINDOW_TRAFFIC_PER_UNIT = (167.846656e6 + 14.420736e6) / 160
-WINDOW_TRAFFIC_SOURCES = "14be97120abb608f"
+WINDOW_TRAFFIC_PER_UNIT = (167.845376e6 + 14.420480e6) / 160
+WINDOW_TRAFFIC_SOURCES = "4e41a49edae754ca"
 
 
 def _kernel_sources_hash() -> str:
@@ -391,7 +391,9 @@ def run_ours(args, ws, rank, local):
                                "mask=target=0x1FFF, chunk direct hash S=4 KiB",
                    "units_per_gpu": U, "unit_bytes": N, "window": 20, "mask": 0x1FFF, "target": 0x1FFF,
                    "chunk_segment_bytes": 4096, "content": "50% repeated 8 KiB blocks from a pool of 64",
-                   "l2": "inputs (256 MiB per step) larger than L2 (126 MB); no flush",
+                   "l2": (f"inputs ({U * N / 2**20:.0f} MiB per step) larger than L2 (126 MB); no flush"
+                          if U * N > 126e6 else f"inputs ({U * N / 2**20:.0f} MiB per step) fit in L2 (126 MB); "
+                                                  "no flush: a small case, not a bench line"),
                    "parallelism": f"replicas x{ws}", "streams": args.streams, "batch_jobs": args.batch_jobs,
                    "graphs": bool(args.graphs)},
         "roofline": {"bound": "alu", "kernel": "k_sliding_windows", "achieved": round(achieved, 3),
