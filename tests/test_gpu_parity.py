@@ -280,3 +280,19 @@ def test_md5_and_sha1_mixed_batch(torch_cuda, C, oracle_mod):
     got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 1, 16, 3])
     want = _oracle_all(oracle_mod, units, kinds, plist, outs)
     _compare(units, kinds, got, want)
+
+
+def test_largest_units_full_oracle(torch_cuda, C, oracle_mod):
+    """The largest units the workloads use (64 MiB, the cap of the served
+    request sizes; a 64 MiB direct unit; a 16 MiB SHA-1 sliding unit), ragged
+    by a few bytes and misaligned, every output byte against the oracle."""
+    sizes = [(64 << 20) + 13, (64 << 20) - 5, (16 << 20) + 3]
+    kinds = [SLIDING, DIRECT, SHA1_SLIDING]
+    units = [_rand(9100 + i, n) for i, n in enumerate(sizes)]
+    plist = [C.params()] * 3
+    outs = [C.sliding_out_bytes(sizes[0], sizes[0] // 4096 + 64), 16,
+            C.sliding_out_bytes(sizes[2], sizes[2] // 4096 + 64, SHA1_SLIDING)]
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[3, 0, 9])
+    want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    assert [st for st, _ in want] == [0, 0, 0]
+    _compare(units, kinds, got, want)
