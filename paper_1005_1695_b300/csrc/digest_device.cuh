@@ -64,8 +64,8 @@ struct SHA1Hash {
         st[4] = sha1::kH4;
     }
     template <bool FMA>
-    __device__ static void compress(uint32_t (&st)[5], uint32_t (&X)[16], uint32_t) {
-        sha1::compress(st, X);
+    __device__ static void compress(uint32_t (&st)[5], uint32_t (&X)[16], uint32_t one) {
+        sha1::compress(st, X, one);
     }
     __device__ static uint32_t word(uint32_t memory_order) { return sha1::bswap(memory_order); }
     __device__ static void length(uint32_t (&X)[16], uint64_t bits) {

@@ -196,7 +196,7 @@ __device__ __forceinline__ uint32_t window_first_word(uint32_t (&X)[16], uint32_
         for (int k = 0; k < 14; ++k) X[k] = sha1::bswap(X[k]);
         X[14] = 0;
         X[15] = 8u * w;
-        return sha1::bswap(sha1::first_word_one_block(X));
+        return sha1::bswap(sha1::first_word_one_block(X, one));
     } else {
         return md5::first_word_one_block(X, one);
     }

@@ -10,8 +10,25 @@
 
 #include <utility>
 
+// Which adds of a step issue on the FMA pipe: 0 none (the compiler's choice),
+// 1 the add of the round function f, 2 that and the add of a <<< 5.  SHA-1's
+// two rotates and its logic op only run on the integer ALU pipe; on B300, 1
+// was measured 1.2% faster than 0 in the window kernel and 4.6% in the chunk
+// digests, and 2 slower than both.
+#ifndef CRYSTAL_SHA1_FMA
+#define CRYSTAL_SHA1_FMA 1
+#endif
+
 namespace crystal {
 namespace sha1 {
+
+// x * one + y issued on the FMA pipe (`one` is a run-time 1 the compiler
+// cannot fold), leaving the integer ALU pipe to the rotates and logic ops.
+__device__ __forceinline__ uint32_t add_fma(uint32_t x, uint32_t one, uint32_t y) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(y));
+    return d;
+}
 
 constexpr uint32_t kH0 = 0x67452301u;
 constexpr uint32_t kH1 = 0xefcdab89u;
@@ -32,7 +49,7 @@ __device__ __forceinline__ uint32_t bswap(uint32_t x) { return __byte_perm(x, 0,
 // Ch / Parity / Maj / Parity, then (a, b, c, d, e) <- (T, a, b<<<30, c, d).
 template <int T>
 __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d, uint32_t& e,
-                                     uint32_t (&W)[16]) {
+                                     uint32_t (&W)[16], uint32_t one) {
     if constexpr (T >= 16) {
         W[T & 15] = rotl(W[(T - 3) & 15] ^ W[(T - 8) & 15] ^ W[(T - 14) & 15] ^ W[T & 15], 1);
     }
@@ -44,7 +61,14 @@ __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint
     } else {
         f = (b & c) | (d & (b | c));      // Maj
     }
-    const uint32_t t = rotl(a, 5) + f + (e + (kK(T) + W[T & 15]));
+    uint32_t t;
+    if constexpr (CRYSTAL_SHA1_FMA == 2) {
+        t = add_fma(rotl(a, 5), one, add_fma(f, one, e + (kK(T) + W[T & 15])));
+    } else if constexpr (CRYSTAL_SHA1_FMA == 1) {
+        t = add_fma(f, one, rotl(a, 5) + (e + (kK(T) + W[T & 15])));
+    } else {
+        t = rotl(a, 5) + f + (e + (kK(T) + W[T & 15]));
+    }
     e = d;
     d = c;
     c = rotl(b, 30);
@@ -54,14 +78,14 @@ __device__ __forceinline__ void step(uint32_t& a, uint32_t& b, uint32_t& c, uint
 
 template <int... T>
 __device__ __forceinline__ void steps_seq(std::integer_sequence<int, T...>, uint32_t& a, uint32_t& b, uint32_t& c,
-                                          uint32_t& d, uint32_t& e, uint32_t (&W)[16]) {
-    (step<T>(a, b, c, d, e, W), ...);
+                                          uint32_t& d, uint32_t& e, uint32_t (&W)[16], uint32_t one) {
+    (step<T>(a, b, c, d, e, W, one), ...);
 }
 
 // One block: W holds the 16 big-endian message words and is consumed.
-__device__ __forceinline__ void compress(uint32_t (&st)[5], uint32_t (&W)[16]) {
+__device__ __forceinline__ void compress(uint32_t (&st)[5], uint32_t (&W)[16], uint32_t one) {
     uint32_t a = st[0], b = st[1], c = st[2], d = st[3], e = st[4];
-    steps_seq(std::make_integer_sequence<int, 80>{}, a, b, c, d, e, W);
+    steps_seq(std::make_integer_sequence<int, 80>{}, a, b, c, d, e, W, one);
     st[0] += a;
     st[1] += b;
     st[2] += c;
@@ -70,9 +94,9 @@ __device__ __forceinline__ void compress(uint32_t (&st)[5], uint32_t (&W)[16]) {
 }
 
 // H0 of a one-block message (W consumed), i.e. big-endian digest bytes 0..3.
-__device__ __forceinline__ uint32_t first_word_one_block(uint32_t (&W)[16]) {
+__device__ __forceinline__ uint32_t first_word_one_block(uint32_t (&W)[16], uint32_t one) {
     uint32_t a = kH0, b = kH1, c = kH2, d = kH3, e = kH4;
-    steps_seq(std::make_integer_sequence<int, 80>{}, a, b, c, d, e, W);
+    steps_seq(std::make_integer_sequence<int, 80>{}, a, b, c, d, e, W, one);
     return kH0 + a;
 }
 
