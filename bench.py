@@ -156,22 +156,44 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def measure_link(torch, dev, total: int, n_streams: int = 8, chunk: int = 8 << 20, reps: int = 3) -> dict:
+def measure_link(torch, dev, total: int, n_streams: int = 8, chunk: int = 8 << 20, reps: int = 3,
+                 out_fraction: float = 0.0) -> dict:
     """Pinned host <-> device copy bandwidth: one stream copying ``total`` bytes
-    at once, and ``n_streams`` streams copying ``chunk``-byte pieces
-    concurrently (which can use several copy engines).  Best of ``reps``."""
-    pinned = torch.empty(total, dtype=torch.uint8).pin_memory()
+    at once, ``n_streams`` streams copying ``chunk``-byte pieces concurrently
+    (which can use several copy engines), and -- when ``out_fraction`` > 0 --
+    ``total`` bytes in while ``out_fraction`` x ``total`` bytes come back on a
+    second stream (both directions share the link).  Best of ``reps``.
+
+    The pinned buffer is allocated pinned and written by one thread: filling
+    it with a multi-threaded torch copy leaves torch's worker threads spinning
+    on every core for a while, and host-to-device copies measured meanwhile
+    were up to 30% slower on the B300 machines."""
+    pinned = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[:] = 1
     dbuf = torch.empty(total, dtype=torch.uint8, device=dev)
     streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
+    n_out = int(total * out_fraction) & ~4095
+    if n_out:
+        pinned_out = torch.empty(n_out, dtype=torch.uint8, pin_memory=True)
+        dout = torch.ones(n_out, dtype=torch.uint8, device=dev)
 
-    def timed(h2d: bool, multi: bool) -> float:
+    def timed(h2d: bool, multi: bool, duplex: bool = False) -> float:
         best = 0.0
         for _ in range(reps + 1):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             cur = torch.cuda.current_stream()
             a.record(cur)
-            if not multi:
+            if duplex:
+                for s in streams[:2]:
+                    s.wait_event(a)
+                with torch.cuda.stream(streams[0]):
+                    dbuf.copy_(pinned, non_blocking=True)
+                with torch.cuda.stream(streams[1]):
+                    pinned_out.copy_(dout, non_blocking=True)
+                for s in streams[:2]:
+                    cur.wait_stream(s)
+            elif not multi:
                 (dbuf.copy_(pinned, non_blocking=True) if h2d else pinned.copy_(dbuf, non_blocking=True))
             else:
                 for s in streams:
@@ -184,13 +206,18 @@ def measure_link(torch, dev, total: int, n_streams: int = 8, chunk: int = 8 << 2
                     cur.wait_stream(s)
             b.record(cur)
             torch.cuda.synchronize()
-            best = max(best, total / (a.elapsed_time(b) / 1e3) / GB)
+            moved = total + (n_out if duplex else 0)
+            best = max(best, moved / (a.elapsed_time(b) / 1e3) / GB)
         return best
 
     out = {"h2d_single_gbs": timed(True, False), "h2d_multi_gbs": timed(True, True),
            "d2h_single_gbs": timed(False, False), "d2h_multi_gbs": timed(False, True)}
+    if n_out:
+        out["duplex_gbs"] = timed(True, False, duplex=True)
     out = {k: round(v, 2) for k, v in out.items()}
-    out["how"] = f"torch pinned copies of {total >> 20} MiB: one stream, and {n_streams} streams x {chunk >> 20} MiB"
+    out["how"] = (f"torch pinned copies of {total >> 20} MiB: one stream, and {n_streams} streams x {chunk >> 20} MiB"
+                  + (f"; duplex: {total >> 20} MiB in while {n_out >> 20} MiB come back, bytes of both per second"
+                     if n_out else ""))
     del pinned, dbuf
     return out
 
@@ -315,50 +342,61 @@ def run_ours(args, ws, rank, local):
 
     # ---- e2e: job API, pinned host buffers, copies inside the timed region ----
     if "e2e" in args.legs:
-        pool_dev = int(total_bytes + U * (out_size + C.scratch_bytes(KIND, N, out_size, p) + 4096) + (64 << 20))
-        pool_host = int(total_bytes + U * (out_size + 4096) + (16 << 20))
+        n_sets = max(1, args.e2e_sets)
+        pool_dev = int(n_sets * (total_bytes + U * (out_size + C.scratch_bytes(KIND, N, out_size, p) + 4096))
+                       + (64 << 20))
+        pool_host = int(n_sets * (total_bytes + U * (out_size + 4096)) + (16 << 20))
         ctx = C.Context(max_in_bytes=N, max_out_bytes=out_size, device_pool_bytes=pool_dev,
                         host_pool_bytes=pool_host, n_streams=args.streams, max_batch_jobs=args.batch_jobs,
                         max_batch_bytes=args.batch_jobs * N, device=local,
                         flags=C.CRYSTAL_FLAG_GRAPHS if args.graphs else 0)
-        tasks = [ctx.task_create(N, out_size) for _ in range(U)]
-        for u, t in enumerate(tasks):
-            t.h_in[:] = host[u * N:(u + 1) * N]
+        # n_sets job sets of U units each (the same bytes), used in turn: step
+        # k + 1 is submitted before step k is waited for, as a streaming
+        # application keeps the pipeline full
+        sets = []
+        for _ in range(n_sets):
+            tasks = [ctx.task_create(N, out_size) for _ in range(U)]
+            for u, t in enumerate(tasks):
+                t.h_in[:] = host[u * N:(u + 1) * N]
+            sets.append((tasks, ctx.task_array(tasks)))
 
-        def e2e_step():
-            st = ctx.submit_many(tasks, KIND, p)
-            assert st == C.CRYSTAL_OK, st
-            for t in tasks:
-                s = t.wait(60_000_000_000)
-                assert s == C.CRYSTAL_OK, s
-            return [t.timing() for t in tasks]
+        def run_steps(n_steps, kind):
+            """n_steps steps, each one submit of a job set and one wait for it
+            (one call each), n_sets - 1 steps ahead; returns the stamps."""
+            stamps = []
+            for k in range(min(n_sets - 1, n_steps)):
+                C.check(ctx.submit_many(sets[k % n_sets][1], kind, p), "submit_many")
+            for i in range(n_steps):
+                if i + n_sets - 1 < n_steps:
+                    C.check(ctx.submit_many(sets[(i + n_sets - 1) % n_sets][1], kind, p), "submit_many")
+                h = sets[i % n_sets][1]
+                C.check(ctx.wait_many(h, 60_000_000_000), "wait_many")
+                stamps.append(ctx.timing_many(h))
+            return stamps
 
-        for _ in range(args.warmup):
-            e2e_step()
+        run_steps(max(args.warmup, n_sets), KIND)
         # the job outputs must equal the device-resident outputs, unit by unit
         got_dev = batch.outputs()
-        for u in range(0, U, max(1, U // 16)):
-            n_chunks = int.from_bytes(got_dev[u][:4], "little")
-            used = 8 + 4 * (N // 32) + (4 + C.digest_size(KIND)) * n_chunks
-            assert tasks[u].output()[:used] == got_dev[u][:used], "job output differs from device batch output"
+        for tasks, _ in sets:
+            for u in range(0, U, max(1, U // 16)):
+                n_chunks = int.from_bytes(got_dev[u][:4], "little")
+                used = 8 + 4 * (N // 32) + (4 + C.digest_size(KIND)) * n_chunks
+                assert tasks[u].output()[:used] == got_dev[u][:used], "job output differs from device batch output"
         lat = []
         launches1 = C.kernel_launches()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            for s_ns, _, d_ns in e2e_step():
-                lat.append((d_ns - s_ns) / 1e6)
+        stamps = run_steps(args.steps, KIND)
         barrier()
         e2e_wall = slowest(time.perf_counter() - t0)
+        for tm in stamps:
+            lat.extend(((tm[:, 2] - tm[:, 0]).astype(np.float64) / 1e6).tolist())
         launches = launches_value + C.kernel_launches() - launches1
         clock_info = clocks.stop()
         e2e_value = aggregate_gbs(ws, total_bytes, args.steps, e2e_wall)
         # the same job shapes with the dummy kernel (copies only): the transfer ceiling
         t1 = time.perf_counter()
-        for _ in range(args.steps):
-            C.check(ctx.submit_many(tasks, C.CRYSTAL_KIND_NOP, p), "submit_many")
-            for t in tasks:
-                assert t.wait(60_000_000_000) == C.CRYSTAL_OK
+        run_steps(args.steps, C.CRYSTAL_KIND_NOP)
         copy_only = aggregate_gbs(ws, total_bytes, args.steps, slowest(time.perf_counter() - t1))
     else:
         clock_info = clocks.stop()
@@ -366,9 +404,13 @@ def run_ours(args, ws, rank, local):
         tasks, ctx = [], None
 
     # ---- host link (pinned copies) measured on this GPU ----
-    link = measure_link(torch, dev, total_bytes)
+    out_bytes = U * out_size
+    link = measure_link(torch, dev, total_bytes, out_fraction=out_bytes / total_bytes)
     h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
     d2h = max(link["d2h_single_gbs"], link["d2h_multi_gbs"])
+    # both directions at once share the link: input rate when the outputs
+    # come back concurrently
+    duplex_in = link["duplex_gbs"] * total_bytes / (total_bytes + out_bytes)
 
     # ---- roofline of the window kernel ----
     windows = U * (N - 20 + 1)
@@ -381,7 +423,7 @@ def run_ours(args, ws, rank, local):
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak = SM_COUNT_B300 * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
     alu_bound_gbs = peak * 1e12 / ops_per_window  # windows/s = bytes/s
-    e2e_bound = min(h2d * GB, alu_bound_gbs, d2h * GB * total_bytes / (U * out_size)) / GB
+    e2e_bound = min(h2d * GB, duplex_in * GB, alu_bound_gbs, d2h * GB * total_bytes / out_bytes) / GB
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
@@ -395,6 +437,7 @@ def run_ours(args, ws, rank, local):
                           if U * N > 126e6 else f"inputs ({U * N / 2**20:.0f} MiB per step) fit in L2 (126 MB); "
                                                   "no flush: a small case, not a bench line"),
                    "parallelism": f"replicas x{ws}", "streams": args.streams, "batch_jobs": args.batch_jobs,
+                   "e2e_job_sets": args.e2e_sets,
                    "graphs": bool(args.graphs)},
         "roofline": {"bound": "alu", "kernel": "k_sliding_windows", "achieved": round(achieved, 3),
                      "peak": round(peak, 3), "unit": "Tops/s (int32)", "frac": round(achieved / peak, 4),
@@ -408,8 +451,9 @@ def run_ours(args, ws, rank, local):
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                            "p99": round(float(np.percentile(lat, 99)), 3)},
             "roofline_gbs": round(e2e_bound, 2), "frac": round(e2e_value / ws / e2e_bound, 4),
-            "roofline_basis": "min(best measured H2D, best measured D2H scaled to the output bytes, "
-                              "issue-rate ALU bound of the window kernel)",
+            "roofline_basis": "min(best measured H2D, measured H2D+D2H duplex rate scaled to the input share, "
+                              "best measured D2H scaled to the output bytes, issue-rate ALU bound of the window "
+                              "kernel)",
             "copy_only_gbs": round(copy_only, 3),
             "copy_only_note": "the same jobs with the dummy kernel: copy-in and copy-out only"},
         "host_link": link,
@@ -747,6 +791,8 @@ def main():
     ap.add_argument("--max-chunks", type=int, default=1024)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--batch-jobs", type=int, default=8)
+    ap.add_argument("--e2e-sets", type=int, default=2,
+                    help="job sets the e2e leg alternates (1: each step waits before the next is submitted)")
     ap.add_argument("--graphs", type=int, default=1)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--cpu-units", type=int, default=0, help="oracle sample units (0: 4 per core, <= 256)")

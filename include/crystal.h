@@ -209,6 +209,17 @@ int crystal_task_poll(crystal_task* task);
  * from a completion callback). */
 int crystal_task_wait(crystal_task* task, int64_t timeout_ns);
 
+/* job_synch() over a set of jobs (no counterpart in the paper, which waits
+ * job by job): blocks until every job of tasks[0..n) finished or timeout_ns
+ * elapsed (one bound for the whole call; < 0: no bound).  All jobs must
+ * belong to one context and have been submitted.  Returns CRYSTAL_OK when all
+ * finished with CRYSTAL_OK, else the first non-OK final status in array
+ * order; CRYSTAL_ETIMEDOUT if some job had not finished in time;
+ * CRYSTAL_EINVAL for tasks == NULL with n > 0, a NULL or never-submitted job,
+ * jobs of two contexts, or a call from a completion callback.  One call
+ * replaces n calls of crystal_task_wait when a caller needs all of them. */
+int crystal_task_wait_many(crystal_task* const* tasks, uint32_t n, int64_t timeout_ns);
+
 /* job_put(), Figure 3: returns the job's buffers to the pool.  EINVAL while
  * the job is queued or running. */
 int crystal_task_release(crystal_task* task);
@@ -218,6 +229,12 @@ int crystal_task_release(crystal_task* task);
  * Any pointer may be NULL. */
 int crystal_task_timing(crystal_task* task, uint64_t* submit_ns, uint64_t* dispatch_ns,
                         uint64_t* done_ns);
+
+/* crystal_task_timing of n jobs at once: out[3 i], out[3 i + 1], out[3 i + 2]
+ * = submit, dispatch, done stamps of tasks[i] (out holds 3 n values, caller
+ * owned).  CRYSTAL_EINVAL for NULL arrays with n > 0 or a NULL job (out is
+ * then partly written). */
+int crystal_task_timing_many(crystal_task* const* tasks, uint32_t n, uint64_t* out);
 
 /* Counters of a context. */
 typedef struct crystal_stats {

@@ -151,6 +151,8 @@ def load() -> ctypes.CDLL:
         "crystal_task_release": (ctypes.c_int, [_vp]),
         "crystal_task_timing": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64),
                                                ctypes.POINTER(_u64)]),
+        "crystal_task_wait_many": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.c_int64]),
+        "crystal_task_timing_many": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, _vp]),
         "crystal_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(crystal_stats)]),
         "crystal_out_bytes": (_u64, [ctypes.c_int, _u64, ctypes.POINTER(crystal_hash_params)]),
         "crystal_sliding_out_bytes": (_u64, [_u64, _u64]),
@@ -313,14 +315,35 @@ class Context:
         self._tasks.add(t)
         return t
 
-    def submit_many(self, tasks: Sequence[Task], kind: int, p: Optional[crystal_hash_params] = None,
+    @staticmethod
+    def task_array(tasks: Sequence[Task]):
+        """The job handles as a C array, for the *_many calls (build it once
+        for a set of jobs submitted again and again)."""
+        return (_vp * len(tasks))(*[t.handle for t in tasks])
+
+    def submit_many(self, tasks, kind: int, p: Optional[crystal_hash_params] = None,
                     callback=None, user=None) -> int:
-        """crystal_task_submit_many: all of ``tasks`` or none."""
-        arr = (_vp * len(tasks))(*[t.handle for t in tasks])
+        """crystal_task_submit_many: all of ``tasks`` (Task list or
+        :meth:`task_array`) or none."""
+        arr = tasks if isinstance(tasks, ctypes.Array) else self.task_array(tasks)
         cb = callback if callback is not None else crystal_callback()
         self._cb_keepalive = cb
-        return load().crystal_task_submit_many(arr, len(tasks), kind, ctypes.byref(p) if p is not None else None,
+        return load().crystal_task_submit_many(arr, len(arr), kind, ctypes.byref(p) if p is not None else None,
                                                cb, user)
+
+    def wait_many(self, tasks, timeout_ns: int = -1) -> int:
+        """crystal_task_wait_many: every job of ``tasks`` finished (first
+        non-OK status in order), or CRYSTAL_ETIMEDOUT."""
+        arr = tasks if isinstance(tasks, ctypes.Array) else self.task_array(tasks)
+        return load().crystal_task_wait_many(arr, len(arr), timeout_ns)
+
+    def timing_many(self, tasks) -> np.ndarray:
+        """crystal_task_timing_many: (n, 3) uint64 stamps (submit, dispatch,
+        done) of ``tasks``."""
+        arr = tasks if isinstance(tasks, ctypes.Array) else self.task_array(tasks)
+        out = np.zeros((len(arr), 3), dtype=np.uint64)
+        check(load().crystal_task_timing_many(arr, len(arr), out.ctypes.data), "crystal_task_timing_many")
+        return out
 
     def serve(self, source: np.ndarray, requests: np.ndarray, direct: Optional[crystal_hash_params] = None,
               sliding: Optional[crystal_hash_params] = None, capture: Optional[np.ndarray] = None,

@@ -996,6 +996,40 @@ int crystal_task_wait(crystal_task* t, int64_t timeout_ns) {
     return t->status;
 }
 
+int crystal_task_wait_many(crystal_task* const* tasks, uint32_t n, int64_t timeout_ns) {
+    if (n == 0) return CRYSTAL_OK;
+    if (!tasks || !tasks[0]) return CRYSTAL_EINVAL;
+    crystal_ctx* c = tasks[0]->ctx;
+    if (tl_callback_ctx == c) return CRYSTAL_EINVAL;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!tasks[i] || tasks[i]->ctx != c) return CRYSTAL_EINVAL;
+    }
+    // jobs finish roughly in array order: advance past the finished prefix
+    uint32_t first = 0;
+    auto all_done = [&] {
+        while (first < n && tasks[first]->state.load() == T_DONE) ++first;
+        return first == n;
+    };
+    {
+        const uint64_t spin = timeout_ns >= 0 && (uint64_t)timeout_ns < kWaitSpinNs ? (uint64_t)timeout_ns : kWaitSpinNs;
+        const uint64_t t0 = now_ns();
+        while (!all_done() && now_ns() - t0 < spin) std::this_thread::yield();
+    }
+    std::unique_lock<std::mutex> lk(c->mu);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!tasks[i]->submitted_once) return CRYSTAL_EINVAL;
+    }
+    if (timeout_ns < 0) {
+        c->cv_done.wait(lk, all_done);
+    } else if (!c->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), all_done)) {
+        return CRYSTAL_ETIMEDOUT;
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        if (tasks[i]->status != CRYSTAL_OK) return tasks[i]->status;
+    }
+    return CRYSTAL_OK;
+}
+
 int crystal_task_release(crystal_task* t) {
     if (!t) return CRYSTAL_EINVAL;
     crystal_ctx* c = t->ctx;
@@ -1019,6 +1053,20 @@ int crystal_task_timing(crystal_task* t, uint64_t* submit_ns, uint64_t* dispatch
     if (submit_ns) *submit_ns = t->t_submit;
     if (dispatch_ns) *dispatch_ns = t->t_dispatch;
     if (done_ns) *done_ns = t->t_done;
+    return CRYSTAL_OK;
+}
+
+int crystal_task_timing_many(crystal_task* const* tasks, uint32_t n, uint64_t* out) {
+    if (n == 0) return CRYSTAL_OK;
+    if (!tasks || !out) return CRYSTAL_EINVAL;
+    for (uint32_t i = 0; i < n; ++i) {
+        crystal_task* t = tasks[i];
+        if (!t) return CRYSTAL_EINVAL;
+        std::lock_guard<std::mutex> lk(t->ctx->mu);
+        out[3 * (uint64_t)i + 0] = t->t_submit;
+        out[3 * (uint64_t)i + 1] = t->t_dispatch;
+        out[3 * (uint64_t)i + 2] = t->t_done;
+    }
     return CRYSTAL_OK;
 }
 

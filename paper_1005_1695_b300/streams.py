@@ -100,14 +100,15 @@ def run_stream(mode: str, unit: Callable[[int], np.ndarray], n_units: int, unit_
             tasks = [ctx.task_create(unit_bytes, out_size) for _ in range(n_units)]
             for i, t in enumerate(tasks):
                 t.h_in[:] = unit(i)  # produced into the job's pinned buffer, before the stream
+            handles = ctx.task_array(tasks)
             t0 = time.perf_counter()
-            C.check(ctx.submit_many(tasks, kind, p), "crystal_task_submit_many")
-            for t in tasks:
-                res.statuses.append(t.wait(600_000_000_000))
+            C.check(ctx.submit_many(handles, kind, p), "crystal_task_submit_many")
+            ctx.wait_many(handles, 600_000_000_000)
             res.seconds = time.perf_counter() - t0
+            stamps = ctx.timing_many(handles)
             for i, t in enumerate(tasks):
-                s, _, d = t.timing()
-                res.latencies_ms.append((d - s) / 1e6)
+                res.statuses.append(t.poll())
+                res.latencies_ms.append(float(stamps[i, 2] - stamps[i, 0]) / 1e6)
                 if i in keep:
                     res.outputs[i] = t.h_out[:_used(kind, unit_bytes, t.h_out)].tobytes()
                 t.release()

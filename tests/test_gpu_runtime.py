@@ -377,3 +377,71 @@ def test_sha1_jobs_through_runtime(C, oracle_mod):
                    host_pool_bytes=64 << 20, n_streams=3, flags=C.CRYSTAL_FLAG_GRAPHS, max_batch_jobs=4) as ctx:
         tasks = _submit_all(C, ctx, jobs)
         _check(C, tasks, jobs, want)
+
+
+def test_wait_many_and_timing_many(C, oracle_mod):
+    """One wait and one stamp read for a set of jobs: the first non-OK status
+    in array order, a bounded wait that runs out, the argument checks, and no
+    waiting from a callback."""
+    L = C.load()
+    from paper_1005_1695_b300 import inputs
+
+    with C.Context(max_in_bytes=64 << 20, max_out_bytes=8 << 20, device_pool_bytes=512 << 20,
+                   host_pool_bytes=256 << 20, n_streams=4, max_batch_jobs=4) as ctx:
+        n = 300000
+        small = C.sliding_out_bytes(n, 2)  # too few chunk records: EOVERFLOW
+        outs = [C.sliding_out_bytes(n, n // 16), small, C.sliding_out_bytes(n, n // 16), 16]
+        kinds = [SLIDING, SLIDING, SLIDING, DIRECT]
+        tasks = []
+        for i, (k, o) in enumerate(zip(kinds, outs)):
+            t = ctx.task_create(n, o)
+            t.h_in[:] = inputs.uniform_unit(31, i, n)
+            tasks.append(t)
+        p = C.params(mask=0x3F, target=0x3F)
+        for t, k in zip(tasks, kinds):
+            assert t.submit(k, p) == C.CRYSTAL_OK
+        assert ctx.wait_many(tasks, 60 * SEC) == C.CRYSTAL_EOVERFLOW  # job 1, first non-OK in order
+        assert [t.poll() for t in tasks] == [C.CRYSTAL_OK, C.CRYSTAL_EOVERFLOW, C.CRYSTAL_OK, C.CRYSTAL_OK]
+        for i in (0, 2):
+            st, want = oracle_mod.task(SLIDING, bytes(tasks[i].h_in), outs[i], mask=0x3F, target=0x3F)
+            assert st == 0 and same_result(SLIDING, n, tasks[i].output(), want)
+        stamps = ctx.timing_many(tasks)
+        assert stamps.shape == (4, 3)
+        for i, t in enumerate(tasks):
+            assert tuple(int(x) for x in stamps[i]) == t.timing()
+            assert 0 < stamps[i, 0] <= stamps[i, 1] <= stamps[i, 2]
+        # all OK; the array can be built once and reused
+        arr = ctx.task_array([tasks[0], tasks[2]])
+        for _ in range(2):
+            assert ctx.submit_many(arr, SLIDING, p) == C.CRYSTAL_OK
+            assert ctx.wait_many(arr, 60 * SEC) == C.CRYSTAL_OK
+        # a bounded wait that runs out, then completes
+        big = ctx.task_create(48 << 20, C.sliding_out_bytes(48 << 20, 1 << 14))
+        big.h_in[:] = 7
+        assert big.submit(SLIDING) == C.CRYSTAL_OK
+        assert ctx.wait_many([tasks[0], big], 0) == C.CRYSTAL_ETIMEDOUT
+        assert ctx.wait_many([tasks[0], big], 60 * SEC) == C.CRYSTAL_OK
+        # argument checks
+        assert ctx.wait_many([], 0) == C.CRYSTAL_OK
+        assert L.crystal_task_wait_many(None, 1, 0) == C.CRYSTAL_EINVAL
+        never = ctx.task_create(100, 16)
+        assert ctx.wait_many([tasks[0], never], 0) == C.CRYSTAL_EINVAL
+        assert L.crystal_task_timing_many(None, 1, None) == C.CRYSTAL_EINVAL
+        with C.Context(device_pool_bytes=16 << 20, host_pool_bytes=16 << 20) as other:
+            o = other.task_create(100, 16)
+            o.h_in[:] = 0
+            assert o.submit(DIRECT) == C.CRYSTAL_OK and o.wait(10 * SEC) == C.CRYSTAL_OK
+            assert ctx.wait_many([tasks[0], o], 0) == C.CRYSTAL_EINVAL  # two contexts
+        # not from a completion callback
+        seen = []
+        handles = ctx.task_array([tasks[0]])
+
+        @C.crystal_callback
+        def cb(handle, status, user):
+            seen.append(L.crystal_task_wait_many(handles, 1, 0))
+
+        t = ctx.task_create(4096, 16)
+        t.h_in[:] = 1
+        assert t.submit(DIRECT, None, cb) == C.CRYSTAL_OK
+        assert t.wait(30 * SEC) == C.CRYSTAL_OK
+        assert seen == [C.CRYSTAL_EINVAL]
