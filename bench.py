@@ -222,6 +222,12 @@ def measure_link(torch, dev, total: int, n_streams: int = 8, chunk: int = 8 << 2
     return out
 
 
+def copy_flags(args, C) -> int:
+    """Context flags for --copy: "dma" keeps every copy on the DMA engines (the
+    runtime's default), "sm" lets small runs be copied by the SMs."""
+    return C.CRYSTAL_FLAG_SM_COPY if getattr(args, "copy", "dma") == "sm" else 0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -349,7 +355,7 @@ def run_ours(args, ws, rank, local):
         ctx = C.Context(max_in_bytes=N, max_out_bytes=out_size, device_pool_bytes=pool_dev,
                         host_pool_bytes=pool_host, n_streams=args.streams, max_batch_jobs=args.batch_jobs,
                         max_batch_bytes=args.batch_jobs * N, device=local,
-                        flags=C.CRYSTAL_FLAG_GRAPHS if args.graphs else 0)
+                        flags=(C.CRYSTAL_FLAG_GRAPHS if args.graphs else 0) | copy_flags(args, C))
         # n_sets job sets of U units each (the same bytes), used in turn: step
         # k + 1 is submitted before step k is waited for, as a streaming
         # application keeps the pipeline full
@@ -616,12 +622,17 @@ def run_serving(args, ws, rank, local):
     pool = args.pool_bytes
     ctx = C.Context(max_in_bytes=64 << 20, max_out_bytes=C.sliding_out_bytes(64 << 20, 4 * 8192 + 64),
                     device_pool_bytes=pool, host_pool_bytes=pool, n_streams=args.streams, device=local,
-                    max_batch_jobs=args.batch_jobs, max_batch_bytes=32 << 20, flags=C.CRYSTAL_FLAG_GRAPHS)
+                    max_batch_jobs=args.batch_jobs, max_batch_bytes=32 << 20,
+                    flags=C.CRYSTAL_FLAG_GRAPHS | copy_flags(args, C))
     out = {}
     pinned = args.source == "pinned"
     if pinned:
         C.host_register(src)
     try:
+        # untimed warm-up: each stream slot captures its graphs and the pools
+        # are touched before the first measured rate
+        warm, _ = S.make_trace(args.seed + 1, 2000, rates[0], src.nbytes)
+        C.check(ctx.serve(src, warm, copy_threads=args.copy_threads, source_pinned=pinned)[0], "crystal_serve")
         for rate in rates:
             n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
             req, _ = S.make_trace(args.seed, n, rate, src.nbytes)
@@ -672,8 +683,9 @@ def run_batched(args, ws, rank, local):
     C.host_register(src)
     try:
         sample = req[:min(U, args.tune_units)]
-        best, table = A.tune(sample, src, device_pool_bytes=pool, device=local)
-        st, res, wall = A.run_batch(req, src, best, device_pool_bytes=pool, device=local)
+        xf = C.CRYSTAL_FLAG_GRAPHS | copy_flags(args, C)
+        best, table = A.tune(sample, src, device_pool_bytes=pool, device=local, flags=xf)
+        st, res, wall = A.run_batch(req, src, best, device_pool_bytes=pool, device=local, flags=xf)
         C.check(st, "crystal_serve")
         plain_n = min(U, args.malloc_units)
         stp, resp, wallp = A.run_batch(req[:plain_n], src, A.Setting(1, 1, 64 << 20), device_pool_bytes=pool,
@@ -791,6 +803,8 @@ def main():
     ap.add_argument("--max-chunks", type=int, default=1024)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--batch-jobs", type=int, default=8)
+    ap.add_argument("--copy", choices=["dma", "sm"], default="dma",
+                    help="job-buffer copies: all by DMA (default), or runs under 1 MiB by the SMs")
     ap.add_argument("--e2e-sets", type=int, default=2,
                     help="job sets the e2e leg alternates (1: each step waits before the next is submitted)")
     ap.add_argument("--graphs", type=int, default=1)

@@ -68,7 +68,18 @@ enum {
     CRYSTAL_FLAG_NO_BATCH = 4u,
     /* Replay each batch's descriptor upload and kernel chain as a captured
      * CUDA graph instead of individual launches. */
-    CRYSTAL_FLAG_GRAPHS = 8u
+    CRYSTAL_FLAG_GRAPHS = 8u,
+    /* Pooled mode: copy contiguous runs of a batch's job buffers smaller than
+     * 1 MiB with a kernel that reads or writes the mapped pinned host memory
+     * instead of the DMA engines.  A DMA transfer has a fixed cost of a few
+     * microseconds (about 3.7 us on B300: 256 KiB moves at 30 GB/s), while the
+     * kernel moves scattered pieces of any size at about 48 GB/s -- but it needs
+     * free SMs, and behind busy hashing kernels it waits where the DMA engines
+     * would overlap: on B300 it was slower for served request streams and
+     * uneven batches and no faster for 1 MiB jobs, so it is off by default.
+     * Inputs bound with crystal_task_bind_input take this path when their
+     * memory is mapped (page-locked with crystal_host_register, or by CUDA). */
+    CRYSTAL_FLAG_SM_COPY = 16u
 };
 
 /* crystal_init's argument.  Zero fields take the defaults listed. */
@@ -243,6 +254,8 @@ typedef struct crystal_stats {
     uint64_t device_pool_bytes, device_pool_used;
     uint64_t host_pool_bytes, host_pool_used;
     uint64_t jobs_outstanding, jobs_running;
+    uint64_t copies_dma;  /* job-buffer copies issued to the DMA engines */
+    uint64_t copies_sm;   /* job-buffer copies made by k_copy_pieces (CRYSTAL_FLAG_SM_COPY) */
 } crystal_stats;
 int crystal_get_stats(crystal_ctx* ctx, crystal_stats* out);
 

@@ -52,7 +52,7 @@ def run_batch(req: np.ndarray, source: np.ndarray, setting: Setting, *, device_p
 
 def tune(req_sample: np.ndarray, source: np.ndarray, *, device_pool_bytes: int, device: int = 0,
          streams: Sequence[int] = (4, 8, 16), batch_jobs: Sequence[int] = (8, 32, 128),
-         batch_bytes: Sequence[int] = (32 << 20, 128 << 20), repeats: int = 2):
+         batch_bytes: Sequence[int] = (32 << 20, 128 << 20), repeats: int = 2, flags: int = C.CRYSTAL_FLAG_GRAPHS):
     """Measure every combination on ``req_sample``; return (best, table)."""
     total = float(req_sample["size"].sum())
     table: List[Dict] = []
@@ -61,7 +61,7 @@ def tune(req_sample: np.ndarray, source: np.ndarray, *, device_pool_bytes: int, 
         walls = []
         for _ in range(repeats):
             st, res, wall = run_batch(req_sample, source, setting, device_pool_bytes=device_pool_bytes,
-                                      device=device)
+                                      device=device, flags=flags)
             C.check(st, "crystal_serve")
             walls.append(wall)
         table.append({**setting.as_dict(), "GB_per_s": round(total / (min(walls) / 1e9) / 1e9, 3)})

@@ -44,6 +44,7 @@ CRYSTAL_FLAG_NO_POOL = 1
 CRYSTAL_FLAG_NO_OVERLAP = 2
 CRYSTAL_FLAG_NO_BATCH = 4
 CRYSTAL_FLAG_GRAPHS = 8
+CRYSTAL_FLAG_SM_COPY = 16
 
 
 
@@ -76,7 +77,7 @@ class crystal_hash_params(ctypes.Structure):
 class crystal_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "jobs_completed", "batches_launched", "device_pool_bytes", "device_pool_used",
-        "host_pool_bytes", "host_pool_used", "jobs_outstanding", "jobs_running")]
+        "host_pool_bytes", "host_pool_used", "jobs_outstanding", "jobs_running", "copies_dma", "copies_sm")]
 
 
 UNIT_DTYPE = np.dtype([

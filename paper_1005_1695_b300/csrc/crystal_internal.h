@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cstddef>
 
 #include "crystal.h"
 
@@ -19,6 +20,26 @@ int launch_sliding_windows(crystal_batch* b, cudaStream_t s);
 int launch_sliding_chunks(crystal_batch* b, cudaStream_t s);
 int launch_sliding_digests(crystal_batch* b, cudaStream_t s);  // two kernels
 int launch_nop(cudaStream_t s);                                 // the dummy kernel
+
+// Copies made by the SMs instead of the DMA engines (runtime.cu decides which):
+// piece i moves n bytes from src to dst, either address may be mapped pinned
+// host memory.  The table lives in device memory; chunks of kCopyChunk bytes
+// of every piece are spread over the CTAs of one launch.
+constexpr uint64_t kCopyChunk = 16384;
+struct CopyPiece {
+    uint64_t src, dst, n;
+    uint64_t first_chunk;  // chunks of the pieces before this one
+};
+struct CopyTable {
+    uint32_t n_pieces;
+    uint32_t reserved;
+    uint64_t n_chunks;  // chunks of all pieces
+    CopyPiece piece[1];  // n_pieces used (the table is allocated for the slot's maximum)
+};
+inline uint64_t copy_table_bytes(uint32_t max_pieces) {
+    return 16 + 32ull * (max_pieces ? max_pieces : 1);
+}
+int launch_copy_pieces(const CopyTable* table, cudaStream_t s);
 
 inline crystal_unit* batch_units(crystal_batch* b) {
     return reinterpret_cast<crystal_unit*>(reinterpret_cast<uint8_t*>(b) + sizeof(crystal_batch));
@@ -40,3 +61,4 @@ inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) & ~(a - 1)
 
 static_assert(sizeof(crystal_unit) == 64, "unit record is 64 bytes");
 static_assert(sizeof(crystal_batch) == 64, "batch header is 64 bytes");
+static_assert(sizeof(crystal::CopyPiece) == 32 && offsetof(crystal::CopyTable, piece) == 16, "copy table layout");

@@ -50,6 +50,7 @@ constexpr int kChunkThreads = 512;
 constexpr int kDigestThreads = 256;
 constexpr int kChunkSegThreads = 128;  // K5a: 5 CTAs per SM at <= 102 registers
 constexpr int kScanThreads = 1024;
+constexpr int kCopyThreads = 256;
 
 constexpr uint32_t kDevBadRecord = 1u;
 
@@ -697,6 +698,102 @@ __global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B
     }
 }
 
+// ---- SM copies of small pieces -------------------------------------------------
+
+// Copy chunk `lc` of piece P (bytes [lc * kCopyChunk, +kCopyChunk) of it) with
+// 16-byte accesses when the destination is 16-byte aligned (every buffer the
+// runtime hands out is): each lane loads the aligned source vector at its
+// position, takes the next one from its neighbour lane (or loads it, for the
+// last lane of the last round), and shifts the pair by the source's
+// misalignment.  A source vector is loaded only if it holds a byte of the
+// piece, so no access leaves the pages of the source range.  The last,
+// partial destination vector is written byte by byte.
+__device__ __forceinline__ uint4 load16_if(const uint8_t* p, bool ok) {
+    return ok ? *reinterpret_cast<const uint4*>(p) : make_uint4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ void copy_chunk_aligned_dst(const CopyPiece& P, uint64_t lc) {
+    constexpr int kRounds = 4;  // vectors per lane per warp pass
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    const uint64_t src = P.src, n = P.n;
+    const uint32_t sh = (uint32_t)(src & 15);
+    const uint32_t q = sh >> 2, bs = (sh & 3) * 8;
+    const uint8_t* s0 = reinterpret_cast<const uint8_t*>(src - sh);
+    uint8_t* d = reinterpret_cast<uint8_t*>(P.dst);
+    const uint64_t v_lo = lc * (kCopyChunk / 16);
+    const uint64_t v_hi = min(v_lo + kCopyChunk / 16, (n + 15) / 16);  // destination vectors of this chunk
+    const uint64_t src_last = sh + n - 1;  // offset from s0 of the piece's last byte
+    for (uint64_t vb = v_lo + (uint64_t)warp * 32 * kRounds; vb < v_hi; vb += (uint64_t)warps * 32 * kRounds) {
+        // source vector u holds bytes [16 u, 16 u + 16) from s0; destination
+        // vector v needs source vectors v and v + 1
+        uint4 a[kRounds];
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const uint64_t u = vb + r * 32 + lane;
+            a[r] = load16_if(s0 + 16 * u, 16 * u <= src_last);
+        }
+        const uint64_t u_next = vb + kRounds * 32;
+        const uint4 tail = load16_if(s0 + 16 * u_next, lane == 31 && sh && 16 * u_next <= src_last);
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            // lane l reads lane l + 1's vector; lane 31 reads lane 0's vector
+            // of the next round, so lane 0 hands that one out
+            const uint4 give = (lane == 0 && r + 1 < kRounds) ? a[r + 1] : a[r];
+            const uint32_t from = (lane + 1) & 31;
+            uint4 b;
+            b.x = __shfl_sync(0xffffffffu, give.x, from);
+            b.y = __shfl_sync(0xffffffffu, give.y, from);
+            b.z = __shfl_sync(0xffffffffu, give.z, from);
+            b.w = __shfl_sync(0xffffffffu, give.w, from);
+            if (lane == 31 && r + 1 == kRounds) b = tail;
+            const uint64_t v = vb + r * 32 + lane;
+            if (v >= v_hi) continue;
+            const uint32_t x[8] = {a[r].x, a[r].y, a[r].z, a[r].w, b.x, b.y, b.z, b.w};
+            uint32_t y1[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) y1[k] = (q & 1) ? x[k + 1] : x[k];
+            uint32_t y[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) y[k] = (q & 2) ? y1[k + 2] : y1[k];
+            const uint4 o = make_uint4(__funnelshift_r(y[0], y[1], bs), __funnelshift_r(y[1], y[2], bs),
+                                       __funnelshift_r(y[2], y[3], bs), __funnelshift_r(y[3], y[4], bs));
+            if (16 * v + 16 <= n) {
+                *reinterpret_cast<uint4*>(d + 16 * v) = o;
+            } else {
+                for (uint64_t i = 16 * v; i < n; ++i) {
+                    const uint32_t k = (uint32_t)(i >> 2) & 3;
+                    const uint32_t wd = k == 0 ? o.x : k == 1 ? o.y : k == 2 ? o.z : o.w;
+                    d[i] = (uint8_t)(wd >> (8 * (i & 3)));
+                }
+            }
+        }
+    }
+}
+
+// One launch copies every piece of the table; CTAs take chunks in turn.
+__global__ void __launch_bounds__(kCopyThreads) k_copy_pieces(const CopyTable* T) {
+    const uint32_t np = T->n_pieces;
+    const uint64_t chunks = T->n_chunks;
+    for (uint64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+        uint32_t lo = 0, hi = np;  // last piece with first_chunk <= c
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (T->piece[mid].first_chunk <= c) lo = mid; else hi = mid;
+        }
+        const CopyPiece P = T->piece[lo];
+        const uint64_t lc = c - P.first_chunk;
+        if ((P.dst & 15) == 0) {
+            copy_chunk_aligned_dst(P, lc);
+        } else {
+            const uint8_t* s = reinterpret_cast<const uint8_t*>(P.src);
+            uint8_t* d = reinterpret_cast<uint8_t*>(P.dst);
+            const uint64_t b1 = min(P.n, (lc + 1) * kCopyChunk);
+            for (uint64_t i = lc * kCopyChunk + threadIdx.x; i < b1; i += blockDim.x) d[i] = s[i];
+        }
+    }
+    __threadfence_system();  // host-side destinations complete before the stream moves on
+}
+
 // ---- the dummy kernel of the overhead experiment ----------------------------
 
 __global__ void k_nop() {}
@@ -760,6 +857,13 @@ int launched(int kernels) {
 
 int launch_nop(cudaStream_t s) {
     k_nop<<<1, 32, 0, s>>>();
+    return launched(1);
+}
+
+int launch_copy_pieces(const CopyTable* table, cudaStream_t s) {
+    const Geometry* g = geometry();
+    if (!g) return CRYSTAL_EDEVICE;
+    k_copy_pieces<<<g->sms * 4, kCopyThreads, 0, s>>>(table);
     return launched(1);
 }
 

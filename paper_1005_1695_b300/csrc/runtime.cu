@@ -58,10 +58,16 @@ struct Slot {
     crystal_batch* h_desc = nullptr;  // pinned
     crystal_batch* d_desc = nullptr;  // device, inside the device arena
     uint64_t d_desc_off = 0;
+    // SM copy tables (inputs, outputs), uploaded with the descriptor
+    CopyTable* h_tin = nullptr;
+    CopyTable* h_tout = nullptr;
+    const CopyTable* d_tin = nullptr;
+    const CopyTable* d_tout = nullptr;
     std::vector<crystal_task*> tasks;
     bool busy = false;
     uint64_t seq = 0;
-    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // index: has_direct | has_sliding<<1
+    // index: has_direct | has_sliding << 1 | sm copy-in << 2 | sm copy-out << 3
+    cudaGraphExec_t graph[16] = {};
 };
 
 thread_local const crystal_ctx* tl_callback_ctx = nullptr;
@@ -77,6 +83,7 @@ struct crystal_task {
     uint8_t* d_scratch = nullptr;
     uint8_t* d_reserved = nullptr;  // scratch reserved at create (crystal_task_create_ex)
     const uint8_t* h_in_ext = nullptr;  // caller memory bound as the input (crystal_task_bind_input)
+    uint64_t h_in_ext_dev = 0;          // its device-visible address when mapped (0: DMA only)
     bool external_input = false;        // created without its own pinned input buffer
     uint64_t h_in_off = 0, h_out_off = 0, d_in_off = 0, d_out_off = 0, d_scratch_off = 0, d_reserved_off = 0;
     uint64_t reserved_bytes = 0;
@@ -140,6 +147,9 @@ struct crystal_ctx {
     uint32_t next_slot = 0;
     uint32_t max_jobs = 64;
     uint64_t max_bytes = 32ull << 20;
+    uint64_t region_bytes = 0;  // per slot: descriptor, then the two copy tables
+    bool sm_copy = false;       // small runs copied by k_copy_pieces
+    int64_t h_dev_delta = 0;    // device-visible address of a host-pool byte minus its address
 
     std::mutex mu;
     std::condition_variable cv_master;
@@ -155,6 +165,7 @@ struct crystal_ctx {
     std::atomic<uint64_t> n_outstanding{0};  // mirrors outstanding.size() for the idle spin
     std::atomic<uint64_t> jobs_completed{0};
     std::atomic<uint64_t> batches{0};
+    std::atomic<uint64_t> copies_dma{0}, copies_sm{0};
     uint64_t n_running_jobs = 0;
 };
 
@@ -291,15 +302,17 @@ int launch_chain(crystal_batch* d, cudaStream_t st, bool direct, bool sliding) {
 
 int kernels_in_chain(bool direct, bool sliding) { return (direct ? 3 : 0) + (sliding ? 7 : 0); }
 
-// Capture descriptor upload + kernel chain of one slot as a graph.
+// Capture descriptor upload, SM copy-in, kernel chain, SM copy-out and the
+// header read-back of one slot as a graph.
 int capture_graph(crystal_ctx* c, Slot& s, int variant) {
-    const bool direct = variant & 1, sliding = variant & 2;
-    const uint64_t desc_bytes = crystal_batch_bytes(c->max_jobs);
+    const bool direct = variant & 1, sliding = variant & 2, copy_in = variant & 4, copy_out = variant & 8;
     const uint64_t before = g_kernel_launches.load();
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CRYSTAL_EDEVICE;
-    cudaMemcpyAsync(s.d_desc, s.h_desc, desc_bytes, cudaMemcpyHostToDevice, s.stream);
-    int r = launch_chain(s.d_desc, s.stream, direct, sliding);
+    cudaMemcpyAsync(s.d_desc, s.h_desc, c->region_bytes, cudaMemcpyHostToDevice, s.stream);
+    int r = copy_in ? launch_copy_pieces(s.d_tin, s.stream) : CRYSTAL_OK;
+    if (r == CRYSTAL_OK) r = launch_chain(s.d_desc, s.stream, direct, sliding);
+    if (r == CRYSTAL_OK && copy_out) r = launch_copy_pieces(s.d_tout, s.stream);
     cudaMemcpyAsync(s.h_desc, s.d_desc, sizeof(crystal_batch), cudaMemcpyDeviceToHost, s.stream);
     cudaError_t e = cudaStreamEndCapture(s.stream, &g);
     g_kernel_launches.store(before);
@@ -313,85 +326,149 @@ int capture_graph(crystal_ctx* c, Slot& s, int variant) {
     return e == cudaSuccess ? CRYSTAL_OK : CRYSTAL_EDEVICE;
 }
 
-// Issue copy-in, kernels and copy-out of the slot's jobs on its stream.
+// One copy of a batch: host range <-> device range, n bytes.  host_dev is the
+// device-visible address of the host range (0: not mapped, DMA only).
+struct Run {
+    const uint8_t* host;
+    uint64_t host_dev;
+    uint8_t* dev;
+    uint64_t n;
+    bool by_sm;
+};
+
+// With CRYSTAL_FLAG_SM_COPY, runs below this size are copied by the SMs when
+// both ends are device-visible: a DMA transfer costs a few microseconds
+// whatever its size (about 3.7 us on B300, so 256 KiB moves at 30 GB/s and
+// 1 MiB at 46 GB/s), while k_copy_pieces moves scattered pieces of any size at
+// about 48 GB/s when it finds free SMs.
+constexpr uint64_t kSmCopyMax = 1ull << 20;
+
 // Copies of several jobs merged into one when their host ranges and their
 // device ranges are both contiguous blocks at the same host-to-device offset
-// (fewer, larger DMA transfers).  A job's block is its whole allocation, so a
+// (fewer, larger transfers).  A job's block is its whole allocation, so a
 // merged copy only ever covers memory of the merged jobs.
-class CopyMerger {
+class RunBuilder {
   public:
-    CopyMerger(cudaStream_t s, cudaMemcpyKind kind) : s_(s), kind_(kind) {}
+    explicit RunBuilder(std::vector<Run>* out) : out_(out) {}
     // host/dev: the job's buffers; used: bytes that matter; block: allocated bytes
-    bool add(const uint8_t* host, uint8_t* dev, uint64_t used, uint64_t block, bool mergeable) {
-        if (!used) return true;
+    void add(const uint8_t* host, uint64_t host_dev, uint8_t* dev, uint64_t used, uint64_t block, bool mergeable) {
+        if (!used) return;
         const int64_t delta = (int64_t)((uint64_t)dev - (uint64_t)host);
-        if (open_ && mergeable && delta == delta_) {
+        const bool mapped = host_dev != 0;
+        const int64_t hdelta = mapped ? (int64_t)(host_dev - (uint64_t)host) : 0;
+        if (open_ && mergeable && delta == delta_ && mapped == mapped_ && hdelta == hdelta_) {
             if (host == hi_) {  // just above the run
                 hi_ = host + block;
                 end_ = host + used;
-                return true;
+                return;
             }
             if (host + block == lo_) {  // just below the run
                 lo_ = host;
-                return true;
+                return;
             }
         }
-        if (!flush()) return false;
-        if (!mergeable) return copy(host, dev, used);
+        flush();
+        if (!mergeable) {
+            out_->push_back(Run{host, host_dev, dev, used, false});
+            return;
+        }
         open_ = true;
         lo_ = host;
         hi_ = host + block;
         end_ = host + used;
         delta_ = delta;
-        return true;
+        mapped_ = mapped;
+        hdelta_ = hdelta;
     }
-    bool flush() {
-        if (!open_) return true;
+    void flush() {
+        if (!open_) return;
         open_ = false;
-        return copy(lo_, reinterpret_cast<uint8_t*>((uint64_t)lo_ + (uint64_t)delta_), (uint64_t)(end_ - lo_));
+        out_->push_back(Run{lo_, mapped_ ? (uint64_t)lo_ + (uint64_t)hdelta_ : 0,
+                            reinterpret_cast<uint8_t*>((uint64_t)lo_ + (uint64_t)delta_), (uint64_t)(end_ - lo_), false});
     }
 
   private:
-    bool copy(const uint8_t* host, uint8_t* dev, uint64_t n) {
-        if (kind_ == cudaMemcpyHostToDevice)
-            return cudaMemcpyAsync(dev, host, n, kind_, s_) == cudaSuccess;
-        return cudaMemcpyAsync(const_cast<uint8_t*>(host), dev, n, kind_, s_) == cudaSuccess;
-    }
-    cudaStream_t s_;
-    cudaMemcpyKind kind_;
+    std::vector<Run>* out_;
     bool open_ = false;
     const uint8_t* lo_ = nullptr;
     const uint8_t* hi_ = nullptr;   // end of the highest block in the run
     const uint8_t* end_ = nullptr;  // end of the bytes to copy (in the highest block)
-    int64_t delta_ = 0;
+    int64_t delta_ = 0, hdelta_ = 0;
+    bool mapped_ = false;
 };
 
+// Put a run into an SM copy table if it is small and mapped; true if taken.
+bool sm_take(CopyTable* T, uint32_t cap, uint64_t src, uint64_t dst, uint64_t n) {
+    if (n >= kSmCopyMax || T->n_pieces >= cap) return false;
+    CopyPiece& p = T->piece[T->n_pieces++];
+    p.src = src;
+    p.dst = dst;
+    p.n = n;
+    p.first_chunk = T->n_chunks;
+    T->n_chunks += (n + kCopyChunk - 1) / kCopyChunk;
+    return true;
+}
+
+bool dma(const Run& r, cudaMemcpyKind kind, cudaStream_t st) {
+    if (kind == cudaMemcpyHostToDevice) return cudaMemcpyAsync(r.dev, r.host, r.n, kind, st) == cudaSuccess;
+    return cudaMemcpyAsync(const_cast<uint8_t*>(r.host), r.dev, r.n, kind, st) == cudaSuccess;
+}
+
+// Issue copy-in, kernels and copy-out of the slot's jobs on its stream.
 int issue(crystal_ctx* c, Slot& s) {
     cudaStream_t st = s.stream;
+    uint32_t nd = 0, ns = 0;
+    build_descriptor(s, &nd, &ns);
+    const bool hashing = nd + ns > 0;
+    // the copy tables ride on the descriptor upload, so only batches that
+    // upload one copy with the SMs
+    const bool sm = c->sm_copy && hashing;
+    std::vector<Run> in_runs, out_runs;
     {
-        CopyMerger in(st, cudaMemcpyHostToDevice);
+        RunBuilder in(&in_runs);
         for (crystal_task* t : s.tasks) {
             const bool own = !t->h_in_ext;
             const uint8_t* src = own ? t->h_in : t->h_in_ext;
-            if (!in.add(src, t->d_in, t->in_size, align_up(t->in_cap ? t->in_cap : 1, 256), own && c->pooled))
-                return CRYSTAL_EDEVICE;
+            const uint64_t src_dev = !sm ? 0 : own ? (uint64_t)t->h_in + (uint64_t)c->h_dev_delta : t->h_in_ext_dev;
+            in.add(src, src_dev, t->d_in, t->in_size, align_up(t->in_cap ? t->in_cap : 1, 256), own && c->pooled);
         }
-        if (!in.flush()) return CRYSTAL_EDEVICE;
+        in.flush();
+        RunBuilder out(&out_runs);
+        for (crystal_task* t : s.tasks) {
+            const uint64_t dst_dev = sm ? (uint64_t)t->h_out + (uint64_t)c->h_dev_delta : 0;
+            out.add(t->h_out, dst_dev, t->d_out, t->out_size, align_up(t->out_cap ? t->out_cap : 1, 256), c->pooled);
+        }
+        out.flush();
     }
-    uint32_t nd = 0, ns = 0;
-    build_descriptor(s, &nd, &ns);
-    if (nd + ns > 0) {
+    if (sm) {
+        s.h_tin->n_pieces = s.h_tout->n_pieces = 0;
+        s.h_tin->n_chunks = s.h_tout->n_chunks = 0;
+        for (Run& r : in_runs) r.by_sm = r.host_dev && sm_take(s.h_tin, c->max_jobs, r.host_dev, (uint64_t)r.dev, r.n);
+        for (Run& r : out_runs) r.by_sm = r.host_dev && sm_take(s.h_tout, c->max_jobs, (uint64_t)r.dev, r.host_dev, r.n);
+    }
+    uint64_t n_sm = 0, n_dma = 0;
+    for (const Run& r : in_runs) {
+        if (r.by_sm) {
+            ++n_sm;
+        } else {
+            ++n_dma;
+            if (!dma(r, cudaMemcpyHostToDevice, st)) return CRYSTAL_EDEVICE;
+        }
+    }
+    if (hashing) {
         if (crystal_batch_plan(s.h_desc, nd, ns) != CRYSTAL_OK) return CRYSTAL_EINVAL;
-        const int variant = (nd ? 1 : 0) | (ns ? 2 : 0);
+        const bool copy_in = sm && s.h_tin->n_pieces, copy_out = sm && s.h_tout->n_pieces;
+        const int variant = (nd ? 1 : 0) | (ns ? 2 : 0) | (copy_in ? 4 : 0) | (copy_out ? 8 : 0);
         if (c->cfg.flags & CRYSTAL_FLAG_GRAPHS) {
             if (!s.graph[variant] && capture_graph(c, s, variant) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
             if (cudaGraphLaunch(s.graph[variant], st) != cudaSuccess) return CRYSTAL_EDEVICE;
-            g_kernel_launches.fetch_add((uint64_t)kernels_in_chain(nd, ns));
+            g_kernel_launches.fetch_add((uint64_t)(kernels_in_chain(nd, ns) + copy_in + copy_out));
         } else {
-            if (cudaMemcpyAsync(s.d_desc, s.h_desc, crystal_batch_bytes(nd + ns), cudaMemcpyHostToDevice, st) !=
-                cudaSuccess)
+            if (cudaMemcpyAsync(s.d_desc, s.h_desc, c->region_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
                 return CRYSTAL_EDEVICE;
-            int r = launch_chain(s.d_desc, st, nd > 0, ns > 0);
+            int r = copy_in ? launch_copy_pieces(s.d_tin, st) : CRYSTAL_OK;
+            if (r == CRYSTAL_OK) r = launch_chain(s.d_desc, st, nd > 0, ns > 0);
+            if (r == CRYSTAL_OK && copy_out) r = launch_copy_pieces(s.d_tout, st);
             if (r != CRYSTAL_OK) return r;
             if (cudaMemcpyAsync(s.h_desc, s.d_desc, sizeof(crystal_batch), cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 return CRYSTAL_EDEVICE;
@@ -402,14 +479,16 @@ int issue(crystal_ctx* c, Slot& s) {
         s.h_desc->status = 0;
         if (launch_nop(st) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     }
-    {
-        CopyMerger out(st, cudaMemcpyDeviceToHost);
-        for (crystal_task* t : s.tasks) {
-            if (!out.add(t->h_out, t->d_out, t->out_size, align_up(t->out_cap ? t->out_cap : 1, 256), c->pooled))
-                return CRYSTAL_EDEVICE;
+    for (const Run& r : out_runs) {
+        if (r.by_sm) {
+            ++n_sm;
+        } else {
+            ++n_dma;
+            if (!dma(r, cudaMemcpyDeviceToHost, st)) return CRYSTAL_EDEVICE;
         }
-        if (!out.flush()) return CRYSTAL_EDEVICE;
     }
+    c->copies_sm.fetch_add(n_sm);
+    c->copies_dma.fetch_add(n_dma);
     if (cudaEventRecord(s.done, st) != cudaSuccess) return CRYSTAL_EDEVICE;
     return CRYSTAL_OK;
 }
@@ -637,7 +716,7 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
     if (u.max_batch_bytes) cfg.max_batch_bytes = u.max_batch_bytes;
     if (cfg.n_streams < 1 || cfg.n_streams > 64 || cfg.max_batch_jobs > 65536) return CRYSTAL_EINVAL;
     if (cfg.flags & ~(uint32_t)(CRYSTAL_FLAG_NO_POOL | CRYSTAL_FLAG_NO_OVERLAP | CRYSTAL_FLAG_NO_BATCH |
-                                CRYSTAL_FLAG_GRAPHS))
+                                CRYSTAL_FLAG_GRAPHS | CRYSTAL_FLAG_SM_COPY))
         return CRYSTAL_EINVAL;
     if (cfg.device_arena && (reinterpret_cast<uint64_t>(cfg.device_arena) & 255)) return CRYSTAL_EINVAL;
     if (cudaSetDevice(cfg.device) != cudaSuccess) {
@@ -654,7 +733,10 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
     c->max_bytes = cfg.max_batch_bytes;
     const uint32_t depth = (cfg.flags & CRYSTAL_FLAG_NO_OVERLAP) ? 1 : 2;  // slots per stream
     const uint32_t n_slots = (uint32_t)c->cfg.n_streams * depth;
-    const uint64_t desc_bytes = align_up(crystal_batch_bytes(c->max_jobs), 256);
+    // per slot: descriptor (header + max_jobs units), then the copy tables
+    const uint64_t tables_off = align_up(crystal_batch_bytes(c->max_jobs), 16);
+    const uint64_t desc_bytes = align_up(tables_off + 2 * copy_table_bytes(c->max_jobs), 256);
+    c->region_bytes = desc_bytes;
 
     // device arena: job buffers (pooled mode), scratch and batch descriptors
     uint64_t d_bytes = cfg.device_pool_bytes;
@@ -677,7 +759,7 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
     }
     if (c->pooled) {
         void* h = nullptr;
-        if (cudaHostAlloc(&h, cfg.host_pool_bytes, cudaHostAllocDefault) != cudaSuccess) {
+        if (cudaHostAlloc(&h, cfg.host_pool_bytes, cudaHostAllocMapped) != cudaSuccess) {
             cudaGetLastError();
             destroy_ctx(c);
             return CRYSTAL_ENOMEM;
@@ -687,6 +769,16 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
             destroy_ctx(c);
             return CRYSTAL_ENOMEM;
         }
+        // SM copies need the pool mapped into the device's address space
+        int uva = 0;
+        void* hd = nullptr;
+        if ((cfg.flags & CRYSTAL_FLAG_SM_COPY) &&
+            cudaDeviceGetAttribute(&uva, cudaDevAttrUnifiedAddressing, cfg.device) == cudaSuccess && uva &&
+            cudaHostGetDevicePointer(&hd, h, 0) == cudaSuccess && hd) {
+            c->sm_copy = true;
+            c->h_dev_delta = (int64_t)((uint64_t)hd - (uint64_t)h);
+        }
+        cudaGetLastError();
     }
     c->slots.resize(n_slots);
     for (uint32_t i = 0; i < n_slots; ++i) {
@@ -719,6 +811,10 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
             return CRYSTAL_ENOMEM;
         }
         s.d_desc = (crystal_batch*)(c->d_base + s.d_desc_off);
+        s.h_tin = reinterpret_cast<CopyTable*>((uint8_t*)h + tables_off);
+        s.h_tout = reinterpret_cast<CopyTable*>((uint8_t*)h + tables_off + copy_table_bytes(c->max_jobs));
+        s.d_tin = reinterpret_cast<const CopyTable*>((uint8_t*)s.d_desc + tables_off);
+        s.d_tout = reinterpret_cast<const CopyTable*>((uint8_t*)s.d_desc + tables_off + copy_table_bytes(c->max_jobs));
     }
     try {
         c->master = std::thread(master_loop, c);
@@ -939,12 +1035,19 @@ int crystal_task_bind_input(crystal_task* t, const void* host, uint64_t size) {
     if (size > t->in_cap) return CRYSTAL_EINVAL;
     t->h_in_ext = static_cast<const uint8_t*>(host);
     t->in_size = size;
+    t->h_in_ext_dev = 0;
+    if (t->ctx->sm_copy) {  // mapped page-locked memory: the SMs may read it in place
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, host) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer)
+            t->h_in_ext_dev = (uint64_t)a.devicePointer;
+        cudaGetLastError();
+    }
     return CRYSTAL_OK;
 }
 
 int crystal_host_register(void* host, uint64_t bytes) {
     if (!host || !bytes) return CRYSTAL_EINVAL;
-    if (cudaHostRegister(host, bytes, cudaHostRegisterDefault) != cudaSuccess) {
+    if (cudaHostRegister(host, bytes, cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
         cudaGetLastError();
         return CRYSTAL_EDEVICE;
     }
@@ -1081,6 +1184,8 @@ int crystal_get_stats(crystal_ctx* c, crystal_stats* out) {
     out->host_pool_used = c->pooled ? crystal_arena_used(c->h_arena) : 0;
     out->jobs_outstanding = c->outstanding.size();
     out->jobs_running = c->n_running_jobs;
+    out->copies_dma = c->copies_dma.load();
+    out->copies_sm = c->copies_sm.load();
     return CRYSTAL_OK;
 }
 

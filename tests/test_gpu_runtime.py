@@ -77,8 +77,9 @@ def _check(C, tasks, jobs, want):
         assert same_result(kind, len(data), g, w), f"job {i}: " + first_difference(kind, len(data), g, w)
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2, 4, 8, 1 | 2 | 4], ids=["pooled", "no_pool", "no_overlap",
-                                                                  "no_batch", "graphs", "plain"])
+@pytest.mark.parametrize("flags", [0, 1, 2, 4, 8, 1 | 2 | 4, 16, 8 | 16], ids=["pooled", "no_pool", "no_overlap",
+                                                                            "no_batch", "graphs", "plain",
+                                                                            "sm_copy", "graphs_sm_copy"])
 def test_runtime_modes_bit_exact(C, oracle_mod, flags):
     jobs = _jobs(C)
     want = _want(oracle_mod, jobs)
@@ -445,3 +446,53 @@ def test_wait_many_and_timing_many(C, oracle_mod):
         assert t.submit(DIRECT, None, cb) == C.CRYSTAL_OK
         assert t.wait(30 * SEC) == C.CRYSTAL_OK
         assert seen == [C.CRYSTAL_EINVAL]
+
+
+@pytest.mark.parametrize("flags", [16, 8 | 16, 0], ids=["sm_copies", "sm_copies_graphs", "dma_only"])
+def test_bound_inputs_every_alignment_and_small_sizes(C, oracle_mod, flags):
+    """Inputs read in place from registered memory at every offset mod 16, with
+    sizes around the 16-byte vectors and the copy kernel's 16 KiB chunks, and
+    small outputs: the kernel-made copies (both directions) and the DMA path
+    give the oracle's bytes."""
+    from paper_1005_1695_b300 import inputs
+
+    sizes = [1, 2, 15, 16, 17, 31, 33, 63, 64, 65, 100, 4095, 4096, 4097, 16383, 16384, 16385, 16400, 40000,
+             300001]
+    total = sum(s + 16 for s in sizes) * 2 + 4096
+    src = C.page_aligned(total)
+    src[:] = inputs.uniform_unit(77, 0, total)
+    C.host_register(src)
+    try:
+        jobs = []
+        pos = 0
+        for i, n in enumerate(sizes * 2):
+            off = pos + (i * 7) % 16
+            kind = SLIDING if i % 4 == 3 else DIRECT
+            osz = C.sliding_out_bytes(n, n // 64 + 8) if kind == SLIDING else 16
+            p = C.params(mask=0x3F, target=0x3F) if kind == SLIDING else C.params(segment_bytes=1024)
+            jobs.append((kind, off, n, osz, p))
+            pos = off + n
+        with C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 20, device_pool_bytes=256 << 20,
+                       host_pool_bytes=64 << 20, n_streams=4, max_batch_jobs=8, flags=flags) as ctx:
+            tasks = []
+            for kind, off, n, osz, p in jobs:
+                t = ctx.task_create(n, osz)
+                t.bind_input(src[off:off + n])
+                tasks.append(t)
+            for t, (kind, off, n, osz, p) in zip(tasks, jobs):
+                assert t.submit(kind, p) == C.CRYSTAL_OK
+            assert ctx.wait_many(tasks, 60 * SEC) == C.CRYSTAL_OK
+            for i, (t, (kind, off, n, osz, p)) in enumerate(zip(tasks, jobs)):
+                st, w = oracle_mod.task(kind, src[off:off + n].tobytes(), osz, seg_bytes=p.segment_bytes,
+                                        mask=p.mask, target=p.target)
+                assert st == 0
+                g = t.output()
+                assert same_result(kind, n, g, w), f"job {i} n={n} off%16={off % 16}: " + \
+                    first_difference(kind, n, g, w)
+            st = ctx.stats()
+            if flags & C.CRYSTAL_FLAG_SM_COPY:
+                assert st.copies_sm > 0  # the kernel path really ran
+            else:
+                assert st.copies_sm == 0 and st.copies_dma > 0
+    finally:
+        C.host_unregister(src)
