@@ -40,6 +40,11 @@ inline uint64_t copy_table_bytes(uint32_t max_pieces) {
     return 16 + 32ull * (max_pieces ? max_pieces : 1);
 }
 int launch_copy_pieces(const CopyTable* table, cudaStream_t s);
+// The batch descriptor fetched by the GPU from mapped pinned memory (bytes a
+// multiple of 16), and its status word posted back to mapped pinned memory:
+// no DMA transfer for either.
+int launch_fetch_descriptor(const void* host_dev, crystal_batch* dst, uint64_t bytes, cudaStream_t s);
+int launch_post_status(const crystal_batch* d, uint32_t* host_status_dev, cudaStream_t s);
 
 inline crystal_unit* batch_units(crystal_batch* b) {
     return reinterpret_cast<crystal_unit*>(reinterpret_cast<uint8_t*>(b) + sizeof(crystal_batch));

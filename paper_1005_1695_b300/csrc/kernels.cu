@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kDigestThreads) k_direct_outer(crystal_batch* 
         digest_to<CRYSTAL_FMA_OUTER>(X, reinterpret_cast<const uint8_t*>(X.scratch), digest_bytes(X) * m,
                                      reinterpret_cast<uint8_t*>(X.out), one);
     }
+    __threadfence_system();  // out may be mapped host memory (the runtime writes digests in place)
 }
 
 // ---- K3: window digests and boundary bitmap ---------------------------------
@@ -794,6 +795,31 @@ __global__ void __launch_bounds__(kCopyThreads) k_copy_pieces(const CopyTable* T
     __threadfence_system();  // host-side destinations complete before the stream moves on
 }
 
+// ---- batch descriptor in, status out, without DMA ------------------------------
+
+__global__ void __launch_bounds__(256) k_fetch_descriptor(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                          uint32_t n16) {
+    constexpr int kIn = 4;  // loads in flight per thread
+    for (uint32_t b = 0; b < n16; b += kIn * blockDim.x) {
+        uint4 v[kIn];
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) {
+            const uint32_t i = b + k * blockDim.x + threadIdx.x;
+            if (i < n16) v[k] = src[i];
+        }
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) {
+            const uint32_t i = b + k * blockDim.x + threadIdx.x;
+            if (i < n16) dst[i] = v[k];
+        }
+    }
+}
+
+__global__ void k_post_status(const crystal_batch* d, uint32_t* host_status) {
+    *host_status = d->status;
+    __threadfence_system();
+}
+
 // ---- the dummy kernel of the overhead experiment ----------------------------
 
 __global__ void k_nop() {}
@@ -857,6 +883,18 @@ int launched(int kernels) {
 
 int launch_nop(cudaStream_t s) {
     k_nop<<<1, 32, 0, s>>>();
+    return launched(1);
+}
+
+int launch_fetch_descriptor(const void* host_dev, crystal_batch* dst, uint64_t bytes, cudaStream_t s) {
+    if ((bytes & 15) || ((uint64_t)host_dev & 15) || ((uint64_t)dst & 15)) return CRYSTAL_EINVAL;
+    k_fetch_descriptor<<<1, 256, 0, s>>>(static_cast<const uint4*>(host_dev), reinterpret_cast<uint4*>(dst),
+                                         (uint32_t)(bytes / 16));
+    return launched(1);
+}
+
+int launch_post_status(const crystal_batch* d, uint32_t* host_status_dev, cudaStream_t s) {
+    k_post_status<<<1, 1, 0, s>>>(d, host_status_dev);
     return launched(1);
 }
 

@@ -56,6 +56,7 @@ struct Slot {
     bool own_stream = false;  // slots beyond the first n_streams share a stream
     cudaEvent_t done = nullptr;
     crystal_batch* h_desc = nullptr;  // pinned
+    uint8_t* h_desc_dev = nullptr;    // its device-visible address when mapped (descriptor fetched by the GPU)
     crystal_batch* d_desc = nullptr;  // device, inside the device arena
     uint64_t d_desc_off = 0;
     // SM copy tables (inputs, outputs), uploaded with the descriptor
@@ -149,6 +150,7 @@ struct crystal_ctx {
     uint64_t max_bytes = 32ull << 20;
     uint64_t region_bytes = 0;  // per slot: descriptor, then the two copy tables
     bool sm_copy = false;       // small runs copied by k_copy_pieces
+    bool h_mapped = false;      // the host pool is mapped into the device's address space
     int64_t h_dev_delta = 0;    // device-visible address of a host-pool byte minus its address
 
     std::mutex mu;
@@ -260,8 +262,13 @@ int resolve_params(int kind, const crystal_hash_params* in, uint64_t n, uint64_t
 
 // ---- issuing a batch --------------------------------------------------------------
 
-// Fill the slot's pinned descriptor from its jobs: direct units first.
-void build_descriptor(Slot& s, uint32_t* nd_out, uint32_t* ns_out) {
+// Fill the slot's pinned descriptor from its jobs: direct units first.  With
+// the host pool mapped, a direct job's digest (its whole output) is written by
+// the kernel straight into the job's pinned output buffer: no copy-out, which
+// for a 16-byte result would cost a full DMA transfer.
+bool digest_in_place(const crystal_ctx* c, const crystal_task* t) { return c->h_mapped && kind_is_direct(t->kind); }
+
+void build_descriptor(const crystal_ctx* c, Slot& s, uint32_t* nd_out, uint32_t* ns_out) {
     crystal_unit* U = batch_units(s.h_desc);
     uint32_t k = 0;
     for (int pass = 0; pass < 2; ++pass) {
@@ -270,7 +277,7 @@ void build_descriptor(Slot& s, uint32_t* nd_out, uint32_t* ns_out) {
             crystal_unit& x = U[k++];
             x.in = (uint64_t)t->d_in;
             x.n = t->in_size;
-            x.out = (uint64_t)t->d_out;
+            x.out = digest_in_place(c, t) ? (uint64_t)t->h_out + (uint64_t)c->h_dev_delta : (uint64_t)t->d_out;
             x.scratch = (uint64_t)t->d_scratch;
             x.work_begin = 0;
             x.out_cap = (uint32_t)std::min<uint64_t>(t->out_size, 0xFFFFFFFFull);
@@ -302,18 +309,38 @@ int launch_chain(crystal_batch* d, cudaStream_t st, bool direct, bool sliding) {
 
 int kernels_in_chain(bool direct, bool sliding) { return (direct ? 3 : 0) + (sliding ? 7 : 0); }
 
-// Capture descriptor upload, SM copy-in, kernel chain, SM copy-out and the
-// header read-back of one slot as a graph.
+// Descriptor in, SM copy-in, kernel chain, SM copy-out, status back: the
+// device side of one batch.  With the slot's descriptor region mapped, the GPU
+// fetches the descriptor and posts the status itself (two small kernels)
+// instead of two DMA transfers of a few microseconds each.
+int batch_sequence(crystal_ctx* c, Slot& s, bool direct, bool sliding, bool copy_in, bool copy_out) {
+    cudaStream_t st = s.stream;
+    int r = CRYSTAL_OK;
+    if (s.h_desc_dev) {
+        r = launch_fetch_descriptor(s.h_desc_dev, s.d_desc, c->region_bytes, st);
+    } else if (cudaMemcpyAsync(s.d_desc, s.h_desc, c->region_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        r = CRYSTAL_EDEVICE;
+    }
+    if (r == CRYSTAL_OK && copy_in) r = launch_copy_pieces(s.d_tin, st);
+    if (r == CRYSTAL_OK) r = launch_chain(s.d_desc, st, direct, sliding);
+    if (r == CRYSTAL_OK && copy_out) r = launch_copy_pieces(s.d_tout, st);
+    if (r != CRYSTAL_OK) return r;
+    if (s.h_desc_dev) {
+        const uint64_t status_off = offsetof(crystal_batch, status);
+        return launch_post_status(s.d_desc, reinterpret_cast<uint32_t*>(s.h_desc_dev + status_off), st);
+    }
+    return cudaMemcpyAsync(s.h_desc, s.d_desc, sizeof(crystal_batch), cudaMemcpyDeviceToHost, st) == cudaSuccess
+               ? CRYSTAL_OK
+               : CRYSTAL_EDEVICE;
+}
+
+// Capture batch_sequence of one slot as a graph.
 int capture_graph(crystal_ctx* c, Slot& s, int variant) {
     const bool direct = variant & 1, sliding = variant & 2, copy_in = variant & 4, copy_out = variant & 8;
     const uint64_t before = g_kernel_launches.load();
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CRYSTAL_EDEVICE;
-    cudaMemcpyAsync(s.d_desc, s.h_desc, c->region_bytes, cudaMemcpyHostToDevice, s.stream);
-    int r = copy_in ? launch_copy_pieces(s.d_tin, s.stream) : CRYSTAL_OK;
-    if (r == CRYSTAL_OK) r = launch_chain(s.d_desc, s.stream, direct, sliding);
-    if (r == CRYSTAL_OK && copy_out) r = launch_copy_pieces(s.d_tout, s.stream);
-    cudaMemcpyAsync(s.h_desc, s.d_desc, sizeof(crystal_batch), cudaMemcpyDeviceToHost, s.stream);
+    int r = batch_sequence(c, s, direct, sliding, copy_in, copy_out);
     cudaError_t e = cudaStreamEndCapture(s.stream, &g);
     g_kernel_launches.store(before);
     if (r != CRYSTAL_OK || e != cudaSuccess) {
@@ -418,7 +445,7 @@ bool dma(const Run& r, cudaMemcpyKind kind, cudaStream_t st) {
 int issue(crystal_ctx* c, Slot& s) {
     cudaStream_t st = s.stream;
     uint32_t nd = 0, ns = 0;
-    build_descriptor(s, &nd, &ns);
+    build_descriptor(c, s, &nd, &ns);
     const bool hashing = nd + ns > 0;
     // the copy tables ride on the descriptor upload, so only batches that
     // upload one copy with the SMs
@@ -435,6 +462,7 @@ int issue(crystal_ctx* c, Slot& s) {
         in.flush();
         RunBuilder out(&out_runs);
         for (crystal_task* t : s.tasks) {
+            if (digest_in_place(c, t)) continue;  // already in h_out when the batch completes
             const uint64_t dst_dev = sm ? (uint64_t)t->h_out + (uint64_t)c->h_dev_delta : 0;
             out.add(t->h_out, dst_dev, t->d_out, t->out_size, align_up(t->out_cap ? t->out_cap : 1, 256), c->pooled);
         }
@@ -462,16 +490,11 @@ int issue(crystal_ctx* c, Slot& s) {
         if (c->cfg.flags & CRYSTAL_FLAG_GRAPHS) {
             if (!s.graph[variant] && capture_graph(c, s, variant) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
             if (cudaGraphLaunch(s.graph[variant], st) != cudaSuccess) return CRYSTAL_EDEVICE;
-            g_kernel_launches.fetch_add((uint64_t)(kernels_in_chain(nd, ns) + copy_in + copy_out));
+            g_kernel_launches.fetch_add(
+                (uint64_t)(kernels_in_chain(nd, ns) + copy_in + copy_out + (s.h_desc_dev ? 2 : 0)));
         } else {
-            if (cudaMemcpyAsync(s.d_desc, s.h_desc, c->region_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-                return CRYSTAL_EDEVICE;
-            int r = copy_in ? launch_copy_pieces(s.d_tin, st) : CRYSTAL_OK;
-            if (r == CRYSTAL_OK) r = launch_chain(s.d_desc, st, nd > 0, ns > 0);
-            if (r == CRYSTAL_OK && copy_out) r = launch_copy_pieces(s.d_tout, st);
+            const int r = batch_sequence(c, s, nd > 0, ns > 0, copy_in, copy_out);
             if (r != CRYSTAL_OK) return r;
-            if (cudaMemcpyAsync(s.h_desc, s.d_desc, sizeof(crystal_batch), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-                return CRYSTAL_EDEVICE;
         }
     } else {
         // only dummy jobs: the "dummy kernel with insignificant execution
@@ -769,14 +792,15 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
             destroy_ctx(c);
             return CRYSTAL_ENOMEM;
         }
-        // SM copies need the pool mapped into the device's address space
+        // the pool mapped into the device's address space: kernels write direct
+        // digests into it, and SM copies read and write it
         int uva = 0;
         void* hd = nullptr;
-        if ((cfg.flags & CRYSTAL_FLAG_SM_COPY) &&
-            cudaDeviceGetAttribute(&uva, cudaDevAttrUnifiedAddressing, cfg.device) == cudaSuccess && uva &&
+        if (cudaDeviceGetAttribute(&uva, cudaDevAttrUnifiedAddressing, cfg.device) == cudaSuccess && uva &&
             cudaHostGetDevicePointer(&hd, h, 0) == cudaSuccess && hd) {
-            c->sm_copy = true;
+            c->h_mapped = true;
             c->h_dev_delta = (int64_t)((uint64_t)hd - (uint64_t)h);
+            c->sm_copy = (cfg.flags & CRYSTAL_FLAG_SM_COPY) != 0;
         }
         cudaGetLastError();
     }
@@ -799,13 +823,16 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
             return CRYSTAL_EDEVICE;
         }
         void* h = nullptr;
-        if (cudaHostAlloc(&h, desc_bytes, cudaHostAllocDefault) != cudaSuccess) {
+        if (cudaHostAlloc(&h, desc_bytes, cudaHostAllocMapped) != cudaSuccess) {
             cudaGetLastError();
             destroy_ctx(c);
             return CRYSTAL_ENOMEM;
         }
         memset(h, 0, desc_bytes);
         s.h_desc = (crystal_batch*)h;
+        void* hd = nullptr;
+        if (c->h_mapped && cudaHostGetDevicePointer(&hd, h, 0) == cudaSuccess && hd) s.h_desc_dev = (uint8_t*)hd;
+        cudaGetLastError();
         if (crystal_arena_alloc(c->d_arena, desc_bytes, &s.d_desc_off) != CRYSTAL_OK) {
             destroy_ctx(c);
             return CRYSTAL_ENOMEM;
