@@ -269,6 +269,37 @@ def cpu_oracle_rate(host: np.ndarray, unit_bytes: int, units: int, cores: int, p
                       f"{cores} threads, {dt:.1f} s"}
 
 
+def cpu_oracle_detail(host: np.ndarray, unit_bytes: int, cores: int, params: dict) -> dict:
+    """The oracle's rates on one host core and on all of them: plain MD5, direct
+    hashing (4 KiB segments) and the sliding-window job, each on a few units of
+    the workload (a few seconds of CPU in all)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    oracle.build()
+    units = [host[u * unit_bytes:(u + 1) * unit_bytes] for u in range(min(len(host) // unit_bytes, cores))]
+    out_size = 8 + 4 * ((unit_bytes + 31) // 32) + 20 * 1024
+
+    def rate(fn, items, threads):
+        t0 = time.perf_counter()
+        if threads == 1:
+            for x in items:
+                fn(x)
+        else:
+            with ThreadPoolExecutor(max_workers=threads) as ex:
+                list(ex.map(fn, items))
+        return round(len(items) * unit_bytes / (time.perf_counter() - t0) / GB, 4)
+
+    md5 = oracle.md5
+    direct = lambda x: oracle.direct(x, 4096)
+    sliding = lambda x: oracle.task(2, x, out_size, **params)
+    return {"unit": "GB/s", "cores": cores, "kind": "oracle",
+            "md5_1core": rate(md5, units * 4, 1), "md5_all_cores": rate(md5, units * 4, cores),
+            "direct_1core": rate(direct, units * 4, 1), "direct_all_cores": rate(direct, units * 4, cores),
+            "sliding_1core": rate(sliding, units[:1], 1), "sliding_all_cores": rate(sliding, units, cores),
+            "sample": f"{len(units)} of the workload's {unit_bytes >> 20} MiB units (x4 for MD5 and direct)"}
+
+
 # ---- our arm ------------------------------------------------------------------------
 
 def run_ours(args, ws, rank, local):
@@ -883,6 +914,7 @@ def main():
         if not args.no_cpu_baseline:
             host = sliding_workload(args.seed, cpu_units, args.unit_bytes)
             out["cpu_baseline"] = cpu_oracle_rate(host, args.unit_bytes, cpu_units, cores, params)
+            out["cpu_oracle_detail"] = cpu_oracle_detail(host, args.unit_bytes, cores, params)
         print(json.dumps(out))
 
 
