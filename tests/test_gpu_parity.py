@@ -296,3 +296,23 @@ def test_largest_units_full_oracle(torch_cuda, C, oracle_mod):
     want = _oracle_all(oracle_mod, units, kinds, plist, outs)
     assert [st for st, _ in want] == [0, 0, 0]
     _compare(units, kinds, got, want)
+
+
+def test_golden_cases_on_gpu(torch_cuda, C):
+    """Every stored oracle case (tests/golden/oracle_cases.txt) through the
+    CUDA path in one batch: same status and the same used output bytes."""
+    import hashlib
+
+    from paper_1005_1695_b300 import inputs
+    from test_golden import CASES
+
+    units = [inputs.uniform_unit(c["seed"], 0, c["n"]) for c in CASES]
+    kinds = [c["kind"] for c in CASES]
+    plist = [C.params(segment_bytes=c["seg"], window_bytes=c["window"], mask=c["mask"], target=c["target"],
+                      chunk_segment_bytes=c["cseg"]) for c in CASES]
+    outs = [c["out_size"] for c in CASES]
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 3, 8, 13])
+    for c, g in zip(CASES, got):
+        if c["kind"] in (2, 4):
+            assert int.from_bytes(g[4:8], "little") == c["status"], c
+        assert hashlib.sha256(g[:c["used"]]).hexdigest() == c["sha"], c
