@@ -267,8 +267,7 @@ __device__ __forceinline__ uint32_t tile_windows20(const uint32_t* sw, uint32_t 
         X[5] = 0x80u;
         X[14] = 8u * 20;
         const uint32_t A = window_first_word<H>(X, 20u, one);
-        const bool hit = (rel0 + 4 * j + 20 <= lim) && ((A & mask) == target);
-        m |= (uint32_t)hit << (sub + 4 * j);
+        m |= (uint32_t)((A & mask) == target) << (sub + 4 * j);
         if (j < 7) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) M[k] = M[k + 1];
@@ -277,6 +276,11 @@ __device__ __forceinline__ uint32_t tile_windows20(const uint32_t* sw, uint32_t 
             raw = nxt;
         }
     }
+    // windows past the unit's last full window (rel0 + 4 j + 20 > lim) do not
+    // count: this lane's first `valid` windows fit, bits s + 4 j of the mask
+    const int32_t room = (int32_t)lim - (int32_t)(rel0 + 20);
+    const uint32_t valid = room < 0 ? 0u : min(8u, (uint32_t)room / 4 + 1);
+    m &= valid ? (0x11111111u >> (4 * (8 - valid))) << sub : 0u;
     m |= __shfl_xor_sync(0xffffffffu, m, 1);
     m |= __shfl_xor_sync(0xffffffffu, m, 2);
     return __shfl_sync(0xffffffffu, m, (lane & 7) * 4);
