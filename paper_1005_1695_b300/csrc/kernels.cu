@@ -302,17 +302,50 @@ __device__ __forceinline__ uint32_t next_owner(const crystal_unit* U, uint32_t c
 #define CRYSTAL_WIN_FAST_OWNER 1
 #endif
 
-// Issue the copies of one tile's bytes [base, min(n, base + kTile + w - 1))
-// from their 16-byte aligned block on into smem; vectors past the unit's end
-// are not loaded.
-__device__ __forceinline__ void stage_tile(uint32_t* sw, const crystal_unit& X, uint64_t base) {
+// What every thread of a CTA needs to know about one tile, worked out once by
+// thread 0 (the unit that owns it, the staging source, the output words).
+struct TileInfo {
+    uint64_t src;     // 16-byte aligned address of the first vector to stage
+    uint64_t out;     // address of the tile's first bitmap word
+    uint32_t nvec;    // 16-byte vectors to stage
+    uint32_t delta;   // byte offset of the tile's first window in the staged data
+    uint32_t lim;     // bytes of the unit from the tile's first window on (at most 2 tiles)
+    uint32_t words;   // bitmap words of the tile that lie inside the unit
+    uint32_t mask, target, w, pad;
+};
+
+__device__ __forceinline__ void describe_tile(TileInfo& I, const crystal_unit* U, uint32_t ns, uint32_t& u,
+                                              uint64_t g) {
+#if CRYSTAL_WIN_FAST_OWNER
+    u = next_owner(U, ns, u, g);
+#else
+    u = owner_of(U, ns, g);
+#endif
+    const crystal_unit X = U[u];
+    const uint64_t base = (g - X.work_begin) * (uint64_t)kTile;
     const uint64_t a = X.in + base;
     const uint32_t delta = (uint32_t)(a & 15);
-    const uint64_t a0 = a - delta;
+    const uint64_t left = X.n - base;
     const uint64_t span = (uint64_t)(kTile + X.window - 1);
-    const uint64_t want = X.n - base < span ? X.n - base : span;
-    const uint32_t nvec = (uint32_t)((delta + want + 15) >> 4);
-    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) cp_async16(sw + 4 * v, a0 + 16ull * v);
+    const uint64_t want = left < span ? left : span;
+    const uint64_t words_left = ((X.n + 31) >> 5) - (base >> 5);
+    I.src = a - delta;
+    I.out = X.out + 8 + 4 * (base >> 5);
+    I.nvec = (uint32_t)((delta + want + 15) >> 4);
+    I.delta = delta;
+    I.lim = left < (uint64_t)(2 * kTile) ? (uint32_t)left : (uint32_t)(2 * kTile);
+    I.words = words_left < (uint64_t)(kTile / 32) ? (uint32_t)words_left : (uint32_t)(kTile / 32);
+    I.mask = X.mask;
+    I.target = X.target;
+    I.w = X.window;
+}
+
+// Copy one described tile's bytes into smem (vectors past the unit's end are
+// not loaded).
+__device__ __forceinline__ void stage_described(uint32_t* sw, const TileInfo& I) {
+    const uint32_t nvec = I.nvec;
+    const uint64_t src = I.src;
+    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) cp_async16(sw + 4 * v, src + 16ull * v);
 }
 
 // Instances (the planner orders the sliding units this way):
@@ -320,7 +353,10 @@ __device__ __forceinline__ void stage_tile(uint32_t* sw, const crystal_unit& X, 
 //   <0, MD5>:  tiles [sliding_tiles_w20, sliding_tiles_md5), other MD5 units;
 //   <0, SHA1>: tiles [sliding_tiles_md5, sliding_tiles), SHA-1 units, any w.
 // The next tile's bytes are copied into the other half of a double buffer
-// while the current tile is hashed.
+// while the current tile is hashed.  Thread 0 describes each tile two tiles
+// ahead into a ring of three TileInfo (the slot it writes was last read by the
+// tile before the current one, which the previous iteration's closing barrier
+// has retired); the other threads only read the ring.
 // Resident CTAs per SM the window kernel is compiled for (sets its register
 // budget: 65536 / (256 * blocks)).  Eight (32 registers) was measured fastest
 // on B300 with 2048-offset tiles (8 windows per thread).
@@ -331,53 +367,54 @@ __device__ __forceinline__ void stage_tile(uint32_t* sw, const crystal_unit& X, 
 template <int W, class H, int MINB>
 __global__ void __launch_bounds__(kWinThreads, MINB) k_sliding_windows(crystal_batch* B, uint32_t one) {
     __shared__ __align__(16) uint32_t sw[2][kStageWords];
+    __shared__ TileInfo ring[3];
     const uint32_t ns = B->n_sliding;
     const crystal_unit* U = units_of(B) + B->n_direct;
     const bool sha = H::kWords == 5;
     const uint64_t lo = sha ? B->sliding_tiles_md5 : (W == 20 ? 0 : B->sliding_tiles_w20);
     const uint64_t hi = sha ? B->sliding_tiles : (W == 20 ? B->sliding_tiles_w20 : B->sliding_tiles_md5);
+    const uint64_t G = gridDim.x;
     uint64_t t = lo + blockIdx.x;
     if (t >= hi) return;
-    uint32_t u = owner_of(U, ns, t);
-    stage_tile(sw[0], U[u], (t - U[u].work_begin) * (uint64_t)kTile);
+    uint32_t u = 0;  // owner of the last tile thread 0 described
+    if (threadIdx.x == 0) {
+        u = owner_of(U, ns, t);
+        describe_tile(ring[0], U, ns, u, t);
+        if (t + G < hi) describe_tile(ring[1], U, ns, u, t + G);
+    }
+    __syncthreads();
+    stage_described(sw[0], ring[0]);
     cp_async_commit();
     int buf = 0;
-    for (; t < hi; t += gridDim.x) {
-        const uint64_t tn = t + gridDim.x;
-        uint32_t un = 0;
-        if (tn < hi) {
-#if CRYSTAL_WIN_FAST_OWNER
-            un = next_owner(U, ns, u, tn);
-#else
-            un = owner_of(U, ns, tn);
-#endif
-            stage_tile(sw[buf ^ 1], U[un], (tn - U[un].work_begin) * (uint64_t)kTile);
-        }
+    uint32_t r0 = 0, r1 = 1, r2 = 2;  // ring slots of tiles t, t + G, t + 2G
+    for (; t < hi; t += G) {
+        if (t + G < hi) stage_described(sw[buf ^ 1], ring[r1]);
         cp_async_commit();
+        if (threadIdx.x == 0 && t + 2 * G < hi) describe_tile(ring[r2], U, ns, u, t + 2 * G);
         cp_async_wait<1>();
         __syncthreads();
-        const crystal_unit& X = U[u];
-        const uint64_t base = (t - X.work_begin) * (uint64_t)kTile;
-        const uint32_t delta = (uint32_t)((X.in + base) & 15);
-        const uint64_t left = X.n - base;
-        const uint32_t lim = left < (uint64_t)(2 * kTile) ? (uint32_t)left : (uint32_t)(2 * kTile);
-        const uint32_t w = W > 0 ? (uint32_t)W : (uint32_t)X.window;
+        const TileInfo& I = ring[r0];
+        const uint32_t delta = I.delta, lim = I.lim;
+        const uint32_t w = W > 0 ? (uint32_t)W : I.w;
         uint32_t mine;
         if constexpr (W == 20) {
-            mine = tile_windows20<H>(sw[buf], delta, lim, X.mask, X.target, one);
+            mine = tile_windows20<H>(sw[buf], delta, lim, I.mask, I.target, one);
         } else if (H::kWords == 5 && w == 20) {
             // SHA-1 units with the common window: padding words fold at compile time
-            mine = tile_windows20<H>(sw[buf], delta, lim, X.mask, X.target, one);
+            mine = tile_windows20<H>(sw[buf], delta, lim, I.mask, I.target, one);
         } else {
-            mine = tile_windows<W, H>(sw[buf], delta, lim, w, X.mask, X.target, one);
+            mine = tile_windows<W, H>(sw[buf], delta, lim, w, I.mask, I.target, one);
         }
         const uint32_t lane = threadIdx.x & 31;
         if (lane < (uint32_t)kWinPerThread) {
-            const uint64_t word = (base >> 5) + (threadIdx.x >> 5) * kWinPerThread + lane;
-            if (word < ((X.n + 31) >> 5)) reinterpret_cast<uint32_t*>(X.out + 8)[word] = mine;
+            const uint32_t word = (threadIdx.x >> 5) * kWinPerThread + lane;
+            if (word < I.words) reinterpret_cast<uint32_t*>(I.out)[word] = mine;
         }
         __syncthreads();
-        u = un;
+        const uint32_t r = r0;
+        r0 = r1;
+        r1 = r2;
+        r2 = r;
         buf ^= 1;
     }
     cp_async_wait<0>();
