@@ -167,7 +167,7 @@ def measure_link(torch, dev, total: int, n_streams: int = 8, chunk: int = 8 << 2
     The pinned buffer is allocated pinned and written by one thread: filling
     it with a multi-threaded torch copy leaves torch's worker threads spinning
     on every core for a while, and host-to-device copies measured meanwhile
-    were up to 30% slower on the B300 machines."""
+    were up to 30% slower on B300 hosts with 16 cores."""
     pinned = torch.empty(total, dtype=torch.uint8, pin_memory=True)
     pinned.numpy()[:] = 1
     dbuf = torch.empty(total, dtype=torch.uint8, device=dev)
