@@ -316,3 +316,19 @@ def test_golden_cases_on_gpu(torch_cuda, C):
         if c["kind"] in (2, 4):
             assert int.from_bytes(g[4:8], "little") == c["status"], c
         assert hashlib.sha256(g[:c["used"]]).hexdigest() == c["sha"], c
+
+
+@pytest.mark.parametrize("kind", [SLIDING, SHA1_SLIDING])
+def test_many_small_units_more_tiles_than_the_grid(torch_cuda, C, oracle_mod, kind):
+    """3,000 sliding units of 1 B - 6 KiB (about 5,000 tiles, several per CTA of the
+    window kernel, their owners hundreds of units apart) with windows of 20 and of
+    other lengths, at odd input alignments: every unit against the oracle."""
+    rng = np.random.default_rng(17)
+    sizes = [int(x) for x in rng.integers(1, 6144, 3000)]
+    units = [_rand(20000 + i, n) for i, n in enumerate(sizes)]
+    kinds = [kind] * len(units)
+    plist = [C.params(window_bytes=[20, 20, 20, 7, 33][i % 5], mask=0x3F, target=0x15) for i in range(len(units))]
+    outs = [C.sliding_out_bytes(n, n // 16 + 8, kind) for n in sizes]
+    got = _run(torch_cuda, C, units, kinds, plist, out_sizes=outs, align=[0, 1, 6, 11, 15])
+    want = _oracle_all(oracle_mod, units, kinds, plist, outs)
+    _compare(units, kinds, got, want)
