@@ -286,22 +286,6 @@ __device__ __forceinline__ uint32_t tile_windows20(const uint32_t* sw, uint32_t 
     return __shfl_sync(0xffffffffu, m, (lane & 7) * 4);
 }
 
-// Owner of tile g >= the tiles of unit u: a short forward walk (the next
-// tile of a CTA is usually in the same unit or the next one), else a binary
-// search over the rest.
-__device__ __forceinline__ uint32_t next_owner(const crystal_unit* U, uint32_t cnt, uint32_t u, uint64_t g) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        if (u + 1 < cnt && U[u + 1].work_begin <= g) ++u;
-    }
-    if (u + 1 < cnt && U[u + 1].work_begin <= g) u = owner_of(U, cnt, g);
-    return u;
-}
-
-#ifndef CRYSTAL_WIN_FAST_OWNER
-#define CRYSTAL_WIN_FAST_OWNER 1
-#endif
-
 // What every thread of a CTA needs to know about one tile, worked out once by
 // thread 0 (the unit that owns it, the staging source, the output words).
 struct TileInfo {
@@ -314,14 +298,8 @@ struct TileInfo {
     uint32_t mask, target, w, pad;
 };
 
-__device__ __forceinline__ void describe_tile(TileInfo& I, const crystal_unit* U, uint32_t ns, uint32_t& u,
-                                              uint64_t g) {
-#if CRYSTAL_WIN_FAST_OWNER
-    u = next_owner(U, ns, u, g);
-#else
-    u = owner_of(U, ns, g);
-#endif
-    const crystal_unit X = U[u];
+__device__ __forceinline__ void describe_tile(TileInfo& I, const crystal_unit* U, uint32_t ns, uint64_t g) {
+    const crystal_unit X = U[owner_of(U, ns, g)];
     const uint64_t base = (g - X.work_begin) * (uint64_t)kTile;
     const uint64_t a = X.in + base;
     const uint32_t delta = (uint32_t)(a & 15);
@@ -353,47 +331,54 @@ __device__ __forceinline__ void stage_described(uint32_t* sw, const TileInfo& I)
 //   <0, MD5>:  tiles [sliding_tiles_w20, sliding_tiles_md5), other MD5 units;
 //   <0, SHA1>: tiles [sliding_tiles_md5, sliding_tiles), SHA-1 units, any w.
 // The next tile's bytes are copied into the other half of a double buffer
-// while the current tile is hashed.  Thread 0 describes each tile two tiles
-// ahead into a ring of three TileInfo (the slot it writes was last read by the
-// tile before the current one, which the previous iteration's closing barrier
-// has retired); the other threads only read the ring.
+// while the current tile is hashed.  A CTA's tiles are described in chunks of
+// kDescChunk, one tile per thread of the first two warps (each finds its
+// tile's unit by binary search), into a double-buffered table: chunk c + 1 is
+// written at the first tile of chunk c, into the half that chunk c - 1 used
+// and the previous iteration's closing barrier retired; it is first read a
+// chunk later.  No thread does per-tile bookkeeping for the others.
 // Resident CTAs per SM the window kernel is compiled for (sets its register
 // budget: 65536 / (256 * blocks)).  Eight (32 registers) was measured fastest
 // on B300 with 2048-offset tiles (8 windows per thread).
 #ifndef CRYSTAL_WIN_MIN_BLOCKS
 #define CRYSTAL_WIN_MIN_BLOCKS 8
 #endif
+constexpr uint32_t kDescChunk = 64;
+static_assert(kDescChunk <= kWinThreads, "one describing thread per tile of a chunk");
 
 template <int W, class H, int MINB>
 __global__ void __launch_bounds__(kWinThreads, MINB) k_sliding_windows(crystal_batch* B, uint32_t one) {
     __shared__ __align__(16) uint32_t sw[2][kStageWords];
-    __shared__ TileInfo ring[3];
+    __shared__ TileInfo desc[2][kDescChunk];
     const uint32_t ns = B->n_sliding;
     const crystal_unit* U = units_of(B) + B->n_direct;
     const bool sha = H::kWords == 5;
     const uint64_t lo = sha ? B->sliding_tiles_md5 : (W == 20 ? 0 : B->sliding_tiles_w20);
     const uint64_t hi = sha ? B->sliding_tiles : (W == 20 ? B->sliding_tiles_w20 : B->sliding_tiles_md5);
     const uint64_t G = gridDim.x;
-    uint64_t t = lo + blockIdx.x;
-    if (t >= hi) return;
-    uint32_t u = 0;  // owner of the last tile thread 0 described
-    if (threadIdx.x == 0) {
-        u = owner_of(U, ns, t);
-        describe_tile(ring[0], U, ns, u, t);
-        if (t + G < hi) describe_tile(ring[1], U, ns, u, t + G);
-    }
+    const uint64_t t0 = lo + blockIdx.x;  // the CTA's tile k is t0 + k G
+    if (t0 >= hi) return;
+    // describe the CTA's tiles [c kDescChunk, (c + 1) kDescChunk) into desc[c & 1]
+    auto describe_chunk = [&](uint32_t c) {
+        if (threadIdx.x < kDescChunk) {
+            const uint64_t g = t0 + ((uint64_t)c * kDescChunk + threadIdx.x) * G;
+            if (g < hi) describe_tile(desc[c & 1][threadIdx.x], U, ns, g);
+        }
+    };
+    describe_chunk(0);
     __syncthreads();
-    stage_described(sw[0], ring[0]);
+    stage_described(sw[0], desc[0][0]);
     cp_async_commit();
     int buf = 0;
-    uint32_t r0 = 0, r1 = 1, r2 = 2;  // ring slots of tiles t, t + G, t + 2G
-    for (; t < hi; t += G) {
-        if (t + G < hi) stage_described(sw[buf ^ 1], ring[r1]);
+    uint32_t k = 0;
+    for (uint64_t t = t0; t < hi; t += G, ++k) {
+        if (k % kDescChunk == 0) describe_chunk(k / kDescChunk + 1);
+        const uint32_t k1 = k + 1;
+        if (t + G < hi) stage_described(sw[buf ^ 1], desc[(k1 / kDescChunk) & 1][k1 % kDescChunk]);
         cp_async_commit();
-        if (threadIdx.x == 0 && t + 2 * G < hi) describe_tile(ring[r2], U, ns, u, t + 2 * G);
         cp_async_wait<1>();
         __syncthreads();
-        const TileInfo& I = ring[r0];
+        const TileInfo& I = desc[(k / kDescChunk) & 1][k % kDescChunk];
         const uint32_t delta = I.delta, lim = I.lim;
         const uint32_t w = W > 0 ? (uint32_t)W : I.w;
         uint32_t mine;
@@ -411,10 +396,6 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_sliding_windows(crystal_b
             if (word < I.words) reinterpret_cast<uint32_t*>(I.out)[word] = mine;
         }
         __syncthreads();
-        const uint32_t r = r0;
-        r0 = r1;
-        r1 = r2;
-        r2 = r;
         buf ^= 1;
     }
     cp_async_wait<0>();
