@@ -62,8 +62,8 @@ INT_LANES_PER_SM = 128  # 4 schedulers x one 32-lane instruction per clock
 # DRAM bytes (read + write) of the window kernel per 1 MiB sliding unit, from one
 # ncu capture of 160 units (traffic grows with the units processed), valid only
 # for the kernel sources it was taken on (checked by hash; otherwise null).
-WINDOW_TRAFFIC_PER_UNIT = (167.955968e6 + 14.296576e6) / 160
-WINDOW_TRAFFIC_SOURCES = "a1ccd219f709c858"
+WINDOW_TRAFFIC_PER_UNIT = (167.863552e6 + 14.007296e6) / 160
+WINDOW_TRAFFIC_SOURCES = "01a00e389f12a6e4"
 
 
 def _kernel_sources_hash() -> str:
