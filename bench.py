@@ -222,10 +222,32 @@ def measure_link(torch, dev, total: int, n_streams: int = 8, chunk: int = 8 << 2
     return out
 
 
-def copy_flags(args, C) -> int:
-    """Context flags for --copy: "dma" keeps every copy on the DMA engines (the
-    runtime's default), "sm" lets small runs be copied by the SMs."""
-    return C.CRYSTAL_FLAG_SM_COPY if getattr(args, "copy", "dma") == "sm" else 0
+def measure_int_pipes(torch, dev, C, ctas_per_sm: int = 16) -> dict:
+    """The integer-pipe microbenchmarks of the library (crystal_alu_probe), on
+    register data only, each timed with CUDA events on its stream (best of 3
+    after a warm-up launch): the 20-byte window hash of MD5 and of SHA-1 as the
+    window kernel computes it (windows/s), and single-instruction chains on
+    one pipe (LOP3, funnel shift, three-input add, IMAD) or two (LOP3 and IMAD
+    alternately: the dual-issue rate), in instructions/s."""
+    sink = torch.zeros(4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    iters = {"md5_windows": 400, "sha1_windows": 150}
+    out = {}
+    for name, kind in C.PROBE_KINDS.items():
+        it = iters.get(name, 200)
+        with torch.cuda.stream(stream):
+            C.alu_probe(kind, ctas_per_sm, max(1, it // 10), sink, stream)
+            best = None
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                work = C.alu_probe(kind, ctas_per_sm, it, sink, stream)
+                b.record(stream)
+                b.synchronize()
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+        out[name] = work / (best / 1e3)
+    return out
 
 
 def _peaks():
@@ -248,25 +270,35 @@ def sliding_workload(seed: int, units: int, unit_bytes: int) -> np.ndarray:
     return host
 
 
-def cpu_oracle_rate(host: np.ndarray, unit_bytes: int, units: int, cores: int, params: dict) -> dict:
-    """The oracle (as it stands) on ``units`` units over ``cores`` host threads."""
+def cpu_oracle_rate(host: np.ndarray, unit_bytes: int, units: int, cores: int, params: dict, kind: int = 2,
+                    results: dict = None) -> dict:
+    """The oracle (as it stands) on ``units`` units over ``cores`` host threads.
+    With ``results`` (unit -> the GPU's used output bytes for that unit), the
+    oracle's output of each of those units is compared with them: the line's
+    ``verified`` record."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
 
     oracle.build()
-    out_size = 8 + 4 * ((unit_bytes + 31) // 32) + 20 * 1024
+    out_size = 8 + 4 * ((unit_bytes + 31) // 32) + (4 + oracle.digest_bytes(kind)) * 1024
 
     def one(u):
-        return oracle.task(2, host[u * unit_bytes:(u + 1) * unit_bytes], out_size, **params)[0]
+        return oracle.task(kind, host[u * unit_bytes:(u + 1) * unit_bytes], out_size, **params)
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=cores) as ex:
-        sts = list(ex.map(one, range(units)))
+        outs = list(ex.map(one, range(units)))
     dt = time.perf_counter() - t0
-    assert all(s == 0 for s in sts)
-    return {"value": units * unit_bytes / dt / GB, "unit": "GB/s", "cores": cores, "kind": "oracle",
+    assert all(st == 0 for st, _ in outs)
+    line = {"value": units * unit_bytes / dt / GB, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": f"{units} of the workload's 1 MiB units (sliding window w=20 + chunk direct hash), "
                       f"{cores} threads, {dt:.1f} s"}
+    if results is not None:
+        checked = [u for u in sorted(results) if u < units]
+        bad = [u for u in checked if outs[u][1][:len(results[u])] != results[u]]
+        line["_verified"] = {"units_checked": len(checked), "bit_exact": len(checked) - len(bad),
+                             "mismatched_units": bad[:8], "against": "the oracle, every output byte"}
+    return line
 
 
 def cpu_oracle_detail(host: np.ndarray, unit_bytes: int, cores: int, params: dict) -> dict:
@@ -326,6 +358,7 @@ def run_ours(args, ws, rank, local):
     U, N = args.units, args.unit_bytes
     p = C.params(window_bytes=20, mask=0x1FFF, target=0x1FFF, chunk_segment_bytes=4096)
     KIND = C.CRYSTAL_KIND_SHA1_SLIDING if args.hash == "sha1" else C.CRYSTAL_KIND_MD5_SLIDING
+    gpu_results = {}  # unit -> used output bytes from the job API
     ops_per_window = OPS_PER_WINDOW_SHA1_W20 if args.hash == "sha1" else OPS_PER_WINDOW_W20
     out_size = C.sliding_out_bytes(N, args.max_chunks, KIND)
     host = sliding_workload(rank_seed(args.seed, rank), U, N)
@@ -386,7 +419,7 @@ def run_ours(args, ws, rank, local):
         ctx = C.Context(max_in_bytes=N, max_out_bytes=out_size, device_pool_bytes=pool_dev,
                         host_pool_bytes=pool_host, n_streams=args.streams, max_batch_jobs=args.batch_jobs,
                         max_batch_bytes=args.batch_jobs * N, device=local,
-                        flags=(C.CRYSTAL_FLAG_GRAPHS if args.graphs else 0) | copy_flags(args, C))
+                        flags=C.CRYSTAL_FLAG_GRAPHS if args.graphs else 0)
         # n_sets job sets of U units each (the same bytes), used in turn: step
         # k + 1 is submitted before step k is waited for, as a streaming
         # application keeps the pipeline full
@@ -429,16 +462,22 @@ def run_ours(args, ws, rank, local):
         for tm in stamps:
             lat.extend(((tm[:, 2] - tm[:, 0]).astype(np.float64) / 1e6).tolist())
         launches = launches_value + C.kernel_launches() - launches1
-        clock_info = clocks.stop()
         e2e_value = aggregate_gbs(ws, total_bytes, args.steps, e2e_wall)
+        # results of the units the CPU baseline leg will also hash (checked there)
+        tasks0 = sets[0][0]
+        for u in range(min(U, args.check_units)):
+            o = tasks0[u].output()
+            gpu_results[u] = o[:8 + 4 * ((N + 31) // 32) + (4 + C.digest_size(KIND)) * int.from_bytes(o[:4], "little")]
         # the same job shapes with the dummy kernel (copies only): the transfer ceiling
         t1 = time.perf_counter()
         run_steps(args.steps, C.CRYSTAL_KIND_NOP)
         copy_only = aggregate_gbs(ws, total_bytes, args.steps, slowest(time.perf_counter() - t1))
     else:
-        clock_info = clocks.stop()
         e2e_value, lat, e2e_wall, launches, copy_only = None, [0.0], None, launches_value, None
         tasks, ctx = [], None
+    # integer-pipe microbenchmarks, inside the clock record of the timed legs
+    pipes = measure_int_pipes(torch, dev, C)
+    clock_info = clocks.stop()
 
     # ---- host link (pinned copies) measured on this GPU ----
     out_bytes = U * out_size
@@ -458,12 +497,18 @@ def run_ours(args, ws, rank, local):
     if _kernel_sources_hash() == WINDOW_TRAFFIC_SOURCES and N == 1 << 20 and args.hash == "md5":
         traffic = round(WINDOW_TRAFFIC_PER_UNIT * U)
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak = SM_COUNT_B300 * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
-    alu_bound_gbs = peak * 1e12 / ops_per_window  # windows/s = bytes/s
+    nominal = SM_COUNT_B300 * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
+    peak = pipes["lop3_imad"] / 1e12  # measured: the most int32 instructions the SMs issue per second
+    mix_name = "sha1_windows" if args.hash == "sha1" else "md5_windows"
+    mix_ceiling = pipes[mix_name] * ops_per_window / 1e12  # the window hash itself, no memory
+    alu_bound_gbs = pipes[mix_name]  # windows/s = bytes/s
     e2e_bound = min(h2d * GB, duplex_in * GB, alu_bound_gbs, d2h * GB * total_bytes / out_bytes) / GB
 
     out = {
-        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "metric": METRIC, "value": round(value, 3),
+        "value_basis": "hashed GB/s with the inputs resident in HBM (the kernel chain through the C ABI); the "
+                       "host-to-digests figure of the metric is e2e.value",
+        "device_resident_gbs": round(value, 3), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"sliding-window {args.hash.upper()}, {U} units x {N // 1024} KiB, w=20, "
@@ -478,10 +523,22 @@ def run_ours(args, ws, rank, local):
                    "graphs": bool(args.graphs)},
         "roofline": {"bound": "alu", "kernel": "k_sliding_windows", "achieved": round(achieved, 3),
                      "peak": round(peak, 3), "unit": "Tops/s (int32)", "frac": round(achieved / peak, 4),
+                     "peak_basis": "measured: LOP3 and IMAD chains alternating (integer ALU and FMA pipes "
+                                   "dual-issuing), crystal_alu_probe, CUDA events, at the sampled clock",
                      "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
                      "ops_per_window": ops_per_window, "windows_per_launch": windows,
                      "avg_launch_ms": round(win_avg_s * 1e3, 4),
-                     "peak_basis": f"{SM_COUNT_B300} SMs x {INT_LANES_PER_SM} int32 lanes/clk x {sm_max:.0f} MHz"},
+                     "window_hash_ceiling": round(mix_ceiling, 3),
+                     "frac_of_window_hash_ceiling": round(achieved / mix_ceiling, 4),
+                     "window_hash_ceiling_basis": f"measured: the {args.hash.upper()} 20-byte window hash on "
+                                                  "register data (crystal_alu_probe), windows/s x ops_per_window",
+                     "nominal_issue_peak": round(nominal, 3),
+                     "frac_of_nominal_issue_peak": round(achieved / nominal, 4),
+                     "nominal_basis": f"{SM_COUNT_B300} SMs x {INT_LANES_PER_SM} int32 lanes/clk x {sm_max:.0f} MHz",
+                     "pipes_measured_Tops": {k: round(v / 1e12, 3) for k, v in pipes.items()
+                                             if not k.endswith("windows")},
+                     "windows_per_s_measured_G": {k: round(v / 1e9, 2) for k, v in pipes.items()
+                                                  if k.endswith("windows")}},
         "e2e": None if e2e_value is None else {
             "value": round(e2e_value, 3), "unit": "GB/s", "h2d_bytes_per_step": total_bytes * ws,
             "d2h_bytes_per_step": U * out_size * ws, "ms_per_step": round(e2e_wall * 1e3 / args.steps, 3),
@@ -489,8 +546,7 @@ def run_ours(args, ws, rank, local):
                            "p99": round(float(np.percentile(lat, 99)), 3)},
             "roofline_gbs": round(e2e_bound, 2), "frac": round(e2e_value / ws / e2e_bound, 4),
             "roofline_basis": "min(best measured H2D, measured H2D+D2H duplex rate scaled to the input share, "
-                              "best measured D2H scaled to the output bytes, issue-rate ALU bound of the window "
-                              "kernel)",
+                              "best measured D2H scaled to the output bytes, measured window-hash ceiling)",
             "copy_only_gbs": round(copy_only, 3),
             "copy_only_note": "the same jobs with the dummy kernel: copy-in and copy-out only"},
         "host_link": link,
@@ -499,6 +555,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches_split": {"value_region": int(launches_value), "e2e_region": int(launches - launches_value)},
         "wall_s": round(wall, 3),
     }
+    out["_gpu_results"] = gpu_results
     if ctx is not None:
         ctx.shutdown()
     if dist is not None:
@@ -561,6 +618,262 @@ def run_direct_value(args, ws, rank, local):
                                 "compressions_per_s_G": round(blocks / seg_ms / 1e6, 2)},
             "outer_kernel_ms": round(tot_ms - seg_ms, 4)}
     print(json.dumps(line))
+
+
+# ---- the other configurations, as compact records of the default line -------------
+
+class Checks:
+    """Outputs the GPU produced for a seeded sample of a configuration's units
+    (at least 1%, always including its largest direct and sliding units),
+    with what the oracle needs to recompute them.  The CPU-baseline leg runs
+    the oracle on exactly these units: its rate is that record's
+    ``cpu_baseline`` and the comparison its ``verified`` record."""
+
+    def __init__(self):
+        self.items = []  # (kind, host bytes, out_size, oracle params, GPU used bytes)
+
+    def add(self, kind, data, out_size, got, params=None):
+        self.items.append((int(kind), data, int(out_size), params or {}, bytes(got)))
+
+    def run_oracle(self, cores: int):
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+
+        oracle.build()
+        order = sorted(range(len(self.items)), key=lambda i: -len(self.items[i][1]))
+
+        def one(i):
+            kind, data, osz, prm, got = self.items[i]
+            st, want = oracle.task(kind, data, osz, **prm)
+            return st in (0, 1) and want[:len(got)] == got and len(got) > 0
+
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=cores) as ex:
+            ok = list(ex.map(one, order))
+        dt = time.perf_counter() - t0
+        nbytes = sum(len(x[1]) for x in self.items)
+        cpu = {"value": round(nbytes / dt / GB, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"the {len(self.items)} checked units ({nbytes / 1e6:.1f} MB), {cores} threads, {dt:.1f} s"}
+        ver = {"units_checked": len(ok), "bit_exact": int(sum(ok)), "against": "the oracle, every output byte",
+               "largest_checked_bytes": max((len(x[1]) for x in self.items), default=0)}
+        return cpu, ver
+
+
+def _sample(sizes, kinds, every: int):
+    """Indices every ``every``-th plus the largest direct and largest sliding unit."""
+    from paper_1005_1695_b300 import crystal as C
+
+    idx = set(range(0, len(sizes), every))
+    for group in (C.DIRECT_KINDS, C.SLIDING_KINDS):
+        cand = [i for i in range(len(sizes)) if int(kinds[i]) in group]
+        if cand:
+            idx.add(max(cand, key=lambda i: int(sizes[i])))
+    return sorted(idx)
+
+
+def record_config1(args, local, link):
+    """64 x 64 KiB, direct hashing, 4 KiB segments: the plain form (per-job
+    allocation, one stream, one job at a time) against the pooled,
+    overlapped, batched form; every unit checked."""
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    U, N = 64, 65536
+    p = C.params(segment_bytes=4096)
+    units = [inputs.uniform_unit(args.seed, i, N) for i in range(U)]
+    rec, checks = {"workload": f"plain direct hashing, {U} units x 64 KiB, S=4 KiB"}, Checks()
+    for mode in ("plain", "pooled"):
+        runs = [S.run_stream(mode, lambda i: units[i], U, N, C.CRYSTAL_KIND_MD5_DIRECT, p, 16, streams=8,
+                             batch_jobs=8, device=local, keep=range(U)) for _ in range(3)]
+        r = sorted(runs, key=lambda x: x.seconds)[1]
+        assert all(st == 0 for st in r.statuses)
+        rec[mode] = {"GB_per_s": round(r.gbs, 3), "latency_ms": {"p50": round(r.latency(50), 3),
+                                                                  "p99": round(r.latency(99), 3)}}
+        if mode == "pooled":
+            for i in range(U):
+                checks.add(C.CRYSTAL_KIND_MD5_DIRECT, units[i], 16, r.outputs[i], {"seg_bytes": 4096})
+    rec["speedup_pooled_vs_plain"] = round(rec["pooled"]["GB_per_s"] / rec["plain"]["GB_per_s"], 2)
+    return rec, checks
+
+
+def record_config3(args, local, link):
+    """Pipelined direct hashing of 4 MiB units (4 KiB segments) over 8 streams:
+    pooled jobs resident in pinned memory, the staging ring fed from pageable
+    memory by C++ copy threads, one job at a time (no overlap), and per-job
+    allocation."""
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import streams as S
+
+    U, N = args.c3_units, 4 << 20
+    # units are 4 MiB windows at seeded offsets of a 2 GiB pageable arena
+    arena_bytes = 2 << 30
+    arena = _arena_pageable(args.seed + 3, arena_bytes)
+    offs = (np.arange(U, dtype=np.int64) * 7919 * 4096 + 13 * np.arange(U)) % (arena_bytes - N)
+    unit = lambda i: arena[int(offs[i]):int(offs[i]) + N]
+    p = C.params(segment_bytes=4096)
+    h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
+    pin = torch.empty(256 << 20, dtype=torch.uint8, pin_memory=True).numpy()
+    pin[:] = 0
+    t0 = time.perf_counter()
+    np.copyto(pin, arena[:256 << 20])
+    memcpy1 = (256 << 20) / (time.perf_counter() - t0) / GB
+    del pin
+    sample = list(range(0, U, max(1, U // 8)))
+    rec = {"workload": f"pipelined direct hashing, {U} units x 4 MiB, S=4 KiB, 8 streams x 8 jobs per batch",
+           "host_link_h2d_gbs": h2d}
+    checks = Checks()
+    modes = [("pooled", U), ("pooled_staged", U), ("no_overlap", U), ("per_job_malloc", min(U, args.malloc_units))]
+    for mode, n in modes:
+        r = S.run_stream(mode, unit, n, N, C.CRYSTAL_KIND_MD5_DIRECT, p, 16, streams=8, batch_jobs=8,
+                         depth=args.ring_jobs if mode == "pooled_staged" else args.depth,
+                         copy_threads=args.copy_threads, device=local, keep=[i for i in sample if i < n])
+        assert all(st == 0 for st in r.statuses), (mode, set(r.statuses))
+        rec[mode] = {"units": n, "GB_per_s": round(r.gbs, 3), "frac_of_link": round(r.gbs / h2d, 4)}
+        for i in sample:
+            if i < n and mode in ("pooled", "pooled_staged"):
+                checks.add(C.CRYSTAL_KIND_MD5_DIRECT, unit(i), 16, r.outputs[i], {"seg_bytes": 4096})
+    bound = min(memcpy1 * args.copy_threads, h2d)
+    rec["pooled_staged"].update({"copy_threads": args.copy_threads, "ring_jobs": args.ring_jobs,
+                                 "memcpy_1thread_gbs": round(memcpy1, 2), "roofline_gbs": round(bound, 2),
+                                 "frac_of_roofline": round(rec["pooled_staged"]["GB_per_s"] / bound, 4),
+                                 "roofline_basis": "min(one-thread pageable->pinned memcpy x copy threads, H2D)"})
+    rec["speedup_pooled_vs_per_job_malloc"] = round(rec["pooled"]["GB_per_s"] / rec["per_job_malloc"]["GB_per_s"], 2)
+    rec["speedup_pooled_vs_no_overlap"] = round(rec["pooled"]["GB_per_s"] / rec["no_overlap"]["GB_per_s"], 2)
+    return rec, checks
+
+
+def _arena_pageable(seed: int, nbytes: int) -> np.ndarray:
+    from paper_1005_1695_b300 import inputs
+
+    return inputs.arena(seed, nbytes)
+
+
+def record_config4(args, local, link):
+    """Uneven units (log-uniform 4 KiB - 16 MiB, 80/20 direct/sliding) read in
+    place from a page-locked arena, autotuned, replayed as CUDA graphs;
+    against the plain single-stream form on a sample."""
+    from paper_1005_1695_b300 import autotune as A
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    U = args.c4_units
+    arena_bytes = 2 << 30
+    src = inputs.arena(args.seed + 4, arena_bytes, out=C.page_aligned(arena_bytes))
+    req, _ = S.make_batch(args.seed + 4, U, src.nbytes)
+    sample = _sample(req["size"], req["kind"], 100)
+    req["capture_offset"] = C.NO_CAPTURE
+    cap = 0
+    for i in sample:
+        req["capture_offset"][i] = cap
+        cap += int(req["out_size"][i] + 15) // 16 * 16
+    capture = np.zeros(cap, dtype=np.uint8)
+    pool = 4 << 30
+    h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
+    C.host_register(src)
+    try:
+        tune_req = req[:min(U, 1000)].copy()
+        tune_req["capture_offset"] = C.NO_CAPTURE
+        best, table = A.tune(tune_req, src, device_pool_bytes=pool, device=local, streams=(8, 16),
+                             batch_jobs=(8, 32), batch_bytes=(64 << 20,), repeats=1)
+        st, res, wall = A.run_batch(req, src, best, device_pool_bytes=pool, device=local, capture=capture)
+        C.check(st, "crystal_serve")
+        plain_n = min(U, args.c4_plain_units)
+        plain_req = req[:plain_n].copy()
+        plain_req["capture_offset"] = C.NO_CAPTURE
+        stp, resp, wallp = A.run_batch(plain_req, src, A.Setting(1, 1, 64 << 20), device_pool_bytes=pool,
+                                       device=local, submit_threads=1,
+                                       flags=C.CRYSTAL_FLAG_NO_OVERLAP | C.CRYSTAL_FLAG_NO_BATCH)
+        C.check(stp, "crystal_serve")
+    finally:
+        C.host_unregister(src)
+    total = float(req["size"].sum())
+    gbs = total / (wall / 1e9) / GB
+    plain = float(plain_req["size"].sum()) / (wallp / 1e9) / GB
+    checks = Checks()
+    for i in sample:
+        o, n, off = int(req["src_offset"][i]), int(req["size"][i]), int(req["capture_offset"][i])
+        checks.add(int(req["kind"][i]), src[o:o + n], int(req["out_size"][i]),
+                   capture[off:off + int(res["used_bytes"][i])])
+    rec = {"workload": f"{U} units, log-uniform 4 KiB-16 MiB, 80/20 direct/sliding (w=20), inputs read in place "
+                       f"from a 2 GiB page-locked arena, CUDA graphs, autotuned",
+           "GB": round(total / GB, 2), "GB_per_s": round(gbs, 3), "frac_of_link": round(gbs / h2d, 4),
+           "chosen": best.as_dict(), "tuning_table": table, "tuning_sample_units": len(tune_req),
+           "plain_single_stream": {"units": plain_n, "GB_per_s": round(plain, 3)},
+           "speedup_vs_plain": round(gbs / plain, 2)}
+    return rec, checks
+
+
+def record_config5(args, local, link):
+    """Open-loop Poisson request streams through crystal_serve: lognormal sizes
+    (median 256 KiB, sigma 1.5, cap 64 MiB), 70/30 direct/sliding, inputs read
+    in place from a page-locked arena, 8 GiB device pool."""
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    arena_bytes = 1 << 30
+    src = inputs.arena(args.seed + 5, arena_bytes, out=C.page_aligned(arena_bytes))
+    pool = args.pool_bytes
+    h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
+    # the host pool holds outputs only (inputs are read in place from the arena)
+    ctx = C.Context(max_in_bytes=64 << 20, max_out_bytes=C.sliding_out_bytes(64 << 20, 4 * 8192 + 64),
+                    device_pool_bytes=pool, host_pool_bytes=1 << 30, n_streams=args.streams, device=local,
+                    max_batch_jobs=args.batch_jobs, max_batch_bytes=32 << 20, flags=C.CRYSTAL_FLAG_GRAPHS)
+    rec = {"workload": "open-loop Poisson requests, lognormal sizes (median 256 KiB, sigma 1.5, cap 64 MiB), "
+                       f"70/30 direct/sliding, {pool >> 30} GiB device pool, {args.streams} streams, "
+                       f"{args.batch_jobs} jobs per batch, inputs read in place from a page-locked arena",
+           "rates_per_s": {}}
+    checks = Checks()
+    C.host_register(src)
+    try:
+        warm, _ = S.make_trace(args.seed + 1, 2000, 10000.0, src.nbytes)
+        C.check(ctx.serve(src, warm, copy_threads=args.copy_threads, source_pinned=True)[0], "crystal_serve")
+        for rate in args.c5_rates:
+            n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
+            req, _ = S.make_trace(args.seed, n, rate, src.nbytes)
+            sample = _sample(req["size"], req["kind"], 100)
+            req["capture_offset"] = C.NO_CAPTURE
+            cap = 0
+            for i in sample:
+                req["capture_offset"][i] = cap
+                cap += int(req["out_size"][i] + 15) // 16 * 16
+            capture = np.zeros(cap, dtype=np.uint8)
+            st, res, wall = ctx.serve(src, req, capture=capture, copy_threads=args.copy_threads, source_pinned=True)
+            C.check(st, "crystal_serve")
+            lat = S.latency_ms(req, res)
+            total = int(req["size"].sum())
+            span = float(req["arrival_ns"][-1]) / 1e9
+            gbs = total / (wall / 1e9) / GB
+            rec["rates_per_s"][str(int(rate))] = {
+                "requests": n, "offered_GB_per_s": round(total / max(span, 1e-9) / GB, 3),
+                "GB_per_s": round(gbs, 3), "frac_of_link": round(gbs / h2d, 4),
+                "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                               "p99": round(float(np.percentile(lat, 99)), 3)}}
+            for i in sample:
+                o, nb, off = int(req["src_offset"][i]), int(req["size"][i]), int(req["capture_offset"][i])
+                checks.add(int(req["kind"][i]), src[o:o + nb], int(req["out_size"][i]),
+                           capture[off:off + int(res["used_bytes"][i])])
+    finally:
+        ctx.shutdown()
+        C.host_unregister(src)
+    return rec, checks
+
+
+def run_config_records(args, local, link):
+    """Records of configurations 1, 3, 4 and 5 (GPU part); returns
+    {name: (record, checks)}."""
+    out = {}
+    for name, fn in (("config1_plain", record_config1), ("config3_pipelined", record_config3),
+                     ("config4_batched", record_config4), ("config5_served", record_config5)):
+        t0 = time.perf_counter()
+        rec, checks = fn(args, local, link)
+        rec["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[name] = (rec, checks)
+    return out
 
 
 def run_stream_modes(args, local, kind, unit_bytes, n_units, modes, subset=None):
@@ -654,7 +967,7 @@ def run_serving(args, ws, rank, local):
     ctx = C.Context(max_in_bytes=64 << 20, max_out_bytes=C.sliding_out_bytes(64 << 20, 4 * 8192 + 64),
                     device_pool_bytes=pool, host_pool_bytes=pool, n_streams=args.streams, device=local,
                     max_batch_jobs=args.batch_jobs, max_batch_bytes=32 << 20,
-                    flags=C.CRYSTAL_FLAG_GRAPHS | copy_flags(args, C))
+                    flags=C.CRYSTAL_FLAG_GRAPHS)
     out = {}
     pinned = args.source == "pinned"
     if pinned:
@@ -667,7 +980,9 @@ def run_serving(args, ws, rank, local):
         for rate in rates:
             n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
             req, _ = S.make_trace(args.seed, n, rate, src.nbytes)
+            s0 = ctx.stats()
             st, res, wall = ctx.serve(src, req, copy_threads=args.copy_threads, source_pinned=pinned)
+            s1 = ctx.stats()
             ok = res["status"] == 0
             lat = S.latency_ms(req, res)[ok]
             wait = (res["admit_ns"].astype(np.float64) - req["arrival_ns"].astype(np.float64))[ok] / 1e6
@@ -679,7 +994,14 @@ def run_serving(args, ws, rank, local):
                 "GB_per_s": round(total / (wall / 1e9) / 1e9, 3),
                 "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                                "p99": round(float(np.percentile(lat, 99)), 3)},
-                "admission_wait_ms_p99": round(float(np.percentile(wait, 99)), 3)}
+                "admission_wait_ms_p99": round(float(np.percentile(wait, 99)), 3),
+                "batches": int(s1.batches_launched - s0.batches_launched),
+                "dma_copies": int(s1.copies_dma - s0.copies_dma),
+                "master_busy_frac": round((s1.master_issue_ns + s1.master_complete_ns - s0.master_issue_ns -
+                                           s0.master_complete_ns) / max(wall, 1), 3),
+                "create_busy_frac": round((s1.create_ns - s0.create_ns) / max(wall, 1), 3),
+                "create_calls": int(s1.create_calls - s0.create_calls),
+                "create_eagain": int(s1.create_eagain - s0.create_eagain)}
     finally:
         ctx.shutdown()
         if pinned:
@@ -714,7 +1036,7 @@ def run_batched(args, ws, rank, local):
     C.host_register(src)
     try:
         sample = req[:min(U, args.tune_units)]
-        xf = C.CRYSTAL_FLAG_GRAPHS | copy_flags(args, C)
+        xf = C.CRYSTAL_FLAG_GRAPHS
         best, table = A.tune(sample, src, device_pool_bytes=pool, device=local, flags=xf)
         st, res, wall = A.run_batch(req, src, best, device_pool_bytes=pool, device=local, flags=xf)
         C.check(st, "crystal_serve")
@@ -834,8 +1156,6 @@ def main():
     ap.add_argument("--max-chunks", type=int, default=1024)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--batch-jobs", type=int, default=8)
-    ap.add_argument("--copy", choices=["dma", "sm"], default="dma",
-                    help="job-buffer copies: all by DMA (default), or runs under 1 MiB by the SMs")
     ap.add_argument("--e2e-sets", type=int, default=2,
                     help="job sets the e2e leg alternates (1: each step waits before the next is submitted)")
     ap.add_argument("--graphs", type=int, default=1)
@@ -860,6 +1180,13 @@ def main():
     ap.add_argument("--depth", type=int, default=24, help="jobs in flight for staged / per-job-allocation modes")
     ap.add_argument("--malloc-units", type=int, default=512, help="units for the per-job-allocation modes")
     ap.add_argument("--segment-bytes", type=int, default=4096)
+    ap.add_argument("--configs", type=int, default=1,
+                    help="add the records of configurations 1, 3, 4 and 5 to the default line (rank 0)")
+    ap.add_argument("--c3-units", type=int, default=512)
+    ap.add_argument("--ring-jobs", type=int, default=48, help="staging ring of the pageable-source form")
+    ap.add_argument("--c4-units", type=int, default=5000)
+    ap.add_argument("--c4-plain-units", type=int, default=300)
+    ap.add_argument("--c5-rates", default="10000,50000")
     args = ap.parse_args()
     ws, rank, local = _dist()
     cores = len(os.sched_getaffinity(0))
@@ -909,11 +1236,26 @@ def main():
         {"direct": run_direct_value, "plain": run_plain, "pipelined": run_pipelined}[args.workload](
             args, ws, rank, local)
         return
+    args.check_units = cpu_units
+    args.c5_rates = [float(r) for r in args.c5_rates.split(",")] if isinstance(args.c5_rates, str) else args.c5_rates
     out = run_ours(args, ws, rank, local)
+    gpu_results = out.pop("_gpu_results")
+    link = out["host_link"]
+    records = run_config_records(args, local, link) if (args.configs and rank == 0) else {}
     if rank == 0:
+        if records:
+            out["configs"] = {}
+            for name, (rec, checks) in records.items():
+                if not args.no_cpu_baseline:
+                    rec["cpu_baseline"], rec["verified"] = checks.run_oracle(cores)
+                out["configs"][name] = rec
         if not args.no_cpu_baseline:
+            kind = 4 if args.hash == "sha1" else 2
             host = sliding_workload(args.seed, cpu_units, args.unit_bytes)
-            out["cpu_baseline"] = cpu_oracle_rate(host, args.unit_bytes, cpu_units, cores, params)
+            cb = cpu_oracle_rate(host, args.unit_bytes, cpu_units, cores, params, kind=kind,
+                                 results=gpu_results)
+            out["verified"] = cb.pop("_verified")
+            out["cpu_baseline"] = cb
             out["cpu_oracle_detail"] = cpu_oracle_detail(host, args.unit_bytes, cores, params)
         print(json.dumps(out))
 

@@ -68,18 +68,7 @@ enum {
     CRYSTAL_FLAG_NO_BATCH = 4u,
     /* Replay each batch's descriptor upload and kernel chain as a captured
      * CUDA graph instead of individual launches. */
-    CRYSTAL_FLAG_GRAPHS = 8u,
-    /* Pooled mode: copy contiguous runs of a batch's job buffers smaller than
-     * 1 MiB with a kernel that reads or writes the mapped pinned host memory
-     * instead of the DMA engines.  A DMA transfer has a fixed cost of a few
-     * microseconds (about 3.7 us on B300: 256 KiB moves at 30 GB/s), while the
-     * kernel moves scattered pieces of any size at about 48 GB/s -- but it needs
-     * free SMs, and behind busy hashing kernels it waits where the DMA engines
-     * would overlap: on B300 it was slower for served request streams and
-     * uneven batches and no faster for 1 MiB jobs, so it is off by default.
-     * Inputs bound with crystal_task_bind_input take this path when their
-     * memory is mapped (page-locked with crystal_host_register, or by CUDA). */
-    CRYSTAL_FLAG_SM_COPY = 16u
+    CRYSTAL_FLAG_GRAPHS = 8u
 };
 
 /* crystal_init's argument.  Zero fields take the defaults listed. */
@@ -247,6 +236,36 @@ int crystal_task_timing(crystal_task* task, uint64_t* submit_ns, uint64_t* dispa
  * then partly written). */
 int crystal_task_timing_many(crystal_task* const* tasks, uint32_t n, uint64_t* out);
 
+/* The configuration a context runs with (defaults filled in; n_streams is 1
+ * under CRYSTAL_FLAG_NO_OVERLAP). */
+int crystal_get_config(crystal_ctx* ctx, crystal_config* out);
+
+/* Launch geometry of the hashing kernels (the paper has no counterpart: it
+ * leaves the kernel to the application).  The runtime sorts each batch into
+ * one of CRYSTAL_SIZE_CLASSES classes by the mean input size of its hashing
+ * jobs (< 64 KiB, < 1 MiB, >= 1 MiB) and launches the batch with that class's
+ * geometry, which an autotuner may set from measurements.  Zero fields take
+ * the defaults; CTAs per SM are capped at what fits.  Results never depend on
+ * the geometry (every kernel walks its work in a grid-stride loop). */
+typedef struct crystal_geometry {
+    uint32_t seg_threads;        /* segment digests: threads per CTA, 64, 128 or 256 (0: 128) */
+    uint32_t seg_ctas_per_sm;    /* segment digests: CTAs per SM (0: as many as fit) */
+    uint32_t win_ctas_per_sm;    /* window kernel: CTAs per SM (0: as many as fit) */
+    uint32_t win_registers;      /* w = 20 MD5 window kernel: 32 or 64 registers per thread (0: 32) */
+    uint32_t digest_ctas_per_sm; /* chunk segment digests: CTAs per SM (0: as many as fit) */
+    uint32_t reserved;           /* must be 0 */
+} crystal_geometry;
+#define CRYSTAL_SIZE_CLASSES 3
+
+/* Set the geometry of size class size_class (0..2; -1: every class) of a
+ * context; g NULL restores the defaults.  Only while the context is idle (no
+ * job outstanding or running): EINVAL otherwise, or for a bad class or field;
+ * the class's captured graphs are dropped and re-captured on next use. */
+int crystal_set_geometry(crystal_ctx* ctx, int size_class, const crystal_geometry* g);
+
+/* The geometry a class runs with, resolved (CTAs per SM as launched). */
+int crystal_get_geometry(crystal_ctx* ctx, int size_class, crystal_geometry* out);
+
 /* Counters of a context. */
 typedef struct crystal_stats {
     uint64_t jobs_completed;
@@ -254,8 +273,12 @@ typedef struct crystal_stats {
     uint64_t device_pool_bytes, device_pool_used;
     uint64_t host_pool_bytes, host_pool_used;
     uint64_t jobs_outstanding, jobs_running;
-    uint64_t copies_dma;  /* job-buffer copies issued to the DMA engines */
-    uint64_t copies_sm;   /* job-buffer copies made by k_copy_pieces (CRYSTAL_FLAG_SM_COPY) */
+    uint64_t copies_dma;  /* job-buffer copies issued to the DMA engines (merged runs count once) */
+    uint64_t master_issue_ns;    /* master-thread time spent issuing batches (copies, launches) */
+    uint64_t master_complete_ns; /* master-thread time spent completing batches (statuses, callbacks) */
+    uint64_t create_ns;          /* time spent inside crystal_task_create[_ex] (all threads) */
+    uint64_t create_calls;       /* calls of crystal_task_create[_ex] */
+    uint64_t create_eagain;      /* of which returned CRYSTAL_EAGAIN (pool full) */
 } crystal_stats;
 int crystal_get_stats(crystal_ctx* ctx, crystal_stats* out);
 
@@ -277,6 +300,31 @@ const char* crystal_strerror(int status);
 /* Kernel launches this process made through the library (all contexts and
  * launchers; a graph replay counts each kernel node). */
 uint64_t crystal_kernel_launches(void);
+
+/* Microbenchmark of the integer pipes the hashing kernels are bound by (the
+ * paper has no counterpart; it gives the integer roofline its measured
+ * denominator).  Launches one kernel of ctas_per_sm x SMs CTAs of 256 threads
+ * on `stream` that runs `iters` iterations on register data only -- no memory
+ * is read, and d_sink (4 bytes of device memory) is written only if the
+ * result equals `magic`, so no work can be optimised away.  Time it with
+ * events on `stream`.  *work (may be NULL) receives the work the launch
+ * performs: windows for the two window kinds (each a 20-byte window's hash up
+ * to its first digest word, eight per thread per iteration, message words
+ * shared from a ring of registers as the window kernel shares them), single
+ * instructions for the others (eight independent chains per thread).
+ * EINVAL for a bad kind, iters = 0, ctas_per_sm outside 1..64 or a NULL
+ * d_sink; EDEVICE on a launch error. */
+enum {
+    CRYSTAL_PROBE_MD5_WINDOWS = 0,  /* MD5 window hash, w = 20, as k_sliding_windows<20> computes it */
+    CRYSTAL_PROBE_SHA1_WINDOWS = 1, /* SHA-1 window hash, w = 20 */
+    CRYSTAL_PROBE_LOP3 = 2,         /* three-input logic op (integer ALU pipe) */
+    CRYSTAL_PROBE_SHF = 3,          /* funnel shift / rotate (integer ALU pipe) */
+    CRYSTAL_PROBE_IADD3 = 4,        /* three-input add */
+    CRYSTAL_PROBE_IMAD = 5,         /* integer multiply-add (FMA pipe) */
+    CRYSTAL_PROBE_LOP3_IMAD = 6     /* LOP3 and IMAD alternately: two pipes at once */
+};
+int crystal_alu_probe(int kind, uint32_t ctas_per_sm, uint32_t iters, uint32_t magic, uint32_t* d_sink,
+                      void* stream, uint64_t* work);
 
 /* The baseline of the overhead experiment (Section 5.1, Figure 5): one job
  * issued without the framework -- copy in_size bytes h_in -> d_in, launch a
@@ -393,9 +441,13 @@ int crystal_launch_batch(const crystal_batch* batch_dev, void* stream);
  * crystal_serve plays an open-loop stream of requests against a context
  * (stream-processing applications, Section 2.2: data units arrive
  * continuously and each needs low latency).  Request i arrives arrival_ns
- * after the call starts; requests are admitted in arrival order as soon as
- * the context's pools can hold the job's buffers and scratch
- * (crystal_task_create_ex); copy threads stage the request's bytes from
+ * after the call starts; requests are admitted as soon as the context's pools
+ * can hold the job's buffers and scratch (crystal_task_create_ex), oldest
+ * first: while the oldest waiting request does not fit, later requests that
+ * fit may be admitted past it until it has waited bypass_ns (then nothing
+ * passes it, so room frees up for it and it cannot starve);
+ * CRYSTAL_SERVE_ARRIVAL_ORDER admits strictly in arrival order instead.
+ * Copy threads stage the request's bytes from
  * `source` into the job's pinned input (or, with CRYSTAL_SERVE_SOURCE_PINNED,
  * bind the job's input to them) and submit it; the master thread
  * batches whatever is outstanding (continuous batching).  On completion the
@@ -425,6 +477,7 @@ typedef struct crystal_request_result {
 } crystal_request_result;
 
 #define CRYSTAL_SERVE_SOURCE_PINNED 1u
+#define CRYSTAL_SERVE_ARRIVAL_ORDER 2u
 typedef struct crystal_serve_config {
     uint32_t copy_threads;                      /* staging threads; default 4 */
     uint32_t flags;                             /* CRYSTAL_SERVE_SOURCE_PINNED: `source` is page-locked;
@@ -434,10 +487,53 @@ typedef struct crystal_serve_config {
     const crystal_hash_params* sliding_params;  /* NULL: defaults */
     void* capture;                              /* host buffer for captured outputs, or NULL */
     uint64_t capture_bytes;
+    uint64_t bypass_ns;                         /* how long later requests may pass a blocked oldest
+                                                   request; default (0) 2 ms */
 } crystal_serve_config;
 
 int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, const crystal_request* requests,
                   uint32_t n, const crystal_serve_config* cfg, crystal_request_result* results, uint64_t* wall_ns);
+
+/* ---- a job stream staged from pageable memory -----------------------------
+ * Section 2.1: the DMA engines copy only from page-locked memory, so bytes an
+ * application holds in ordinary (pageable) memory must first be copied into a
+ * pinned buffer; Section 3 keeps pinned job buffers in a pool allocated once,
+ * and Section 4.1 / Figure 4 overlaps the copies of some jobs with the kernels
+ * of others.  crystal_stream_staged hashes units[0..n) (pageable or pinned
+ * host memory, sizes[i] bytes each, read-only during the call) through a ring
+ * of ring_jobs jobs created at the start of the call (each with a pinned
+ * input of the largest unit's size, a pinned output of out_size bytes and its
+ * device scratch reserved) and released at its end:
+ *   - copy_threads host threads take the units in index order, copy each into
+ *     the pinned input of a free job (FIFO over the ring) and submit it;
+ *   - the master thread batches the submitted jobs as for any other job;
+ *   - a finished job returns to the ring; the thread that takes it next first
+ *     copies the finished unit's used output bytes (at most out_stride) to
+ *     outputs + i * out_stride (outputs may be NULL: results not kept).
+ * results[i] receives the unit's status, admit_ns (a ring job taken),
+ * submit_ns (bytes staged, job submitted), done_ns (completion seen by the
+ * master) relative to the call's start, and used_bytes.  *wall_ns (may be
+ * NULL) receives the time from the start to the last result copied out.
+ * ring_jobs 0 = 3 x n_streams x min(max_batch_jobs, 4) (at most n); the
+ * context's pools must hold the ring (host: ring x (largest unit + out_size);
+ * device: the same plus each job's scratch, crystal_scratch_bytes).
+ * Returns CRYSTAL_OK when every unit finished with OK or EOVERFLOW, else the
+ * last other per-unit error; EINVAL for bad arguments (NULL arrays, a unit
+ * larger than the context's max_in_bytes, out_size above max_out_bytes, a
+ * bad kind or params); EAGAIN / ENOMEM if the pools cannot hold the ring (no
+ * unit is then processed). */
+typedef struct crystal_stream_config {
+    int32_t kind;                       /* CRYSTAL_KIND_* of every unit */
+    uint32_t copy_threads;              /* staging threads; default 4, at most 64 */
+    uint32_t ring_jobs;                 /* jobs in the ring; 0 = the default above */
+    uint32_t reserved;                  /* must be 0 */
+    uint64_t out_size;                  /* output bytes of each job */
+    const crystal_hash_params* params;  /* NULL: defaults */
+} crystal_stream_config;
+
+int crystal_stream_staged(crystal_ctx* ctx, const void* const* units, const uint64_t* sizes, uint32_t n,
+                          const crystal_stream_config* cfg, void* outputs, uint64_t out_stride,
+                          crystal_request_result* results, uint64_t* wall_ns);
 
 /* ---- direct hashing that allocates nothing --------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot
@@ -469,7 +565,10 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
  *     wrong digests: order them, e.g. issue them on one stream.
  * Returns CRYSTAL_OK (also for n_units = 0), CRYSTAL_EINVAL (NULL pointers,
  * segment_bytes = 0, misaligned d_digests, or the size limit) or
- * CRYSTAL_EDEVICE (launch failure). */
+ * CRYSTAL_EDEVICE (launch failure; a launch error already pending on the
+ * calling thread from earlier work is reported this way too, and cleared,
+ * before anything is queued; if the descriptor kernel fails to launch, the
+ * hashing kernels are not queued). */
 #define CRYSTAL_NOALLOC_SCRATCH_BYTES (8u << 20)
 int crystal_md5_direct_noalloc(const void* d_in, uint64_t unit_bytes, uint32_t n_units, uint32_t segment_bytes,
                                void* d_digests, void* stream);

@@ -44,7 +44,15 @@ CRYSTAL_FLAG_NO_POOL = 1
 CRYSTAL_FLAG_NO_OVERLAP = 2
 CRYSTAL_FLAG_NO_BATCH = 4
 CRYSTAL_FLAG_GRAPHS = 8
-CRYSTAL_FLAG_SM_COPY = 16
+
+CRYSTAL_PROBE_MD5_WINDOWS = 0
+CRYSTAL_PROBE_SHA1_WINDOWS = 1
+CRYSTAL_PROBE_LOP3 = 2
+CRYSTAL_PROBE_SHF = 3
+CRYSTAL_PROBE_IADD3 = 4
+CRYSTAL_PROBE_IMAD = 5
+CRYSTAL_PROBE_LOP3_IMAD = 6
+PROBE_KINDS = {"md5_windows": 0, "sha1_windows": 1, "lop3": 2, "shf": 3, "iadd3": 4, "imad": 5, "lop3_imad": 6}
 
 
 
@@ -77,7 +85,8 @@ class crystal_hash_params(ctypes.Structure):
 class crystal_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "jobs_completed", "batches_launched", "device_pool_bytes", "device_pool_used",
-        "host_pool_bytes", "host_pool_used", "jobs_outstanding", "jobs_running", "copies_dma", "copies_sm")]
+        "host_pool_bytes", "host_pool_used", "jobs_outstanding", "jobs_running", "copies_dma",
+        "master_issue_ns", "master_complete_ns", "create_ns", "create_calls", "create_eagain")]
 
 
 UNIT_DTYPE = np.dtype([
@@ -100,12 +109,37 @@ NO_CAPTURE = (1 << 64) - 1
 
 CRYSTAL_TASK_EXTERNAL_INPUT = 1
 CRYSTAL_SERVE_SOURCE_PINNED = 1
+CRYSTAL_SERVE_ARRIVAL_ORDER = 2
+
+
+class crystal_geometry(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("seg_threads", "seg_ctas_per_sm", "win_ctas_per_sm", "win_registers",
+                                               "digest_ctas_per_sm", "reserved")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
+
+
+CRYSTAL_SIZE_CLASSES = 3
+SIZE_CLASS_NAMES = ("under 64 KiB", "64 KiB to 1 MiB", "1 MiB and up")
+
+
+def geometry(**kw) -> crystal_geometry:
+    g = crystal_geometry()
+    for k, v in kw.items():
+        setattr(g, k, int(v))
+    return g
+
+
+class crystal_stream_config(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("copy_threads", ctypes.c_uint32), ("ring_jobs", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("out_size", ctypes.c_uint64), ("params", ctypes.c_void_p)]
 
 
 class crystal_serve_config(ctypes.Structure):
     _fields_ = [("copy_threads", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("direct_params", ctypes.c_void_p), ("sliding_params", ctypes.c_void_p),
-                ("capture", ctypes.c_void_p), ("capture_bytes", ctypes.c_uint64)]
+                ("capture", ctypes.c_void_p), ("capture_bytes", ctypes.c_uint64), ("bypass_ns", ctypes.c_uint64)]
 
 _lib = None
 _u64 = ctypes.c_uint64
@@ -148,6 +182,11 @@ def load() -> ctypes.CDLL:
         "crystal_host_unregister": (ctypes.c_int, [_vp]),
         "crystal_serve": (ctypes.c_int, [_vp, _vp, _u64, _vp, ctypes.c_uint32, ctypes.POINTER(crystal_serve_config),
                                          _vp, ctypes.POINTER(_u64)]),
+        "crystal_stream_staged": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_uint32, ctypes.POINTER(crystal_stream_config),
+                                                 _vp, _u64, _vp, ctypes.POINTER(_u64)]),
+        "crystal_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(crystal_config)]),
+        "crystal_set_geometry": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(crystal_geometry)]),
+        "crystal_get_geometry": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(crystal_geometry)]),
         "crystal_task_wait": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "crystal_task_release": (ctypes.c_int, [_vp]),
         "crystal_task_timing": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64),
@@ -161,6 +200,8 @@ def load() -> ctypes.CDLL:
         "crystal_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "crystal_kernel_launches": (_u64, []),
         "crystal_direct_job": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _u64, _vp]),
+        "crystal_alu_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp,
+                                             _vp, ctypes.POINTER(_u64)]),
         "crystal_scratch_bytes": (_u64, [ctypes.c_int, _u64, _u64, ctypes.POINTER(crystal_hash_params)]),
         "crystal_batch_plan": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32]),
         "crystal_batch_bytes": (_u64, [ctypes.c_uint32]),
@@ -348,15 +389,21 @@ class Context:
 
     def serve(self, source: np.ndarray, requests: np.ndarray, direct: Optional[crystal_hash_params] = None,
               sliding: Optional[crystal_hash_params] = None, capture: Optional[np.ndarray] = None,
-              copy_threads: int = 4, source_pinned: bool = False):
+              copy_threads: int = 4, source_pinned: bool = False, arrival_order: bool = False,
+              bypass_ns: int = 0):
         """crystal_serve: play ``requests`` (REQUEST_DTYPE, arrival order)
-        against this context.  Returns (status, results, wall_ns)."""
+        against this context.  ``arrival_order`` admits strictly in arrival
+        order; otherwise later requests that fit may pass a blocked oldest one
+        for ``bypass_ns`` (0: the library's default).  Returns (status,
+        results, wall_ns)."""
         src = np.ascontiguousarray(source, dtype=np.uint8)
         req = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
         res = np.zeros(len(req), dtype=RESULT_DTYPE)
         cfg = crystal_serve_config()
         cfg.copy_threads = copy_threads
-        cfg.flags = CRYSTAL_SERVE_SOURCE_PINNED if source_pinned else 0
+        cfg.flags = (CRYSTAL_SERVE_SOURCE_PINNED if source_pinned else 0) | \
+            (CRYSTAL_SERVE_ARRIVAL_ORDER if arrival_order else 0)
+        cfg.bypass_ns = bypass_ns
         cfg.direct_params = ctypes.cast(ctypes.pointer(direct), ctypes.c_void_p) if direct is not None else None
         cfg.sliding_params = ctypes.cast(ctypes.pointer(sliding), ctypes.c_void_p) if sliding is not None else None
         if capture is not None:
@@ -365,6 +412,46 @@ class Context:
         st = load().crystal_serve(self.handle, src.ctypes.data, src.nbytes, req.ctypes.data, len(req),
                                   ctypes.byref(cfg), res.ctypes.data, ctypes.byref(wall))
         return st, res, wall.value
+
+    def stream_staged(self, units: Sequence[np.ndarray], kind: int, out_size: int,
+                      p: Optional[crystal_hash_params] = None, copy_threads: int = 4, ring_jobs: int = 0,
+                      out_stride: Optional[int] = None, keep_outputs: bool = True):
+        """crystal_stream_staged: hash ``units`` (host uint8 arrays, e.g. views
+        of one pageable buffer) through a ring of pinned jobs filled by
+        ``copy_threads`` C++ threads.  Returns (status, results, wall_ns,
+        outputs) with ``outputs`` an (n, out_stride) uint8 array or None."""
+        n = len(units)
+        arrs = [np.ascontiguousarray(u, dtype=np.uint8) for u in units]
+        ptrs = (_vp * max(n, 1))(*[a.ctypes.data for a in arrs])
+        sizes = np.array([a.nbytes for a in arrs], dtype=np.uint64)
+        stride = out_stride if out_stride is not None else out_size
+        outs = np.zeros((n, stride), dtype=np.uint8) if keep_outputs and n else None
+        res = np.zeros(n, dtype=RESULT_DTYPE)
+        cfg = crystal_stream_config()
+        cfg.kind, cfg.copy_threads, cfg.ring_jobs, cfg.reserved, cfg.out_size = kind, copy_threads, ring_jobs, 0, \
+            out_size
+        cfg.params = ctypes.cast(ctypes.pointer(p), ctypes.c_void_p) if p is not None else None
+        wall = _u64()
+        st = load().crystal_stream_staged(self.handle, ptrs, sizes.ctypes.data, n, ctypes.byref(cfg),
+                                          outs.ctypes.data if outs is not None else None, stride,
+                                          res.ctypes.data, ctypes.byref(wall))
+        del arrs
+        return st, res, wall.value, outs
+
+    def set_geometry(self, size_class: int, g: Optional[crystal_geometry]) -> None:
+        """crystal_set_geometry (size_class -1: every class; g None: defaults)."""
+        check(load().crystal_set_geometry(self.handle, size_class, ctypes.byref(g) if g is not None else None),
+              "crystal_set_geometry")
+
+    def get_geometry(self, size_class: int) -> crystal_geometry:
+        g = crystal_geometry()
+        check(load().crystal_get_geometry(self.handle, size_class, ctypes.byref(g)), "crystal_get_geometry")
+        return g
+
+    def config(self) -> crystal_config:
+        c = crystal_config()
+        check(load().crystal_get_config(self.handle, ctypes.byref(c)), "crystal_get_config")
+        return c
 
     def stats(self) -> crystal_stats:
         s = crystal_stats()
@@ -516,3 +603,16 @@ class DeviceBatch:
         """Each unit's output bytes, in the caller's order."""
         host = self.d_out.cpu().numpy()
         return [host[self.out_off[i]:self.out_off[i] + self.out_size[i]].tobytes() for i in range(len(self.sizes))]
+
+
+def alu_probe(kind: int, ctas_per_sm: int, iters: int, sink, stream=None) -> int:
+    """Launch crystal_alu_probe on ``stream`` (a torch stream; default: the
+    current one); ``sink`` is a CUDA tensor of at least 4 bytes.  Returns the
+    work of the launch (windows or instructions)."""
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    w = _u64()
+    check(load().crystal_alu_probe(kind, ctas_per_sm, iters, 0x9E3779B9, sink.data_ptr(), s.cuda_stream,
+                                   ctypes.byref(w)), "crystal_alu_probe")
+    return int(w.value)

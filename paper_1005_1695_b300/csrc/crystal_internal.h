@@ -13,33 +13,29 @@ namespace crystal {
 
 extern std::atomic<uint64_t> g_kernel_launches;
 
-// Kernel launchers on a device-resident batch (kernels.cu).
-int launch_direct_segments(crystal_batch* b, cudaStream_t s);
-int launch_direct_outer(crystal_batch* b, cudaStream_t s);
-int launch_sliding_windows(crystal_batch* b, cudaStream_t s);
-int launch_sliding_chunks(crystal_batch* b, cudaStream_t s);
-int launch_sliding_digests(crystal_batch* b, cudaStream_t s);  // two kernels
+// Grid and CTA shape of each kernel of a batch (kernels.cu): resolved from a
+// crystal_geometry against the kernels' occupancy on the current device.
+struct LaunchGeom {
+    int sms = 0;
+    int seg_threads = 128;  // K1 threads per CTA: 64, 128 or 256
+    int seg_per_sm = 0, seg_blocks = 0, seg_sha1_blocks = 0;
+    int win20_wide = 0;  // 1: the 64-register instance of the w = 20 MD5 window kernel
+    int win_per_sm = 0, win20_blocks = 0, win_blocks = 0, win_sha1_blocks = 0;
+    int digest_per_sm = 0, digest_blocks = 0;
+    int outer_blocks = 0, unit_blocks = 0;
+};
+int make_geometry(const crystal_geometry* in, LaunchGeom* out);  // EINVAL / EDEVICE
+void describe_geometry(const LaunchGeom& g, crystal_geometry* out);
+
+// Kernel launchers on a device-resident batch (kernels.cu); geom NULL: the
+// device's default geometry.
+int launch_direct_segments(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom = nullptr);
+int launch_direct_outer(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom = nullptr);
+int launch_sliding_windows(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom = nullptr);
+int launch_sliding_chunks(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom = nullptr);
+int launch_sliding_digests(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom = nullptr);  // two kernels
 int launch_nop(cudaStream_t s);                                 // the dummy kernel
 
-// Copies made by the SMs instead of the DMA engines (runtime.cu decides which):
-// piece i moves n bytes from src to dst, either address may be mapped pinned
-// host memory.  The table lives in device memory; chunks of kCopyChunk bytes
-// of every piece are spread over the CTAs of one launch.
-constexpr uint64_t kCopyChunk = 16384;
-struct CopyPiece {
-    uint64_t src, dst, n;
-    uint64_t first_chunk;  // chunks of the pieces before this one
-};
-struct CopyTable {
-    uint32_t n_pieces;
-    uint32_t reserved;
-    uint64_t n_chunks;  // chunks of all pieces
-    CopyPiece piece[1];  // n_pieces used (the table is allocated for the slot's maximum)
-};
-inline uint64_t copy_table_bytes(uint32_t max_pieces) {
-    return 16 + 32ull * (max_pieces ? max_pieces : 1);
-}
-int launch_copy_pieces(const CopyTable* table, cudaStream_t s);
 // The batch descriptor fetched by the GPU from mapped pinned memory (bytes a
 // multiple of 16), and its status word posted back to mapped pinned memory:
 // no DMA transfer for either.
@@ -66,4 +62,4 @@ inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) & ~(a - 1)
 
 static_assert(sizeof(crystal_unit) == 64, "unit record is 64 bytes");
 static_assert(sizeof(crystal_batch) == 64, "batch header is 64 bytes");
-static_assert(sizeof(crystal::CopyPiece) == 32 && offsetof(crystal::CopyTable, piece) == 16, "copy table layout");
+

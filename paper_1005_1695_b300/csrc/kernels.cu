@@ -45,12 +45,10 @@ static_assert(kWinPerThread * kWinThreads == kTile && kWinPerThread <= 32, "tile
 // word reads.
 constexpr int kStageWords = 4 * ((kTile + 69 + 15) / 16) + 4;
 
-constexpr int kSegThreads = 128;
 constexpr int kChunkThreads = 512;
 constexpr int kDigestThreads = 256;
 constexpr int kChunkSegThreads = 128;  // K5a: 5 CTAs per SM at <= 102 registers
 constexpr int kScanThreads = 1024;
-constexpr int kCopyThreads = 256;
 
 constexpr uint32_t kDevBadRecord = 1u;
 
@@ -111,9 +109,11 @@ __device__ __forceinline__ uint64_t num_segments(uint64_t n, uint32_t S) {
 // ---- K1: segment digests of direct units ------------------------------------
 
 // One instance per hash: MD5 units are [0, direct_segments_md5) of the
-// segment space (the planner puts them first), SHA-1 units the rest.
-template <class H>
-__global__ void __launch_bounds__(kSegThreads, 5) k_direct_segments(crystal_batch* B, uint32_t one) {
+// segment space (the planner puts them first), SHA-1 units the rest.  NT
+// threads per CTA (64, 128 or 256: a launch-geometry choice), compiled for
+// 640 resident threads per SM at least.
+template <class H, int NT>
+__global__ void __launch_bounds__(NT, 640 / NT) k_direct_segments(crystal_batch* B, uint32_t one) {
     const uint32_t nd = B->n_direct;
     const bool sha = H::kWords == 5;
     const uint64_t lo = sha ? B->direct_segments_md5 : 0;
@@ -721,102 +721,6 @@ __global__ void __launch_bounds__(kDigestThreads) k_chunk_outer(crystal_batch* B
     }
 }
 
-// ---- SM copies of small pieces -------------------------------------------------
-
-// Copy chunk `lc` of piece P (bytes [lc * kCopyChunk, +kCopyChunk) of it) with
-// 16-byte accesses when the destination is 16-byte aligned (every buffer the
-// runtime hands out is): each lane loads the aligned source vector at its
-// position, takes the next one from its neighbour lane (or loads it, for the
-// last lane of the last round), and shifts the pair by the source's
-// misalignment.  A source vector is loaded only if it holds a byte of the
-// piece, so no access leaves the pages of the source range.  The last,
-// partial destination vector is written byte by byte.
-__device__ __forceinline__ uint4 load16_if(const uint8_t* p, bool ok) {
-    return ok ? *reinterpret_cast<const uint4*>(p) : make_uint4(0, 0, 0, 0);
-}
-
-__device__ __forceinline__ void copy_chunk_aligned_dst(const CopyPiece& P, uint64_t lc) {
-    constexpr int kRounds = 4;  // vectors per lane per warp pass
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-    const uint64_t src = P.src, n = P.n;
-    const uint32_t sh = (uint32_t)(src & 15);
-    const uint32_t q = sh >> 2, bs = (sh & 3) * 8;
-    const uint8_t* s0 = reinterpret_cast<const uint8_t*>(src - sh);
-    uint8_t* d = reinterpret_cast<uint8_t*>(P.dst);
-    const uint64_t v_lo = lc * (kCopyChunk / 16);
-    const uint64_t v_hi = min(v_lo + kCopyChunk / 16, (n + 15) / 16);  // destination vectors of this chunk
-    const uint64_t src_last = sh + n - 1;  // offset from s0 of the piece's last byte
-    for (uint64_t vb = v_lo + (uint64_t)warp * 32 * kRounds; vb < v_hi; vb += (uint64_t)warps * 32 * kRounds) {
-        // source vector u holds bytes [16 u, 16 u + 16) from s0; destination
-        // vector v needs source vectors v and v + 1
-        uint4 a[kRounds];
-#pragma unroll
-        for (int r = 0; r < kRounds; ++r) {
-            const uint64_t u = vb + r * 32 + lane;
-            a[r] = load16_if(s0 + 16 * u, 16 * u <= src_last);
-        }
-        const uint64_t u_next = vb + kRounds * 32;
-        const uint4 tail = load16_if(s0 + 16 * u_next, lane == 31 && sh && 16 * u_next <= src_last);
-#pragma unroll
-        for (int r = 0; r < kRounds; ++r) {
-            // lane l reads lane l + 1's vector; lane 31 reads lane 0's vector
-            // of the next round, so lane 0 hands that one out
-            const uint4 give = (lane == 0 && r + 1 < kRounds) ? a[r + 1] : a[r];
-            const uint32_t from = (lane + 1) & 31;
-            uint4 b;
-            b.x = __shfl_sync(0xffffffffu, give.x, from);
-            b.y = __shfl_sync(0xffffffffu, give.y, from);
-            b.z = __shfl_sync(0xffffffffu, give.z, from);
-            b.w = __shfl_sync(0xffffffffu, give.w, from);
-            if (lane == 31 && r + 1 == kRounds) b = tail;
-            const uint64_t v = vb + r * 32 + lane;
-            if (v >= v_hi) continue;
-            const uint32_t x[8] = {a[r].x, a[r].y, a[r].z, a[r].w, b.x, b.y, b.z, b.w};
-            uint32_t y1[7];
-#pragma unroll
-            for (int k = 0; k < 7; ++k) y1[k] = (q & 1) ? x[k + 1] : x[k];
-            uint32_t y[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) y[k] = (q & 2) ? y1[k + 2] : y1[k];
-            const uint4 o = make_uint4(__funnelshift_r(y[0], y[1], bs), __funnelshift_r(y[1], y[2], bs),
-                                       __funnelshift_r(y[2], y[3], bs), __funnelshift_r(y[3], y[4], bs));
-            if (16 * v + 16 <= n) {
-                *reinterpret_cast<uint4*>(d + 16 * v) = o;
-            } else {
-                for (uint64_t i = 16 * v; i < n; ++i) {
-                    const uint32_t k = (uint32_t)(i >> 2) & 3;
-                    const uint32_t wd = k == 0 ? o.x : k == 1 ? o.y : k == 2 ? o.z : o.w;
-                    d[i] = (uint8_t)(wd >> (8 * (i & 3)));
-                }
-            }
-        }
-    }
-}
-
-// One launch copies every piece of the table; CTAs take chunks in turn.
-__global__ void __launch_bounds__(kCopyThreads) k_copy_pieces(const CopyTable* T) {
-    const uint32_t np = T->n_pieces;
-    const uint64_t chunks = T->n_chunks;
-    for (uint64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
-        uint32_t lo = 0, hi = np;  // last piece with first_chunk <= c
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (T->piece[mid].first_chunk <= c) lo = mid; else hi = mid;
-        }
-        const CopyPiece P = T->piece[lo];
-        const uint64_t lc = c - P.first_chunk;
-        if ((P.dst & 15) == 0) {
-            copy_chunk_aligned_dst(P, lc);
-        } else {
-            const uint8_t* s = reinterpret_cast<const uint8_t*>(P.src);
-            uint8_t* d = reinterpret_cast<uint8_t*>(P.dst);
-            const uint64_t b1 = min(P.n, (lc + 1) * kCopyChunk);
-            for (uint64_t i = lc * kCopyChunk + threadIdx.x; i < b1; i += blockDim.x) d[i] = s[i];
-        }
-    }
-    __threadfence_system();  // host-side destinations complete before the stream moves on
-}
-
 // ---- batch descriptor in, status out, without DMA ------------------------------
 
 __global__ void __launch_bounds__(256) k_fetch_descriptor(const uint4* __restrict__ src, uint4* __restrict__ dst,
@@ -846,26 +750,116 @@ __global__ void k_post_status(const crystal_batch* d, uint32_t* host_status) {
 
 __global__ void k_nop() {}
 
+// ---- integer-pipe microbenchmarks (crystal_alu_probe) --------------------------
+//
+// Register-resident loops that measure what the hashing kernels are bound by:
+// the window hash itself with no memory traffic or bookkeeping (kinds MD5 and
+// SHA-1: eight 20-byte windows per thread per iteration, their message words
+// taken from a 12-word ring of registers the way the window kernel shares
+// them), and single-instruction chains that load one pipe (LOP3, funnel shift,
+// three-input add, integer multiply-add), or two alternately.  Eight
+// independent chains per thread keep every scheduler supplied.  The result is
+// written only if it equals `magic`, so no work can be dropped.
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+
+template <class H>
+__device__ __forceinline__ uint32_t probe_windows(uint32_t (&M)[12], uint32_t one) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t X[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) X[k] = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) X[k] = M[j + k];
+        X[5] = 0x80u;
+        X[14] = 8u * 20;
+        acc ^= window_first_word<H>(X, 20u, one);
+    }
+    return acc;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kProbeThreads) k_alu_probe(uint32_t iters, uint32_t one, uint32_t magic,
+                                                             uint32_t* sink) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    if constexpr (KIND == CRYSTAL_PROBE_MD5_WINDOWS || KIND == CRYSTAL_PROBE_SHA1_WINDOWS) {
+        uint32_t M[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) M[k] = tid * 0x9E3779B9u + (uint32_t)k * 0x85EBCA6Bu;
+        for (uint32_t it = 0; it < iters; ++it) {
+            const uint32_t a = KIND == CRYSTAL_PROBE_MD5_WINDOWS ? probe_windows<MD5Hash>(M, one)
+                                                                : probe_windows<SHA1Hash>(M, one);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) M[k] += a;
+            acc ^= a;
+        }
+    } else {
+        uint32_t x[kProbeChains];
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) x[c] = tid + (uint32_t)c * 0x01000193u;
+        const uint32_t y = tid ^ 0x5bd1e995u, z = tid * 3u + 1u;
+        for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+#pragma unroll
+                for (int c = 0; c < kProbeChains; ++c) {
+                    uint32_t v = x[c];
+                    if constexpr (KIND == CRYSTAL_PROBE_LOP3) {
+                        asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(v) : "r"(y), "r"(z));
+                    } else if constexpr (KIND == CRYSTAL_PROBE_SHF) {
+                        asm volatile("shf.l.wrap.b32 %0, %0, %0, 7;" : "+r"(v));
+                    } else if constexpr (KIND == CRYSTAL_PROBE_IADD3) {
+                        asm volatile("{\n\t.reg .u32 t;\n\tadd.u32 t, %0, %1;\n\tadd.u32 %0, t, %2;\n\t}"
+                                     : "+r"(v) : "r"(y), "r"(z));
+                    } else if constexpr (KIND == CRYSTAL_PROBE_IMAD) {
+                        asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(v) : "r"(one), "r"(z));
+                    } else {  // CRYSTAL_PROBE_LOP3_IMAD: one of each, alternately
+                        if (r & 1) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(v) : "r"(one), "r"(z));
+                        else asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(v) : "r"(y), "r"(z));
+                    }
+                    x[c] = v;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) acc ^= x[c];
+    }
+    if (acc == magic) sink[0] = acc;
+}
+
 // ---- launch geometry -----------------------------------------------------------
 
-// The three window-kernel instances (SHA-1 needs more registers for its
-// 16-word schedule: four CTAs per SM).
+// The window-kernel instances (SHA-1 needs more registers for its 16-word
+// schedule: four CTAs per SM).  The w = 20 MD5 instance also exists at a
+// 64-register budget (four CTAs per SM), a launch-geometry choice.
 constexpr auto kWin20 = k_sliding_windows<20, MD5Hash, CRYSTAL_WIN_MIN_BLOCKS>;
+constexpr auto kWin20Wide = k_sliding_windows<20, MD5Hash, 4>;
 constexpr auto kWinAny = k_sliding_windows<0, MD5Hash, CRYSTAL_WIN_MIN_BLOCKS>;
 #ifndef CRYSTAL_SHA1_WIN_MIN_BLOCKS
 #define CRYSTAL_SHA1_WIN_MIN_BLOCKS 4
 #endif
 constexpr auto kWinSha1 = k_sliding_windows<0, SHA1Hash, CRYSTAL_SHA1_WIN_MIN_BLOCKS>;
 
-struct Geometry {
+template <class H>
+const void* seg_kernel(int threads) {
+    return threads == 64 ? (const void*)k_direct_segments<H, 64>
+                         : threads == 256 ? (const void*)k_direct_segments<H, 256> : (const void*)k_direct_segments<H, 128>;
+}
+
+// Resident CTAs per SM of each kernel at each choice, per device.
+struct Occupancy {
     int sms = 0;
-    int seg_blocks = 0, seg_sha1_blocks = 0, outer_blocks = 0, win20_blocks = 0, win_blocks = 0, win_sha1_blocks = 0, unit_blocks = 0,
-        digest_blocks = 0;
+    int seg[3] = {}, seg_sha1[3] = {};  // 64, 128, 256 threads
+    int win20 = 0, win20_wide = 0, win = 0, win_sha1 = 0, digest = 0;
 };
 
 constexpr int kMaxDevices = 64;
-Geometry g_geom[kMaxDevices];
-std::once_flag g_geom_once[kMaxDevices];
+Occupancy g_occ[kMaxDevices];
+std::once_flag g_occ_once[kMaxDevices];
 
 int resident(const void* fn, int threads) {
     int occ = 0;
@@ -873,23 +867,44 @@ int resident(const void* fn, int threads) {
     return occ > 0 ? occ : 1;
 }
 
-const Geometry* geometry() {
+int seg_index(int threads) { return threads == 64 ? 0 : threads == 256 ? 2 : 1; }
+
+const Occupancy* occupancy() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::call_once(g_geom_once[dev], [dev] {
-        Geometry g;
-        cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev);
-        g.seg_blocks = g.sms * resident((const void*)k_direct_segments<MD5Hash>, kSegThreads);
-        g.seg_sha1_blocks = g.sms * resident((const void*)k_direct_segments<SHA1Hash>, kSegThreads);
-        g.win20_blocks = g.sms * resident((const void*)kWin20, kWinThreads);
-        g.win_blocks = g.sms * resident((const void*)kWinAny, kWinThreads);
-        g.win_sha1_blocks = g.sms * resident((const void*)kWinSha1, kWinThreads);
-        g.digest_blocks = g.sms * resident((const void*)k_chunk_segments, kChunkSegThreads);
-        g.outer_blocks = g.sms * 2;
-        g.unit_blocks = g.sms * 2;
-        g_geom[dev] = g;
+    std::call_once(g_occ_once[dev], [dev] {
+        Occupancy o;
+        cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int t : {64, 128, 256}) {
+            o.seg[seg_index(t)] = resident(seg_kernel<MD5Hash>(t), t);
+            o.seg_sha1[seg_index(t)] = resident(seg_kernel<SHA1Hash>(t), t);
+        }
+        o.win20 = resident((const void*)kWin20, kWinThreads);
+        o.win20_wide = resident((const void*)kWin20Wide, kWinThreads);
+        o.win = resident((const void*)kWinAny, kWinThreads);
+        o.win_sha1 = resident((const void*)kWinSha1, kWinThreads);
+        o.digest = resident((const void*)k_chunk_segments, kChunkSegThreads);
+        g_occ[dev] = o;
     });
-    return g_geom[dev].sms > 0 ? &g_geom[dev] : nullptr;
+    return g_occ[dev].sms > 0 ? &g_occ[dev] : nullptr;
+}
+
+// CTAs per SM: the request (0 = as many as fit), never more than fit.
+int per_sm(uint32_t want, int fit) { return want == 0 || (int)want > fit ? fit : (int)want; }
+
+LaunchGeom g_default[kMaxDevices];
+std::once_flag g_default_once[kMaxDevices];
+
+const LaunchGeom* default_geometry() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::call_once(g_default_once[dev], [] {
+        int d = 0;
+        cudaGetDevice(&d);
+        crystal_geometry zero{};
+        make_geometry(&zero, &g_default[d]);
+    });
+    return g_default[dev].sms > 0 ? &g_default[dev] : nullptr;
 }
 
 // Passed to every hashing kernel as its `one` argument (see md5::add_on_fma).
@@ -901,7 +916,55 @@ int launched(int kernels) {
     return CRYSTAL_OK;
 }
 
+const LaunchGeom* resolve(const LaunchGeom* g) { return g ? g : default_geometry(); }
+
+template <class H>
+void launch_seg(const LaunchGeom* g, int blocks, crystal_batch* b, cudaStream_t s) {
+    switch (g->seg_threads) {
+        case 64: k_direct_segments<H, 64><<<blocks, 64, 0, s>>>(b, g_one); break;
+        case 256: k_direct_segments<H, 256><<<blocks, 256, 0, s>>>(b, g_one); break;
+        default: k_direct_segments<H, 128><<<blocks, 128, 0, s>>>(b, g_one); break;
+    }
+}
+
 }  // namespace
+
+int make_geometry(const crystal_geometry* in, LaunchGeom* out) {
+    if (!in || !out) return CRYSTAL_EINVAL;
+    if (in->reserved) return CRYSTAL_EINVAL;
+    const int threads = in->seg_threads ? (int)in->seg_threads : 128;
+    if (threads != 64 && threads != 128 && threads != 256) return CRYSTAL_EINVAL;
+    if (in->win_registers && in->win_registers != 32 && in->win_registers != 64) return CRYSTAL_EINVAL;
+    if (in->seg_ctas_per_sm > 64 || in->win_ctas_per_sm > 64 || in->digest_ctas_per_sm > 64) return CRYSTAL_EINVAL;
+    const Occupancy* o = occupancy();
+    if (!o) return CRYSTAL_EDEVICE;
+    LaunchGeom g;
+    g.sms = o->sms;
+    g.seg_threads = threads;
+    g.seg_per_sm = per_sm(in->seg_ctas_per_sm, o->seg[seg_index(threads)]);
+    g.seg_blocks = o->sms * g.seg_per_sm;
+    g.seg_sha1_blocks = o->sms * per_sm(in->seg_ctas_per_sm, o->seg_sha1[seg_index(threads)]);
+    g.win20_wide = in->win_registers == 64;
+    g.win_per_sm = per_sm(in->win_ctas_per_sm, g.win20_wide ? o->win20_wide : o->win20);
+    g.win20_blocks = o->sms * g.win_per_sm;
+    g.win_blocks = o->sms * per_sm(in->win_ctas_per_sm, o->win);
+    g.win_sha1_blocks = o->sms * per_sm(in->win_ctas_per_sm, o->win_sha1);
+    g.digest_per_sm = per_sm(in->digest_ctas_per_sm, o->digest);
+    g.digest_blocks = o->sms * g.digest_per_sm;
+    g.outer_blocks = o->sms * 2;
+    g.unit_blocks = o->sms * 2;
+    *out = g;
+    return CRYSTAL_OK;
+}
+
+void describe_geometry(const LaunchGeom& g, crystal_geometry* out) {
+    out->seg_threads = (uint32_t)g.seg_threads;
+    out->seg_ctas_per_sm = (uint32_t)g.seg_per_sm;
+    out->win_ctas_per_sm = (uint32_t)g.win_per_sm;
+    out->win_registers = g.win20_wide ? 64u : 32u;
+    out->digest_ctas_per_sm = (uint32_t)g.digest_per_sm;
+    out->reserved = 0;
+}
 
 int launch_nop(cudaStream_t s) {
     k_nop<<<1, 32, 0, s>>>();
@@ -920,47 +983,41 @@ int launch_post_status(const crystal_batch* d, uint32_t* host_status_dev, cudaSt
     return launched(1);
 }
 
-int launch_copy_pieces(const CopyTable* table, cudaStream_t s) {
-    const Geometry* g = geometry();
+int launch_direct_segments(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom) {
+    const LaunchGeom* g = resolve(geom);
     if (!g) return CRYSTAL_EDEVICE;
-    k_copy_pieces<<<g->sms * 4, kCopyThreads, 0, s>>>(table);
-    return launched(1);
-}
-
-int launch_direct_segments(crystal_batch* b, cudaStream_t s) {
-    const Geometry* g = geometry();
-    if (!g) return CRYSTAL_EDEVICE;
-    k_direct_segments<MD5Hash><<<g->seg_blocks, kSegThreads, 0, s>>>(b, g_one);
-    k_direct_segments<SHA1Hash><<<g->seg_sha1_blocks, kSegThreads, 0, s>>>(b, g_one);
+    launch_seg<MD5Hash>(g, g->seg_blocks, b, s);
+    launch_seg<SHA1Hash>(g, g->seg_sha1_blocks, b, s);
     return launched(2);
 }
 
-int launch_direct_outer(crystal_batch* b, cudaStream_t s) {
-    const Geometry* g = geometry();
+int launch_direct_outer(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom) {
+    const LaunchGeom* g = resolve(geom);
     if (!g) return CRYSTAL_EDEVICE;
     k_direct_outer<<<g->outer_blocks, kDigestThreads, 0, s>>>(b, g_one);
     return launched(1);
 }
 
-int launch_sliding_windows(crystal_batch* b, cudaStream_t s) {
-    const Geometry* g = geometry();
+int launch_sliding_windows(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom) {
+    const LaunchGeom* g = resolve(geom);
     if (!g) return CRYSTAL_EDEVICE;
-    kWin20<<<g->win20_blocks, kWinThreads, 0, s>>>(b, g_one);
+    if (g->win20_wide) kWin20Wide<<<g->win20_blocks, kWinThreads, 0, s>>>(b, g_one);
+    else kWin20<<<g->win20_blocks, kWinThreads, 0, s>>>(b, g_one);
     kWinAny<<<g->win_blocks, kWinThreads, 0, s>>>(b, g_one);
     kWinSha1<<<g->win_sha1_blocks, kWinThreads, 0, s>>>(b, g_one);
     return launched(3);
 }
 
-int launch_sliding_chunks(crystal_batch* b, cudaStream_t s) {
-    const Geometry* g = geometry();
+int launch_sliding_chunks(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom) {
+    const LaunchGeom* g = resolve(geom);
     if (!g) return CRYSTAL_EDEVICE;
     k_sliding_chunks<<<g->unit_blocks, kChunkThreads, 0, s>>>(b);
     k_chunk_seg_scan<<<1, kScanThreads, 0, s>>>(b);
     return launched(2);
 }
 
-int launch_sliding_digests(crystal_batch* b, cudaStream_t s) {
-    const Geometry* g = geometry();
+int launch_sliding_digests(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom) {
+    const LaunchGeom* g = resolve(geom);
     if (!g) return CRYSTAL_EDEVICE;
     k_chunk_segments<<<g->digest_blocks, kChunkSegThreads, 0, s>>>(b, g_one);
     k_chunk_outer<<<g->unit_blocks, kDigestThreads, 0, s>>>(b, g_one);
@@ -1049,18 +1106,25 @@ int crystal_md5_direct_noalloc(const void* d_in, uint64_t unit_bytes, uint32_t n
         g_noalloc_addr[dev] = g_noalloc_err[dev] == cudaSuccess ? static_cast<uint8_t*>(p) : nullptr;
     });
     if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_addr[dev]) return CRYSTAL_EDEVICE;
-    const Geometry* g = geometry();
+    const LaunchGeom* g = default_geometry();
     if (!g) return CRYSTAL_EDEVICE;
     crystal_batch* B = reinterpret_cast<crystal_batch*>(g_noalloc_addr[dev]);
     const uint64_t digests = reinterpret_cast<uint64_t>(g_noalloc_addr[dev]) + desc;
     cudaStream_t s = (cudaStream_t)stream;
     const int threads = 256;
     const int blocks = (int)((n_units + threads - 1) / threads < 1024 ? (n_units + threads - 1) / threads : 1024);
+    // a launch error left pending by earlier work on this thread is reported
+    // (and cleared) here, before anything is queued
+    if (cudaGetLastError() != cudaSuccess) return CRYSTAL_EDEVICE;
     k_noalloc_describe<<<blocks, threads, 0, s>>>(B, reinterpret_cast<uint64_t>(d_in), unit_bytes, n_units,
                                                    segment_bytes, reinterpret_cast<uint64_t>(d_digests), digests);
-    k_direct_segments<MD5Hash><<<g->seg_blocks, kSegThreads, 0, s>>>(B, g_one);
+    // the hashing kernels read the descriptor this launch writes: queue them
+    // only if it was queued
+    if (launched(1) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
+    launch_seg<MD5Hash>(g, g->seg_blocks, B, s);
+    if (launched(1) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     k_direct_outer<<<g->outer_blocks, kDigestThreads, 0, s>>>(B, g_one);
-    return launched(3);
+    return launched(1);
 }
 
 int crystal_launch_direct_segments(const crystal_batch* b, void* stream) {
@@ -1108,6 +1172,51 @@ int crystal_launch_batch(const crystal_batch* b, void* stream) {
 }
 
 uint64_t crystal_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
+
+int crystal_alu_probe(int kind, uint32_t ctas_per_sm, uint32_t iters, uint32_t magic, uint32_t* d_sink,
+                      void* stream, uint64_t* work) {
+    if (!d_sink || ctas_per_sm == 0 || ctas_per_sm > 64 || iters == 0) return CRYSTAL_EINVAL;
+    const LaunchGeom* g = default_geometry();
+    if (!g) return CRYSTAL_EDEVICE;
+    const uint32_t blocks = (uint32_t)g->sms * ctas_per_sm;
+    const uint64_t threads = (uint64_t)blocks * kProbeThreads;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t units;
+    switch (kind) {
+        case CRYSTAL_PROBE_MD5_WINDOWS:
+            k_alu_probe<CRYSTAL_PROBE_MD5_WINDOWS><<<blocks, kProbeThreads, 0, s>>>(iters, g_one, magic, d_sink);
+            units = threads * iters * 8;  // windows
+            break;
+        case CRYSTAL_PROBE_SHA1_WINDOWS:
+            k_alu_probe<CRYSTAL_PROBE_SHA1_WINDOWS><<<blocks, kProbeThreads, 0, s>>>(iters, g_one, magic, d_sink);
+            units = threads * iters * 8;
+            break;
+        case CRYSTAL_PROBE_LOP3:
+            k_alu_probe<CRYSTAL_PROBE_LOP3><<<blocks, kProbeThreads, 0, s>>>(iters, g_one, magic, d_sink);
+            units = threads * iters * 8 * kProbeChains;  // instructions (per thread)
+            break;
+        case CRYSTAL_PROBE_SHF:
+            k_alu_probe<CRYSTAL_PROBE_SHF><<<blocks, kProbeThreads, 0, s>>>(iters, g_one, magic, d_sink);
+            units = threads * iters * 8 * kProbeChains;
+            break;
+        case CRYSTAL_PROBE_IADD3:
+            k_alu_probe<CRYSTAL_PROBE_IADD3><<<blocks, kProbeThreads, 0, s>>>(iters, g_one, magic, d_sink);
+            units = threads * iters * 8 * kProbeChains;
+            break;
+        case CRYSTAL_PROBE_IMAD:
+            k_alu_probe<CRYSTAL_PROBE_IMAD><<<blocks, kProbeThreads, 0, s>>>(iters, g_one, magic, d_sink);
+            units = threads * iters * 8 * kProbeChains;
+            break;
+        case CRYSTAL_PROBE_LOP3_IMAD:
+            k_alu_probe<CRYSTAL_PROBE_LOP3_IMAD><<<blocks, kProbeThreads, 0, s>>>(iters, g_one, magic, d_sink);
+            units = threads * iters * 8 * kProbeChains;
+            break;
+        default:
+            return CRYSTAL_EINVAL;
+    }
+    if (work) *work = units;
+    return launched(1);
+}
 
 int crystal_direct_job(const void* h_in, void* d_in, uint64_t in_size, void* h_out, const void* d_out,
                        uint64_t out_size, void* stream) {

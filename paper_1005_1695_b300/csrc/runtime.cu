@@ -59,16 +59,11 @@ struct Slot {
     uint8_t* h_desc_dev = nullptr;    // its device-visible address when mapped (descriptor fetched by the GPU)
     crystal_batch* d_desc = nullptr;  // device, inside the device arena
     uint64_t d_desc_off = 0;
-    // SM copy tables (inputs, outputs), uploaded with the descriptor
-    CopyTable* h_tin = nullptr;
-    CopyTable* h_tout = nullptr;
-    const CopyTable* d_tin = nullptr;
-    const CopyTable* d_tout = nullptr;
     std::vector<crystal_task*> tasks;
     bool busy = false;
     uint64_t seq = 0;
-    // index: has_direct | has_sliding << 1 | sm copy-in << 2 | sm copy-out << 3
-    cudaGraphExec_t graph[16] = {};
+    // [size class][has_direct | has_sliding << 1]
+    cudaGraphExec_t graph[CRYSTAL_SIZE_CLASSES][4] = {};
 };
 
 thread_local const crystal_ctx* tl_callback_ctx = nullptr;
@@ -84,7 +79,6 @@ struct crystal_task {
     uint8_t* d_scratch = nullptr;
     uint8_t* d_reserved = nullptr;  // scratch reserved at create (crystal_task_create_ex)
     const uint8_t* h_in_ext = nullptr;  // caller memory bound as the input (crystal_task_bind_input)
-    uint64_t h_in_ext_dev = 0;          // its device-visible address when mapped (0: DMA only)
     bool external_input = false;        // created without its own pinned input buffer
     uint64_t h_in_off = 0, h_out_off = 0, d_in_off = 0, d_out_off = 0, d_scratch_off = 0, d_reserved_off = 0;
     uint64_t reserved_bytes = 0;
@@ -148,9 +142,9 @@ struct crystal_ctx {
     uint32_t next_slot = 0;
     uint32_t max_jobs = 64;
     uint64_t max_bytes = 32ull << 20;
-    uint64_t region_bytes = 0;  // per slot: descriptor, then the two copy tables
-    bool sm_copy = false;       // small runs copied by k_copy_pieces
+    uint64_t region_bytes = 0;  // per slot: the batch descriptor (header + max_jobs units)
     bool h_mapped = false;      // the host pool is mapped into the device's address space
+    LaunchGeom geom[CRYSTAL_SIZE_CLASSES];  // launch geometry per batch size class
     int64_t h_dev_delta = 0;    // device-visible address of a host-pool byte minus its address
 
     std::mutex mu;
@@ -167,7 +161,9 @@ struct crystal_ctx {
     std::atomic<uint64_t> n_outstanding{0};  // mirrors outstanding.size() for the idle spin
     std::atomic<uint64_t> jobs_completed{0};
     std::atomic<uint64_t> batches{0};
-    std::atomic<uint64_t> copies_dma{0}, copies_sm{0};
+    std::atomic<uint64_t> copies_dma{0};
+    std::atomic<uint64_t> issue_ns{0}, complete_ns{0};  // master thread time issuing / completing batches
+    std::atomic<uint64_t> create_ns{0}, create_calls{0}, create_eagain{0};  // crystal_task_create_ex
     uint64_t n_running_jobs = 0;
 };
 
@@ -293,27 +289,39 @@ void build_descriptor(const crystal_ctx* c, Slot& s, uint32_t* nd_out, uint32_t*
     *ns_out = k - *nd_out;
 }
 
-int launch_chain(crystal_batch* d, cudaStream_t st, bool direct, bool sliding) {
+int launch_chain(crystal_batch* d, cudaStream_t st, bool direct, bool sliding, const LaunchGeom* g) {
     int r = CRYSTAL_OK;
     if (direct) {
-        r = launch_direct_segments(d, st);
-        if (r == CRYSTAL_OK) r = launch_direct_outer(d, st);
+        r = launch_direct_segments(d, st, g);
+        if (r == CRYSTAL_OK) r = launch_direct_outer(d, st, g);
     }
     if (sliding && r == CRYSTAL_OK) {
-        r = launch_sliding_windows(d, st);
-        if (r == CRYSTAL_OK) r = launch_sliding_chunks(d, st);
-        if (r == CRYSTAL_OK) r = launch_sliding_digests(d, st);
+        r = launch_sliding_windows(d, st, g);
+        if (r == CRYSTAL_OK) r = launch_sliding_chunks(d, st, g);
+        if (r == CRYSTAL_OK) r = launch_sliding_digests(d, st, g);
     }
     return r;
 }
 
+// Size class of a batch: the mean input bytes of its hashing jobs.
+int size_class(const Slot& s) {
+    uint64_t bytes = 0, n = 0;
+    for (const crystal_task* t : s.tasks) {
+        if (t->kind == CRYSTAL_KIND_NOP) continue;
+        bytes += t->in_size;
+        ++n;
+    }
+    const uint64_t mean = n ? bytes / n : 0;
+    return mean < (64u << 10) ? 0 : mean < (1u << 20) ? 1 : 2;
+}
+
 int kernels_in_chain(bool direct, bool sliding) { return (direct ? 3 : 0) + (sliding ? 7 : 0); }
 
-// Descriptor in, SM copy-in, kernel chain, SM copy-out, status back: the
-// device side of one batch.  With the slot's descriptor region mapped, the GPU
-// fetches the descriptor and posts the status itself (two small kernels)
-// instead of two DMA transfers of a few microseconds each.
-int batch_sequence(crystal_ctx* c, Slot& s, bool direct, bool sliding, bool copy_in, bool copy_out) {
+// Descriptor in, kernel chain, status back: the device side of one batch.
+// With the slot's descriptor region mapped, the GPU fetches the descriptor
+// and posts the status itself (two small kernels) instead of two DMA
+// transfers of a few microseconds each.
+int batch_sequence(crystal_ctx* c, Slot& s, bool direct, bool sliding, const LaunchGeom* g) {
     cudaStream_t st = s.stream;
     int r = CRYSTAL_OK;
     if (s.h_desc_dev) {
@@ -321,9 +329,7 @@ int batch_sequence(crystal_ctx* c, Slot& s, bool direct, bool sliding, bool copy
     } else if (cudaMemcpyAsync(s.d_desc, s.h_desc, c->region_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
         r = CRYSTAL_EDEVICE;
     }
-    if (r == CRYSTAL_OK && copy_in) r = launch_copy_pieces(s.d_tin, st);
-    if (r == CRYSTAL_OK) r = launch_chain(s.d_desc, st, direct, sliding);
-    if (r == CRYSTAL_OK && copy_out) r = launch_copy_pieces(s.d_tout, st);
+    if (r == CRYSTAL_OK) r = launch_chain(s.d_desc, st, direct, sliding, g);
     if (r != CRYSTAL_OK) return r;
     if (s.h_desc_dev) {
         const uint64_t status_off = offsetof(crystal_batch, status);
@@ -335,12 +341,12 @@ int batch_sequence(crystal_ctx* c, Slot& s, bool direct, bool sliding, bool copy
 }
 
 // Capture batch_sequence of one slot as a graph.
-int capture_graph(crystal_ctx* c, Slot& s, int variant) {
-    const bool direct = variant & 1, sliding = variant & 2, copy_in = variant & 4, copy_out = variant & 8;
+int capture_graph(crystal_ctx* c, Slot& s, int cls, int variant) {
+    const bool direct = variant & 1, sliding = variant & 2;
     const uint64_t before = g_kernel_launches.load();
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CRYSTAL_EDEVICE;
-    int r = batch_sequence(c, s, direct, sliding, copy_in, copy_out);
+    int r = batch_sequence(c, s, direct, sliding, &c->geom[cls]);
     cudaError_t e = cudaStreamEndCapture(s.stream, &g);
     g_kernel_launches.store(before);
     if (r != CRYSTAL_OK || e != cudaSuccess) {
@@ -348,42 +354,32 @@ int capture_graph(crystal_ctx* c, Slot& s, int variant) {
         cudaGetLastError();
         return CRYSTAL_EDEVICE;
     }
-    e = cudaGraphInstantiate(&s.graph[variant], g, 0);
+    e = cudaGraphInstantiate(&s.graph[cls][variant], g, 0);
     cudaGraphDestroy(g);
     return e == cudaSuccess ? CRYSTAL_OK : CRYSTAL_EDEVICE;
 }
 
-// One copy of a batch: host range <-> device range, n bytes.  host_dev is the
-// device-visible address of the host range (0: not mapped, DMA only).
+// One copy of a batch: host range <-> device range, n bytes.
 struct Run {
     const uint8_t* host;
-    uint64_t host_dev;
     uint8_t* dev;
     uint64_t n;
-    bool by_sm;
 };
-
-// With CRYSTAL_FLAG_SM_COPY, runs below this size are copied by the SMs when
-// both ends are device-visible: a DMA transfer costs a few microseconds
-// whatever its size (about 3.7 us on B300, so 256 KiB moves at 30 GB/s and
-// 1 MiB at 46 GB/s), while k_copy_pieces moves scattered pieces of any size at
-// about 48 GB/s when it finds free SMs.
-constexpr uint64_t kSmCopyMax = 1ull << 20;
 
 // Copies of several jobs merged into one when their host ranges and their
 // device ranges are both contiguous blocks at the same host-to-device offset
-// (fewer, larger transfers).  A job's block is its whole allocation, so a
-// merged copy only ever covers memory of the merged jobs.
+// (fewer, larger transfers: a DMA transfer costs a few microseconds whatever
+// its size -- about 3.7 us on B300, so 256 KiB moves at 30 GB/s and 4 MiB at
+// 53).  A job's block is its whole allocation, so a merged copy only ever
+// covers memory of the merged jobs.
 class RunBuilder {
   public:
     explicit RunBuilder(std::vector<Run>* out) : out_(out) {}
     // host/dev: the job's buffers; used: bytes that matter; block: allocated bytes
-    void add(const uint8_t* host, uint64_t host_dev, uint8_t* dev, uint64_t used, uint64_t block, bool mergeable) {
+    void add(const uint8_t* host, uint8_t* dev, uint64_t used, uint64_t block, bool mergeable) {
         if (!used) return;
         const int64_t delta = (int64_t)((uint64_t)dev - (uint64_t)host);
-        const bool mapped = host_dev != 0;
-        const int64_t hdelta = mapped ? (int64_t)(host_dev - (uint64_t)host) : 0;
-        if (open_ && mergeable && delta == delta_ && mapped == mapped_ && hdelta == hdelta_) {
+        if (open_ && mergeable && delta == delta_) {
             if (host == hi_) {  // just above the run
                 hi_ = host + block;
                 end_ = host + used;
@@ -396,7 +392,7 @@ class RunBuilder {
         }
         flush();
         if (!mergeable) {
-            out_->push_back(Run{host, host_dev, dev, used, false});
+            out_->push_back(Run{host, dev, used});
             return;
         }
         open_ = true;
@@ -404,14 +400,11 @@ class RunBuilder {
         hi_ = host + block;
         end_ = host + used;
         delta_ = delta;
-        mapped_ = mapped;
-        hdelta_ = hdelta;
     }
     void flush() {
         if (!open_) return;
         open_ = false;
-        out_->push_back(Run{lo_, mapped_ ? (uint64_t)lo_ + (uint64_t)hdelta_ : 0,
-                            reinterpret_cast<uint8_t*>((uint64_t)lo_ + (uint64_t)delta_), (uint64_t)(end_ - lo_), false});
+        out_->push_back(Run{lo_, reinterpret_cast<uint8_t*>((uint64_t)lo_ + (uint64_t)delta_), (uint64_t)(end_ - lo_)});
     }
 
   private:
@@ -420,21 +413,8 @@ class RunBuilder {
     const uint8_t* lo_ = nullptr;
     const uint8_t* hi_ = nullptr;   // end of the highest block in the run
     const uint8_t* end_ = nullptr;  // end of the bytes to copy (in the highest block)
-    int64_t delta_ = 0, hdelta_ = 0;
-    bool mapped_ = false;
+    int64_t delta_ = 0;
 };
-
-// Put a run into an SM copy table if it is small and mapped; true if taken.
-bool sm_take(CopyTable* T, uint32_t cap, uint64_t src, uint64_t dst, uint64_t n) {
-    if (n >= kSmCopyMax || T->n_pieces >= cap) return false;
-    CopyPiece& p = T->piece[T->n_pieces++];
-    p.src = src;
-    p.dst = dst;
-    p.n = n;
-    p.first_chunk = T->n_chunks;
-    T->n_chunks += (n + kCopyChunk - 1) / kCopyChunk;
-    return true;
-}
 
 bool dma(const Run& r, cudaMemcpyKind kind, cudaStream_t st) {
     if (kind == cudaMemcpyHostToDevice) return cudaMemcpyAsync(r.dev, r.host, r.n, kind, st) == cudaSuccess;
@@ -447,53 +427,53 @@ int issue(crystal_ctx* c, Slot& s) {
     uint32_t nd = 0, ns = 0;
     build_descriptor(c, s, &nd, &ns);
     const bool hashing = nd + ns > 0;
-    // the copy tables ride on the descriptor upload, so only batches that
-    // upload one copy with the SMs
-    const bool sm = c->sm_copy && hashing;
+    // The batch's copies in host-address order, so that the buffers of jobs
+    // that sit next to each other in the pools merge into one transfer
+    // whatever order the jobs were submitted in (the units' order in the
+    // descriptor does not matter: every unit carries its own pointers).
     std::vector<Run> in_runs, out_runs;
     {
-        RunBuilder in(&in_runs);
+        struct Piece {
+            const uint8_t* host;
+            uint8_t* dev;
+            uint64_t used, block;
+            bool mergeable;
+        };
+        std::vector<Piece> pieces;
+        pieces.reserve(s.tasks.size());
+        auto build = [&](std::vector<Run>* runs) {
+            std::sort(pieces.begin(), pieces.end(), [](const Piece& a, const Piece& b) { return a.host < b.host; });
+            RunBuilder rb(runs);
+            for (const Piece& q : pieces) rb.add(q.host, q.dev, q.used, q.block, q.mergeable);
+            rb.flush();
+            pieces.clear();
+        };
         for (crystal_task* t : s.tasks) {
             const bool own = !t->h_in_ext;
-            const uint8_t* src = own ? t->h_in : t->h_in_ext;
-            const uint64_t src_dev = !sm ? 0 : own ? (uint64_t)t->h_in + (uint64_t)c->h_dev_delta : t->h_in_ext_dev;
-            in.add(src, src_dev, t->d_in, t->in_size, align_up(t->in_cap ? t->in_cap : 1, 256), own && c->pooled);
+            pieces.push_back(Piece{own ? t->h_in : t->h_in_ext, t->d_in, t->in_size,
+                                   align_up(t->in_cap ? t->in_cap : 1, 256), own && c->pooled});
         }
-        in.flush();
-        RunBuilder out(&out_runs);
+        build(&in_runs);
         for (crystal_task* t : s.tasks) {
             if (digest_in_place(c, t)) continue;  // already in h_out when the batch completes
-            const uint64_t dst_dev = sm ? (uint64_t)t->h_out + (uint64_t)c->h_dev_delta : 0;
-            out.add(t->h_out, dst_dev, t->d_out, t->out_size, align_up(t->out_cap ? t->out_cap : 1, 256), c->pooled);
+            pieces.push_back(Piece{t->h_out, t->d_out, t->out_size, align_up(t->out_cap ? t->out_cap : 1, 256),
+                                   c->pooled});
         }
-        out.flush();
+        build(&out_runs);
     }
-    if (sm) {
-        s.h_tin->n_pieces = s.h_tout->n_pieces = 0;
-        s.h_tin->n_chunks = s.h_tout->n_chunks = 0;
-        for (Run& r : in_runs) r.by_sm = r.host_dev && sm_take(s.h_tin, c->max_jobs, r.host_dev, (uint64_t)r.dev, r.n);
-        for (Run& r : out_runs) r.by_sm = r.host_dev && sm_take(s.h_tout, c->max_jobs, (uint64_t)r.dev, r.host_dev, r.n);
-    }
-    uint64_t n_sm = 0, n_dma = 0;
-    for (const Run& r : in_runs) {
-        if (r.by_sm) {
-            ++n_sm;
-        } else {
-            ++n_dma;
-            if (!dma(r, cudaMemcpyHostToDevice, st)) return CRYSTAL_EDEVICE;
-        }
-    }
+    for (const Run& r : in_runs)
+        if (!dma(r, cudaMemcpyHostToDevice, st)) return CRYSTAL_EDEVICE;
     if (hashing) {
         if (crystal_batch_plan(s.h_desc, nd, ns) != CRYSTAL_OK) return CRYSTAL_EINVAL;
-        const bool copy_in = sm && s.h_tin->n_pieces, copy_out = sm && s.h_tout->n_pieces;
-        const int variant = (nd ? 1 : 0) | (ns ? 2 : 0) | (copy_in ? 4 : 0) | (copy_out ? 8 : 0);
+        const int variant = (nd ? 1 : 0) | (ns ? 2 : 0);
+        const int cls = size_class(s);
         if (c->cfg.flags & CRYSTAL_FLAG_GRAPHS) {
-            if (!s.graph[variant] && capture_graph(c, s, variant) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
-            if (cudaGraphLaunch(s.graph[variant], st) != cudaSuccess) return CRYSTAL_EDEVICE;
-            g_kernel_launches.fetch_add(
-                (uint64_t)(kernels_in_chain(nd, ns) + copy_in + copy_out + (s.h_desc_dev ? 2 : 0)));
+            cudaGraphExec_t& ge = s.graph[cls][variant];
+            if (!ge && capture_graph(c, s, cls, variant) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
+            if (cudaGraphLaunch(ge, st) != cudaSuccess) return CRYSTAL_EDEVICE;
+            g_kernel_launches.fetch_add((uint64_t)(kernels_in_chain(nd, ns) + (s.h_desc_dev ? 2 : 0)));
         } else {
-            const int r = batch_sequence(c, s, nd > 0, ns > 0, copy_in, copy_out);
+            const int r = batch_sequence(c, s, nd > 0, ns > 0, &c->geom[cls]);
             if (r != CRYSTAL_OK) return r;
         }
     } else {
@@ -502,16 +482,9 @@ int issue(crystal_ctx* c, Slot& s) {
         s.h_desc->status = 0;
         if (launch_nop(st) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     }
-    for (const Run& r : out_runs) {
-        if (r.by_sm) {
-            ++n_sm;
-        } else {
-            ++n_dma;
-            if (!dma(r, cudaMemcpyDeviceToHost, st)) return CRYSTAL_EDEVICE;
-        }
-    }
-    c->copies_sm.fetch_add(n_sm);
-    c->copies_dma.fetch_add(n_dma);
+    for (const Run& r : out_runs)
+        if (!dma(r, cudaMemcpyDeviceToHost, st)) return CRYSTAL_EDEVICE;
+    c->copies_dma.fetch_add(in_runs.size() + out_runs.size());
     if (cudaEventRecord(s.done, st) != cudaSuccess) return CRYSTAL_EDEVICE;
     return CRYSTAL_OK;
 }
@@ -579,57 +552,73 @@ bool take_batch(crystal_ctx* c, Slot& s) {
     return !s.tasks.empty();
 }
 
+// Cancel every outstanding job (shutdown): status ESHUTDOWN, callbacks run.
+void cancel_outstanding(crystal_ctx* c) {
+    std::vector<crystal_task*> cancel;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        cancel = c->outstanding.drain();
+        c->n_outstanding.store(0);
+        for (crystal_task* t : cancel) t->state = T_RUNNING;  // callbacks may release it
+    }
+    for (crystal_task* t : cancel) {
+        free_job_scratch(c, t);
+        t->status = CRYSTAL_ESHUTDOWN;
+        t->t_done = now_ns();
+        if (t->cb) {
+            tl_callback_ctx = c;
+            t->cb(t, t->status, t->user);
+            tl_callback_ctx = nullptr;
+        }
+        std::lock_guard<std::mutex> g(c->mu);
+        if (t->release_in_callback) {
+            c->tasks.erase(t);
+            free_task_buffers(t);
+            delete t;
+        } else {
+            t->state = T_DONE;
+        }
+    }
+    c->cv_done.notify_all();
+}
+
+// The master thread (Section 4.2).  The running list and the slots' busy
+// flags belong to this thread alone, so completion polling runs without the
+// context lock; the lock is taken only to move jobs off the outstanding
+// queue and to read the shutdown flag, so threads that create, submit and
+// release jobs are not held up by the polling.
 void master_loop(crystal_ctx* c) {
     cudaSetDevice(c->device);
     const bool sequential = c->cfg.flags & CRYSTAL_FLAG_NO_OVERLAP;
-    std::unique_lock<std::mutex> lk(c->mu);
     for (;;) {
         bool progressed = false;
         // completion: every running slot whose event has fired
         for (size_t i = 0; i < c->running.size();) {
             Slot& s = c->slots[c->running[i]];
-            cudaError_t e = cudaEventQuery(s.done);
+            const cudaError_t e = cudaEventQuery(s.done);
             if (e == cudaErrorNotReady) {
                 ++i;
                 continue;
             }
             c->running.erase(c->running.begin() + i);
-            lk.unlock();
+            const uint64_t f0 = now_ns();
             if (e != cudaSuccess) cudaGetLastError();
             finish_slot(c, s, e == cudaSuccess ? CRYSTAL_OK : CRYSTAL_EDEVICE);
-            lk.lock();
+            c->complete_ns.fetch_add(now_ns() - f0, std::memory_order_relaxed);
             progressed = true;
         }
+        bool stop;
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            stop = c->stop;
+        }
         // cancellation on shutdown
-        if (c->stop && !c->outstanding.empty()) {
-            std::vector<crystal_task*> cancel = c->outstanding.drain();
-            c->n_outstanding.store(0);
-            for (crystal_task* t : cancel) t->state = T_RUNNING;  // callbacks may release it
-            lk.unlock();
-            for (crystal_task* t : cancel) {
-                free_job_scratch(c, t);
-                t->status = CRYSTAL_ESHUTDOWN;
-                t->t_done = now_ns();
-                if (t->cb) {
-                    tl_callback_ctx = c;
-                    t->cb(t, t->status, t->user);
-                    tl_callback_ctx = nullptr;
-                }
-                std::lock_guard<std::mutex> g(c->mu);
-                if (t->release_in_callback) {
-                    c->tasks.erase(t);
-                    free_task_buffers(t);
-                    delete t;
-                } else {
-                    t->state = T_DONE;
-                }
-            }
-            c->cv_done.notify_all();
-            lk.lock();
+        if (stop && c->n_outstanding.load() > 0) {
+            cancel_outstanding(c);
             progressed = true;
         }
         // dispatch: from the outstanding queue (priority, then FIFO) into free slots
-        while (!c->outstanding.empty()) {
+        while (c->n_outstanding.load() > 0) {
             const uint32_t ns = (uint32_t)c->slots.size();
             uint32_t pick = ns;
             for (uint32_t k = 0; k < ns; ++k) {
@@ -641,14 +630,17 @@ void master_loop(crystal_ctx* c) {
             }
             if (pick == ns) break;
             Slot& s = c->slots[pick];
-            if (!take_batch(c, s)) break;
-            s.busy = true;
-            s.seq = ++c->seq;
+            {
+                std::lock_guard<std::mutex> lk(c->mu);
+                if (!take_batch(c, s)) break;
+                s.busy = true;
+                s.seq = ++c->seq;
+            }
             c->next_slot = (pick + 1) % ns;
             const uint64_t t = now_ns();
             for (crystal_task* j : s.tasks) j->t_dispatch = t;
-            lk.unlock();
             int r = issue(c, s);
+            c->issue_ns.fetch_add(now_ns() - t, std::memory_order_relaxed);
             c->batches.fetch_add(1);
             if (r != CRYSTAL_OK) {
                 cudaGetLastError();
@@ -657,35 +649,33 @@ void master_loop(crystal_ctx* c) {
             } else if (sequential) {
                 cudaEventSynchronize(s.done);
                 finish_slot(c, s, CRYSTAL_OK);
+            } else {
+                c->running.push_back(pick);
             }
-            lk.lock();
-            if (r == CRYSTAL_OK && !sequential) c->running.push_back(pick);
             progressed = true;
         }
-        if (c->stop && c->running.empty() && c->outstanding.empty()) break;
         if (progressed) continue;
         if (c->running.empty()) {
+            if (stop && c->n_outstanding.load() == 0) break;
             // idle: poll for new jobs for a short while before sleeping, so a
             // job submitted soon after is dispatched without a thread wake-up
-            lk.unlock();
             const uint64_t t0 = now_ns();
             while (c->n_outstanding.load(std::memory_order_relaxed) == 0 && now_ns() - t0 < kIdleSpinNs)
                 std::this_thread::yield();
-            lk.lock();
-            if (c->outstanding.empty() && c->running.empty() && !c->stop) c->cv_master.wait(lk);
+            std::unique_lock<std::mutex> lk(c->mu);
+            if (c->outstanding.empty() && !c->stop) c->cv_master.wait(lk);
         } else {
             // poll the running slots (Section 4.1: completion is found by polling)
-            lk.unlock();
             std::this_thread::yield();
-            lk.lock();
         }
     }
 }
 
 void destroy_ctx(crystal_ctx* c) {
     for (Slot& s : c->slots) {
-        for (auto& g : s.graph)
-            if (g) cudaGraphExecDestroy(g);
+        for (auto& per_class : s.graph)
+            for (auto& g : per_class)
+                if (g) cudaGraphExecDestroy(g);
         if (s.done) cudaEventDestroy(s.done);
         if (s.stream && s.own_stream) cudaStreamDestroy(s.stream);
         if (s.h_desc) cudaFreeHost(s.h_desc);
@@ -739,7 +729,7 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
     if (u.max_batch_bytes) cfg.max_batch_bytes = u.max_batch_bytes;
     if (cfg.n_streams < 1 || cfg.n_streams > 64 || cfg.max_batch_jobs > 65536) return CRYSTAL_EINVAL;
     if (cfg.flags & ~(uint32_t)(CRYSTAL_FLAG_NO_POOL | CRYSTAL_FLAG_NO_OVERLAP | CRYSTAL_FLAG_NO_BATCH |
-                                CRYSTAL_FLAG_GRAPHS | CRYSTAL_FLAG_SM_COPY))
+                                CRYSTAL_FLAG_GRAPHS))
         return CRYSTAL_EINVAL;
     if (cfg.device_arena && (reinterpret_cast<uint64_t>(cfg.device_arena) & 255)) return CRYSTAL_EINVAL;
     if (cudaSetDevice(cfg.device) != cudaSuccess) {
@@ -751,14 +741,22 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
     c->cfg = cfg;
     c->device = cfg.device;
     c->pooled = !(cfg.flags & CRYSTAL_FLAG_NO_POOL);
+    {
+        const crystal_geometry defaults{};
+        for (LaunchGeom& g : c->geom) {
+            if (make_geometry(&defaults, &g) != CRYSTAL_OK) {
+                delete c;
+                return CRYSTAL_EDEVICE;
+            }
+        }
+    }
     if (cfg.flags & CRYSTAL_FLAG_NO_OVERLAP) c->cfg.n_streams = 1;
     c->max_jobs = (cfg.flags & (CRYSTAL_FLAG_NO_BATCH | CRYSTAL_FLAG_NO_OVERLAP)) ? 1 : cfg.max_batch_jobs;
     c->max_bytes = cfg.max_batch_bytes;
     const uint32_t depth = (cfg.flags & CRYSTAL_FLAG_NO_OVERLAP) ? 1 : 2;  // slots per stream
     const uint32_t n_slots = (uint32_t)c->cfg.n_streams * depth;
-    // per slot: descriptor (header + max_jobs units), then the copy tables
-    const uint64_t tables_off = align_up(crystal_batch_bytes(c->max_jobs), 16);
-    const uint64_t desc_bytes = align_up(tables_off + 2 * copy_table_bytes(c->max_jobs), 256);
+    // per slot: the batch descriptor (header + max_jobs units)
+    const uint64_t desc_bytes = align_up(crystal_batch_bytes(c->max_jobs), 256);
     c->region_bytes = desc_bytes;
 
     // device arena: job buffers (pooled mode), scratch and batch descriptors
@@ -793,14 +791,13 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
             return CRYSTAL_ENOMEM;
         }
         // the pool mapped into the device's address space: kernels write direct
-        // digests into it, and SM copies read and write it
+        // digests into it
         int uva = 0;
         void* hd = nullptr;
         if (cudaDeviceGetAttribute(&uva, cudaDevAttrUnifiedAddressing, cfg.device) == cudaSuccess && uva &&
             cudaHostGetDevicePointer(&hd, h, 0) == cudaSuccess && hd) {
             c->h_mapped = true;
             c->h_dev_delta = (int64_t)((uint64_t)hd - (uint64_t)h);
-            c->sm_copy = (cfg.flags & CRYSTAL_FLAG_SM_COPY) != 0;
         }
         cudaGetLastError();
     }
@@ -838,10 +835,6 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
             return CRYSTAL_ENOMEM;
         }
         s.d_desc = (crystal_batch*)(c->d_base + s.d_desc_off);
-        s.h_tin = reinterpret_cast<CopyTable*>((uint8_t*)h + tables_off);
-        s.h_tout = reinterpret_cast<CopyTable*>((uint8_t*)h + tables_off + copy_table_bytes(c->max_jobs));
-        s.d_tin = reinterpret_cast<const CopyTable*>((uint8_t*)s.d_desc + tables_off);
-        s.d_tout = reinterpret_cast<const CopyTable*>((uint8_t*)s.d_desc + tables_off + copy_table_bytes(c->max_jobs));
     }
     try {
         c->master = std::thread(master_loop, c);
@@ -873,9 +866,29 @@ int crystal_task_create(crystal_ctx* c, uint64_t in_size, uint64_t out_size, cry
     return crystal_task_create_ex(c, in_size, out_size, 0, 0, out);
 }
 
+namespace {
+int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes, uint32_t flags,
+               crystal_task** out);
+}
+
 int crystal_task_create_ex(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes,
                            uint32_t flags, crystal_task** out) {
-    if (!c || !out) return CRYSTAL_EINVAL;
+    if (!c) return CRYSTAL_EINVAL;
+    const uint64_t t0 = now_ns();
+    const int st = create_job(c, in_size, out_size, scratch_bytes, flags, out);
+    c->create_ns.fetch_add(now_ns() - t0, std::memory_order_relaxed);
+    c->create_calls.fetch_add(1, std::memory_order_relaxed);
+    if (st == CRYSTAL_EAGAIN) c->create_eagain.fetch_add(1, std::memory_order_relaxed);
+    return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes, uint32_t flags,
+               crystal_task** out) {
+    if (!out) return CRYSTAL_EINVAL;
     if (flags & ~(uint32_t)CRYSTAL_TASK_EXTERNAL_INPUT) return CRYSTAL_EINVAL;
     *out = nullptr;
     if (in_size > c->cfg.max_in_bytes || out_size > c->cfg.max_out_bytes) return CRYSTAL_EINVAL;
@@ -909,6 +922,10 @@ int crystal_task_create_ex(crystal_ctx* c, uint64_t in_size, uint64_t out_size, 
     *out = t;
     return CRYSTAL_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 void* crystal_task_host_in(crystal_task* t) { return t ? t->h_in : nullptr; }
 void* crystal_task_host_out(crystal_task* t) { return t ? t->h_out : nullptr; }
@@ -1062,13 +1079,6 @@ int crystal_task_bind_input(crystal_task* t, const void* host, uint64_t size) {
     if (size > t->in_cap) return CRYSTAL_EINVAL;
     t->h_in_ext = static_cast<const uint8_t*>(host);
     t->in_size = size;
-    t->h_in_ext_dev = 0;
-    if (t->ctx->sm_copy) {  // mapped page-locked memory: the SMs may read it in place
-        cudaPointerAttributes a{};
-        if (cudaPointerGetAttributes(&a, host) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer)
-            t->h_in_ext_dev = (uint64_t)a.devicePointer;
-        cudaGetLastError();
-    }
     return CRYSTAL_OK;
 }
 
@@ -1200,6 +1210,44 @@ int crystal_task_timing_many(crystal_task* const* tasks, uint32_t n, uint64_t* o
     return CRYSTAL_OK;
 }
 
+int crystal_set_geometry(crystal_ctx* c, int size_class, const crystal_geometry* g) {
+    if (!c || size_class < -1 || size_class >= CRYSTAL_SIZE_CLASSES) return CRYSTAL_EINVAL;
+    const crystal_geometry defaults{};
+    cudaSetDevice(c->device);
+    LaunchGeom lg;
+    const int st = make_geometry(g ? g : &defaults, &lg);
+    if (st != CRYSTAL_OK) return st;
+    // idle: the master issues nothing (issuing needs an outstanding job), so
+    // no graph is in use or being captured while they are dropped here
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->outstanding.empty() || c->n_running_jobs) return CRYSTAL_EINVAL;
+    for (int k = 0; k < CRYSTAL_SIZE_CLASSES; ++k) {
+        if (size_class != -1 && k != size_class) continue;
+        c->geom[k] = lg;
+        for (Slot& s : c->slots)
+            for (auto& ge : s.graph[k])
+                if (ge) {
+                    cudaGraphExecDestroy(ge);
+                    ge = nullptr;
+                }
+    }
+    return CRYSTAL_OK;
+}
+
+int crystal_get_geometry(crystal_ctx* c, int size_class, crystal_geometry* out) {
+    if (!c || !out || size_class < 0 || size_class >= CRYSTAL_SIZE_CLASSES) return CRYSTAL_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    describe_geometry(c->geom[size_class], out);
+    return CRYSTAL_OK;
+}
+
+int crystal_get_config(crystal_ctx* c, crystal_config* out) {
+    if (!c || !out) return CRYSTAL_EINVAL;
+    *out = c->cfg;
+    out->max_batch_jobs = c->max_jobs;
+    return CRYSTAL_OK;
+}
+
 int crystal_get_stats(crystal_ctx* c, crystal_stats* out) {
     if (!c || !out) return CRYSTAL_EINVAL;
     std::lock_guard<std::mutex> lk(c->mu);
@@ -1212,7 +1260,11 @@ int crystal_get_stats(crystal_ctx* c, crystal_stats* out) {
     out->jobs_outstanding = c->outstanding.size();
     out->jobs_running = c->n_running_jobs;
     out->copies_dma = c->copies_dma.load();
-    out->copies_sm = c->copies_sm.load();
+    out->master_issue_ns = c->issue_ns.load();
+    out->master_complete_ns = c->complete_ns.load();
+    out->create_ns = c->create_ns.load();
+    out->create_calls = c->create_calls.load();
+    out->create_eagain = c->create_eagain.load();
     return CRYSTAL_OK;
 }
 

@@ -3,12 +3,14 @@
 // Section 2.2 of the CrystalGPU paper describes stream-processing
 // applications: data units arrive continuously and each must be processed
 // with low latency.  crystal_serve plays such a stream against a context:
-// requests arrive at their given times, are admitted in arrival order as
-// soon as the context's pools can hold their buffers and scratch (admission
-// by pool memory), have their bytes staged into the job's pinned buffer by
-// copy threads, and are submitted; the master thread batches whatever is
-// outstanding when a stream slot frees (continuous batching), so requests
-// that arrive while others run join the next batch and overlap on the GPU.
+// requests arrive at their given times, are admitted as soon as the
+// context's pools can hold their buffers and scratch (admission by pool
+// memory) -- in arrival order, except that while the oldest waiting request
+// does not fit, later ones that do fit may pass it for a bounded time --
+// have their bytes staged into the job's pinned buffer by copy threads, and
+// are submitted; the master thread batches whatever is outstanding when a
+// stream slot frees (continuous batching), so requests that arrive while
+// others run join the next batch and overlap on the GPU.
 // Completion callbacks record the times, optionally copy the result out,
 // and release the job, which frees room for the next admission.
 #include <stdint.h>
@@ -25,6 +27,11 @@
 #include "crystal.h"
 
 namespace {
+
+// A blocked oldest request may be passed for this long by default
+// (crystal_serve_config.bypass_ns), by up to this many candidates per pass.
+constexpr uint64_t kDefaultBypassNs = 2000000;
+constexpr uint32_t kBypassCandidates = 32;
 
 uint64_t mono_ns() {
     timespec ts;
@@ -49,6 +56,7 @@ struct Serve {
     uint64_t capture_bytes = 0;
     uint64_t t0 = 0;
     bool pinned_source = false;
+    uint64_t bypass_ns = 0;  // how long the oldest waiting request may be passed
     std::vector<Ticket> tickets;
 
     std::mutex mu;
@@ -75,27 +83,35 @@ struct Serve {
     }
 };
 
+// Output bytes of a finished request that carry results.  Only called for a
+// job that completed (OK or EOVERFLOW), whose header the kernels wrote; never
+// more than the job's output buffer.
 uint64_t used_bytes(int kind, uint64_t n, const uint8_t* out, uint64_t out_size) {
     const bool sha = kind == CRYSTAL_KIND_SHA1_DIRECT || kind == CRYSTAL_KIND_SHA1_SLIDING;
     const uint64_t D = sha ? 20 : 16;
     if (kind == CRYSTAL_KIND_MD5_DIRECT || kind == CRYSTAL_KIND_SHA1_DIRECT) return out_size < D ? 0 : D;
     if (kind != CRYSTAL_KIND_MD5_SLIDING && kind != CRYSTAL_KIND_SHA1_SLIDING) return out_size;
+    if (out_size < 8) return 0;
     uint32_t hdr[2];
     memcpy(hdr, out, 8);
     const uint64_t fixed = 8 + 4 * ((n + 31) / 32);
-    return (hdr[1] & 1u) ? fixed : fixed + (4 + D) * hdr[0];
+    const uint64_t used = (hdr[1] & 1u) ? fixed : fixed + (4 + D) * (uint64_t)hdr[0];
+    return used < out_size ? used : out_size;
 }
 
-// Completion callback, on the master thread.
+// Completion callback, on the master thread.  A job that failed (a device
+// or issue error, or cancellation) has no result: nothing is captured.
 void on_done(crystal_task* t, int status, void* user) {
     Ticket* tk = static_cast<Ticket*>(user);
     Serve* s = tk->s;
     const uint32_t i = tk->idx;
     const crystal_request& r = s->req[i];
     const uint8_t* out = static_cast<const uint8_t*>(crystal_task_host_out(t));
-    const uint64_t used = used_bytes(r.kind, r.size, out, r.out_size);
+    const bool has_result = status == CRYSTAL_OK || status == CRYSTAL_EOVERFLOW;
+    const uint64_t used = has_result ? used_bytes(r.kind, r.size, out, r.out_size) : 0;
     s->res[i].used_bytes = used;
-    if (r.capture_offset != UINT64_MAX && s->capture && r.capture_offset + used <= s->capture_bytes)
+    if (used && r.capture_offset != UINT64_MAX && s->capture && r.capture_offset <= s->capture_bytes &&
+        used <= s->capture_bytes - r.capture_offset)
         memcpy(s->capture + r.capture_offset, out, used);
     crystal_task_release(t);  // freed by the master once this callback returns
     s->finish(i, status);
@@ -155,6 +171,8 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
         if (cfg->copy_threads) threads = cfg->copy_threads;
         s.pinned_source = cfg->flags & CRYSTAL_SERVE_SOURCE_PINNED;
     }
+    s.bypass_ns = (cfg && (cfg->flags & CRYSTAL_SERVE_ARRIVAL_ORDER)) ? 0
+                  : (cfg && cfg->bypass_ns) ? cfg->bypass_ns : kDefaultBypassNs;
     if (threads > 64) threads = 64;
     memset(res, 0, sizeof(crystal_request_result) * n);
     s.tickets.resize(n);
@@ -166,38 +184,73 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
     std::deque<uint32_t> fifo;  // arrived, not yet admitted (arrival order)
     uint32_t next = 0;
     uint32_t admitted = 0;      // admitted or refused at admission
-    for (;;) {
-        const uint64_t now = mono_ns() - s.t0;
-        while (next < n && req[next].arrival_ns <= now) fifo.push_back(next++);
-        // admission: in arrival order, while the pools can hold the head request
-        while (!fifo.empty()) {
-            const uint32_t i = fifo.front();
-            const crystal_request& r = req[i];
-            const uint64_t scratch = crystal_scratch_bytes(r.kind, r.size, r.out_size, s.params_for(r.kind));
-            crystal_task* t = nullptr;
-            int st = crystal_task_create_ex(ctx, r.size, r.out_size, scratch,
-                                            s.pinned_source ? CRYSTAL_TASK_EXTERNAL_INPUT : 0u, &t);
-            if (st == CRYSTAL_EAGAIN) {
-                uint32_t finished;
-                {
-                    std::lock_guard<std::mutex> lk(s.mu);
-                    finished = s.finished;
-                }
-                if (finished < admitted) break;  // wait for a completion to free room
-                st = CRYSTAL_ENOMEM;             // nothing in flight: it can never fit
-            }
-            fifo.pop_front();
+    // Create request i's job; CRYSTAL_OK queues it for staging and submit.
+    auto try_admit = [&](uint32_t i) {
+        const crystal_request& r = req[i];
+        const uint64_t scratch = crystal_scratch_bytes(r.kind, r.size, r.out_size, s.params_for(r.kind));
+        crystal_task* t = nullptr;
+        const int st = crystal_task_create_ex(ctx, r.size, r.out_size, scratch,
+                                              s.pinned_source ? CRYSTAL_TASK_EXTERNAL_INPUT : 0u, &t);
+        if (st == CRYSTAL_OK) {
             ++admitted;
             res[i].admit_ns = mono_ns() - s.t0;
-            if (st != CRYSTAL_OK) {
-                s.finish(i, st);
-                continue;
-            }
             {
                 std::lock_guard<std::mutex> lk(s.mu);
                 s.work.emplace_back(i, t);
             }
             s.cv_work.notify_one();
+        }
+        return st;
+    };
+    auto refuse = [&](uint32_t i, int st) {
+        ++admitted;
+        res[i].admit_ns = mono_ns() - s.t0;
+        s.finish(i, st);
+    };
+    for (;;) {
+        const uint64_t now = mono_ns() - s.t0;
+        while (next < n && req[next].arrival_ns <= now) fifo.push_back(next++);
+        // admission: the oldest waiting request first
+        while (!fifo.empty()) {
+            const uint32_t i = fifo.front();
+            const int st = try_admit(i);
+            if (st == CRYSTAL_OK) {
+                fifo.pop_front();
+                continue;
+            }
+            if (st != CRYSTAL_EAGAIN) {
+                fifo.pop_front();
+                refuse(i, st);
+                continue;
+            }
+            uint32_t finished;
+            {
+                std::lock_guard<std::mutex> lk(s.mu);
+                finished = s.finished;
+            }
+            if (finished == admitted) {  // nothing in flight: it can never fit
+                fifo.pop_front();
+                refuse(i, CRYSTAL_ENOMEM);
+                continue;
+            }
+            // The oldest request waits for room.  While it is young, later
+            // requests that fit now are admitted past it (a few candidates per
+            // pass); once it has waited bypass_ns nothing passes it any more,
+            // so completions free room for it and it cannot starve.
+            if (now - std::min(now, req[i].arrival_ns) < s.bypass_ns) {
+                size_t k = 1;
+                for (uint32_t tried = 0; k < fifo.size() && tried < kBypassCandidates; ++tried) {
+                    const uint32_t j = fifo[k];
+                    const int sj = try_admit(j);
+                    if (sj == CRYSTAL_EAGAIN) {
+                        ++k;
+                        continue;
+                    }
+                    fifo.erase(fifo.begin() + (std::ptrdiff_t)k);
+                    if (sj != CRYSTAL_OK) refuse(j, sj);
+                }
+            }
+            break;  // wait for a completion (or the next arrival)
         }
         std::unique_lock<std::mutex> lk(s.mu);
         if (s.finished == n) break;

@@ -9,9 +9,10 @@ in the forms the paper compares (Section 5.2, Figure 7):
                       streams, outstanding jobs batched per launch; the data
                       are produced straight into the jobs' pinned buffers
                       (Section 2.1's advice) before the stream starts.
-* ``pooled_staged``   the same runtime, but a ring of ``depth`` jobs is
-                      refilled from pageable memory by the application thread
-                      (one host copy per job inside the timed region).
+* ``pooled_staged``   the same runtime fed from pageable memory: the
+                      library's staging ring (``crystal_stream_staged``) of
+                      ``depth`` pooled jobs, refilled by ``copy_threads`` C++
+                      threads (one host copy per unit inside the timed region).
 * ``no_overlap``      pooled buffers, one stream, one job at a time: copy-in,
                       kernel and copy-out of a job never overlap another job.
 * ``per_job_malloc``  every job allocates its pinned and device buffers when
@@ -75,7 +76,8 @@ def _used(kind: int, n: int, out: np.ndarray) -> int:
 def run_stream(mode: str, unit: Callable[[int], np.ndarray], n_units: int, unit_bytes: int, kind: int,
                p: C.crystal_hash_params, out_size: int, *, streams: int = 8, batch_jobs: int = 8,
                depth: int = 24, graphs: bool = True, device: int = 0, keep: Sequence[int] = (),
-               device_pool_bytes: Optional[int] = None, host_pool_bytes: Optional[int] = None) -> StreamResult:
+               device_pool_bytes: Optional[int] = None, host_pool_bytes: Optional[int] = None,
+               copy_threads: int = 8) -> StreamResult:
     """Hash ``n_units`` units (``unit(i)`` returns unit i's bytes) in ``mode``.
 
     Returns wall time of the stream (first submit to last completion seen by
@@ -96,7 +98,16 @@ def run_stream(mode: str, unit: Callable[[int], np.ndarray], n_units: int, unit_
                     max_batch_jobs=batch_jobs, max_batch_bytes=batch_jobs * max(unit_bytes, 1))
     res = StreamResult(mode, n_units, n_units * unit_bytes, 0.0, [])
     try:
-        if resident:
+        if mode == "pooled_staged":
+            src = [unit(i) for i in range(n_units)]  # pageable application memory
+            st, rr, wall, outs = ctx.stream_staged(src, kind, out_size, p, copy_threads=copy_threads,
+                                                   ring_jobs=ring, keep_outputs=bool(keep))
+            res.seconds = wall / 1e9
+            res.statuses = [int(x) for x in rr["status"]]
+            res.latencies_ms = ((rr["done_ns"].astype(np.float64) - rr["submit_ns"].astype(np.float64)) / 1e6).tolist()
+            for i in keep:
+                res.outputs[i] = outs[i, :int(rr["used_bytes"][i])].tobytes()
+        elif resident:
             tasks = [ctx.task_create(unit_bytes, out_size) for _ in range(n_units)]
             for i, t in enumerate(tasks):
                 t.h_in[:] = unit(i)  # produced into the job's pinned buffer, before the stream
@@ -113,10 +124,9 @@ def run_stream(mode: str, unit: Callable[[int], np.ndarray], n_units: int, unit_
                     res.outputs[i] = t.h_out[:_used(kind, unit_bytes, t.h_out)].tobytes()
                 t.release()
         else:
-            src = [unit(i) for i in range(n_units)]  # pageable application memory
-            pool = None
-            if mode == "pooled_staged":
-                pool = [ctx.task_create(unit_bytes, out_size) for _ in range(ring)]
+            # per-job allocation: each job allocated, filled from pageable
+            # application memory, submitted, waited for and freed
+            src = [unit(i) for i in range(n_units)]
             inflight = []  # (unit index, task)
 
             def retire():
@@ -126,25 +136,19 @@ def run_stream(mode: str, unit: Callable[[int], np.ndarray], n_units: int, unit_
                 res.latencies_ms.append((d - s) / 1e6)
                 if i in keep:
                     res.outputs[i] = t.h_out[:_used(kind, unit_bytes, t.h_out)].tobytes()
-                if pool is None:
-                    t.release()
-                else:
-                    pool.append(t)
+                t.release()
 
             t0 = time.perf_counter()
             for i in range(n_units):
                 if len(inflight) >= ring:
                     retire()
-                t = pool.pop(0) if pool is not None else ctx.task_create(unit_bytes, out_size)
+                t = ctx.task_create(unit_bytes, out_size)
                 t.h_in[:] = src[i]
                 C.check(t.submit(kind, p), "crystal_task_submit")
                 inflight.append((i, t))
             while inflight:
                 retire()
             res.seconds = time.perf_counter() - t0
-            if pool is not None:
-                for t in pool:
-                    t.release()
     finally:
         ctx.shutdown()
     return res
@@ -173,26 +177,44 @@ def make_trace(seed: int, n: int, rate_per_s: float, source_bytes: int, *, media
     req["src_offset"] = offs
     req["size"] = sizes
     req["kind"] = np.where(sliding, C.CRYSTAL_KIND_MD5_SLIDING, C.CRYSTAL_KIND_MD5_DIRECT)
-    out = np.full(n, 16, dtype=np.uint64)
-    for i in np.nonzero(sliding)[0]:
-        n_i = int(sizes[i])
-        out[i] = C.sliding_out_bytes(n_i, chunk_room * (n_i // 8192) + 64)
+    set_out_sizes(req, chunk_room)
+    cap_bytes = assign_capture(req, capture_every)
+    return req, cap_bytes
+
+
+def set_out_sizes(req, chunk_room: int = 4) -> None:
+    """Output bytes of every request from its kind and size: the digest for
+    direct requests; for sliding ones the header, the bitmap and room for
+    ``chunk_room`` times the expected chunk count (one chunk per 8 KiB on
+    random data) plus 64 records."""
+    out = np.empty(len(req), dtype=np.uint64)
+    for i in range(len(req)):
+        k, n = int(req["kind"][i]), int(req["size"][i])
+        out[i] = C.sliding_out_bytes(n, chunk_room * (n // 8192) + 64, k) if k in C.SLIDING_KINDS else \
+            C.digest_size(k)
     req["out_size"] = out
+
+
+def assign_capture(req, every: int = 1) -> int:
+    """Give every ``every``-th request (0: none) a 16-byte aligned slot of its
+    ``out_size`` bytes in one capture buffer; returns the buffer's size."""
     req["capture_offset"] = C.NO_CAPTURE
     cap_bytes = 0
-    if capture_every:
-        for i in range(0, n, capture_every):
+    if every:
+        for i in range(0, len(req), every):
             req["capture_offset"][i] = cap_bytes
-            cap_bytes += int(out[i] + 15) // 16 * 16
-    return req, cap_bytes
+            cap_bytes += int(req["out_size"][i] + 15) // 16 * 16
+    return cap_bytes
 
 
 def serve_trace(req, source, *, device_pool_bytes: int, host_pool_bytes: int, streams: int = 8,
                 batch_jobs: int = 8, copy_threads: int = 8, device: int = 0, capture_bytes: int = 0,
-                graphs: bool = True, direct=None, sliding=None, source_pinned: bool = False):
+                graphs: bool = True, direct=None, sliding=None, source_pinned: bool = False,
+                arrival_order: bool = False, bypass_ns: int = 0):
     """Run a trace through crystal_serve on a fresh context sized to the pools.
     With ``source_pinned`` the source is page-locked for the run and jobs read
-    their input from it directly.  Returns (status, results, wall_ns, capture)."""
+    their input from it directly; ``arrival_order`` / ``bypass_ns`` set the
+    admission policy.  Returns (status, results, wall_ns, capture)."""
     max_in = int(req["size"].max()) if len(req) else 1
     max_out = int(req["out_size"].max()) if len(req) else 16
     ctx = C.Context(max_in_bytes=max(max_in, 1), max_out_bytes=max(max_out, 16),
@@ -204,7 +226,8 @@ def serve_trace(req, source, *, device_pool_bytes: int, host_pool_bytes: int, st
         C.host_register(source)
     try:
         st, res, wall = ctx.serve(source, req, direct=direct, sliding=sliding, capture=capture,
-                                  copy_threads=copy_threads, source_pinned=source_pinned)
+                                  copy_threads=copy_threads, source_pinned=source_pinned,
+                                  arrival_order=arrival_order, bypass_ns=bypass_ns)
     finally:
         ctx.shutdown()
         if source_pinned:
@@ -231,15 +254,6 @@ def make_batch(seed: int, n: int, source_bytes: int, *, lo: int = 4096, hi: int 
     req["src_offset"] = offs
     req["size"] = sizes
     req["kind"] = np.where(sliding, C.CRYSTAL_KIND_MD5_SLIDING, C.CRYSTAL_KIND_MD5_DIRECT)
-    out = np.full(n, 16, dtype=np.uint64)
-    for i in np.nonzero(sliding)[0]:
-        n_i = int(sizes[i])
-        out[i] = C.sliding_out_bytes(n_i, chunk_room * (n_i // 8192) + 64)
-    req["out_size"] = out
-    req["capture_offset"] = C.NO_CAPTURE
-    cap_bytes = 0
-    if capture:
-        for i in range(n):
-            req["capture_offset"][i] = cap_bytes
-            cap_bytes += int(out[i] + 15) // 16 * 16
+    set_out_sizes(req, chunk_room)
+    cap_bytes = assign_capture(req, 1 if capture else 0)
     return req, cap_bytes

@@ -35,6 +35,9 @@ def test_batched_uneven_autotuned_bit_exact(C, oracle_mod):
         best, table = A.tune(req[:400], src, device_pool_bytes=512 << 20, streams=(2, 8), batch_jobs=(4, 64),
                              batch_bytes=(32 << 20,), repeats=1)
         assert len(table) == 4 and best.streams in (2, 8)
+        best, gtable = A.tune_geometry(req[:400], src, best, device_pool_bytes=512 << 20, repeats=1,
+                                       knobs=(("seg_threads", (128, 64)), ("win_ctas_per_sm", (0, 2))))
+        assert set(best.geometry) <= {0, 1, 2} and len(best.geometry) >= 2 and len(gtable) >= 2 * len(best.geometry)
         import numpy as np
 
         capture = np.zeros(cap, dtype=np.uint8)

@@ -77,9 +77,8 @@ def _check(C, tasks, jobs, want):
         assert same_result(kind, len(data), g, w), f"job {i}: " + first_difference(kind, len(data), g, w)
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2, 4, 8, 1 | 2 | 4, 16, 8 | 16], ids=["pooled", "no_pool", "no_overlap",
-                                                                            "no_batch", "graphs", "plain",
-                                                                            "sm_copy", "graphs_sm_copy"])
+@pytest.mark.parametrize("flags", [0, 1, 2, 4, 8, 1 | 2 | 4], ids=["pooled", "no_pool", "no_overlap", "no_batch",
+                                                                  "graphs", "plain"])
 def test_runtime_modes_bit_exact(C, oracle_mod, flags):
     jobs = _jobs(C)
     want = _want(oracle_mod, jobs)
@@ -448,12 +447,11 @@ def test_wait_many_and_timing_many(C, oracle_mod):
         assert seen == [C.CRYSTAL_EINVAL]
 
 
-@pytest.mark.parametrize("flags", [16, 8 | 16, 0], ids=["sm_copies", "sm_copies_graphs", "dma_only"])
+@pytest.mark.parametrize("flags", [0, 8], ids=["launches", "graphs"])
 def test_bound_inputs_every_alignment_and_small_sizes(C, oracle_mod, flags):
     """Inputs read in place from registered memory at every offset mod 16, with
-    sizes around the 16-byte vectors and the copy kernel's 16 KiB chunks, and
-    small outputs: the kernel-made copies (both directions) and the DMA path
-    give the oracle's bytes."""
+    sizes around 16-byte vectors and 16 KiB, and small outputs: the oracle's
+    bytes, each bound input copied by its own DMA transfer."""
     from paper_1005_1695_b300 import inputs
 
     sizes = [1, 2, 15, 16, 17, 31, 33, 63, 64, 65, 100, 4095, 4096, 4097, 16383, 16384, 16385, 16400, 40000,
@@ -490,9 +488,40 @@ def test_bound_inputs_every_alignment_and_small_sizes(C, oracle_mod, flags):
                 assert same_result(kind, n, g, w), f"job {i} n={n} off%16={off % 16}: " + \
                     first_difference(kind, n, g, w)
             st = ctx.stats()
-            if flags & C.CRYSTAL_FLAG_SM_COPY:
-                assert st.copies_sm > 0  # the kernel path really ran
-            else:
-                assert st.copies_sm == 0 and st.copies_dma > 0
+            # bound inputs never merge; direct digests are written in place (no copy-out)
+            n_sliding = sum(1 for j in jobs if j[0] == SLIDING)
+            assert st.copies_dma >= len(jobs) and st.copies_dma <= len(jobs) + n_sliding
     finally:
         C.host_unregister(src)
+
+
+@pytest.mark.parametrize("graphs", [0, 8], ids=["launches", "graphs"])
+def test_launch_geometry_per_size_class_bit_exact(C, oracle_mod, graphs):
+    """Every geometry choice (segment-kernel CTA size and CTAs per SM, window
+    kernel CTAs per SM and register budget, chunk-segment CTAs per SM), set per
+    batch size class, gives the oracle's bytes; bad fields are refused."""
+    jobs = _jobs(C, count=30, seed=13)
+    want = _want(oracle_mod, jobs)
+    geoms = [C.geometry(seg_threads=64, seg_ctas_per_sm=1, win_ctas_per_sm=1, win_registers=64, digest_ctas_per_sm=1),
+             C.geometry(seg_threads=256, seg_ctas_per_sm=2, win_ctas_per_sm=3, win_registers=32, digest_ctas_per_sm=2),
+             C.geometry()]
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=256 << 20,
+                   host_pool_bytes=128 << 20, n_streams=3, flags=graphs, max_batch_jobs=4) as ctx:
+        for k in range(len(geoms)):
+            for cls in range(C.CRYSTAL_SIZE_CLASSES):
+                ctx.set_geometry(cls, geoms[(k + cls) % len(geoms)])
+            g = ctx.get_geometry(1)
+            assert g.seg_threads in (64, 128, 256) and g.win_registers in (32, 64) and g.seg_ctas_per_sm >= 1
+            tasks = _submit_all(C, ctx, jobs)
+            _check(C, tasks, jobs, want)
+            for t in tasks:
+                assert t.release() == C.CRYSTAL_OK
+        got = ctx.get_geometry(0)
+        assert (got.seg_threads, got.seg_ctas_per_sm, got.win_ctas_per_sm) == (256, 2, 3)
+        L = C.load()
+        for bad in (C.geometry(seg_threads=96), C.geometry(win_registers=48), C.geometry(reserved=1),
+                    C.geometry(win_ctas_per_sm=65)):
+            assert L.crystal_set_geometry(ctx.handle, 0, ctypes.byref(bad)) == C.CRYSTAL_EINVAL
+        assert L.crystal_set_geometry(ctx.handle, 3, None) == C.CRYSTAL_EINVAL
+        ctx.set_geometry(-1, None)
+        assert ctx.get_geometry(2).seg_threads == 128

@@ -81,3 +81,41 @@ def test_request_that_never_fits_fails_cleanly(C):
     others = np.delete(res["status"], 5)
     assert (others == 0).all()
     assert st == C.CRYSTAL_ENOMEM
+
+
+@pytest.mark.parametrize("arrival_order", [False, True], ids=["bypass", "arrival_order"])
+def test_admission_past_a_blocked_large_request(C, oracle_mod, arrival_order):
+    """Two 12 MiB requests (3 and 5) cannot be resident together in a 20 MiB
+    device pool.  While request 5 waits for room, the small requests behind it
+    that fit are admitted past it (for a bounded time); with strict arrival
+    order nothing passes it.  Every output stays bit-exact either way."""
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    src = inputs.arena(6, 32 << 20, out=C.page_aligned(32 << 20))
+    req, _ = S.make_trace(6, 40, 1000.0, src.nbytes, median=64 << 10, sigma=0.5, cap=256 << 10, p_sliding=0.3)
+    req["arrival_ns"] = 0  # all waiting at once
+    for i in (3, 5):
+        req["size"][i] = 12 << 20
+        req["src_offset"][i] = 1 << 20
+        req["kind"][i] = C.CRYSTAL_KIND_MD5_DIRECT
+    S.set_out_sizes(req)
+    cap = S.assign_capture(req)
+    st, res, wall, capture = S.serve_trace(req, src, device_pool_bytes=20 << 20, host_pool_bytes=64 << 20,
+                                           streams=4, batch_jobs=4, copy_threads=4, capture_bytes=cap,
+                                           source_pinned=True, arrival_order=arrival_order,
+                                           bypass_ns=1_000_000_000)
+    assert st == C.CRYSTAL_OK and (res["status"] == 0).all()
+    admit = res["admit_ns"].astype(np.int64)
+    passed = int((admit[6:] < admit[5]).sum())
+    if arrival_order:
+        assert (np.diff(admit) >= 0).all() and passed == 0
+    else:
+        assert passed > 0
+    for i in range(len(req)):
+        k, n, o = int(req["kind"][i]), int(req["size"][i]), int(req["src_offset"][i])
+        ost, want = oracle_mod.task(k, src[o:o + n], int(req["out_size"][i]))
+        off = int(req["capture_offset"][i])
+        got = capture[off:off + int(res["used_bytes"][i])].tobytes()
+        assert ost == 0 and same_result(k, n, got, want), f"request {i}: " + first_difference(k, n, got, want)
+

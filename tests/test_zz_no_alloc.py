@@ -3,8 +3,9 @@ device memory where they hash (a latency-bound storage or network data path,
 where cudaMalloc/cudaFree could synchronise the device, or a process whose
 free device memory belongs to another allocator).  Its scratch is a fixed
 array inside the library; this checks, through the C ABI, that two calls in a
-row give the same digests as the allocating batch launcher, and that a
-request above the array's size is refused.
+row give the same digests as the allocating batch launcher and as the CPU
+oracle, that a request exactly at the array's size is accepted and correct,
+and that one unit or one segment more is refused.
 
 This file is collected last on purpose, so that a run stopping at the first
 failure has run every other test first.
@@ -55,7 +56,7 @@ def _noalloc(torch, fn, d_in, unit_bytes, n_units, seg):
     return [host[16 * u:16 * (u + 1)].tobytes() for u in range(n_units)]
 
 
-def test_noalloc_matches_existing_entry_point_twice(env):
+def test_noalloc_matches_existing_entry_point_twice(env, oracle_mod):
     torch, C, fn = env
     from paper_1005_1695_b300 import inputs
 
@@ -66,13 +67,40 @@ def test_noalloc_matches_existing_entry_point_twice(env):
         want = _reference(torch, C, d_in, unit_bytes, n_units, seg)
         got = _noalloc(torch, fn, d_in, unit_bytes, n_units, seg)
         assert got == want, (unit_bytes, n_units, seg)
+        oracle = [oracle_mod.direct(host[u * unit_bytes:(u + 1) * unit_bytes], seg) for u in range(n_units)]
+        assert got == oracle, (unit_bytes, n_units, seg)
+
+
+def _limit_case():
+    """16 units of 32,763 segments of 64 bytes: align_up(64 + 64 * 16, 256) +
+    16 * 16 * 32,763 = 1,280 + 8,387,328 bytes, exactly the array's size."""
+    n_units, seg, m = 16, 64, 32763
+    desc = (64 + 64 * n_units + 255) // 256 * 256
+    assert desc + 16 * n_units * m == SCRATCH_BYTES
+    return n_units, seg, m * seg
+
+
+def test_noalloc_exactly_at_the_limit(env, oracle_mod):
+    torch, C, fn = env
+    from paper_1005_1695_b300 import inputs
+
+    n_units, seg, unit_bytes = _limit_case()
+    host = np.concatenate([inputs.uniform_unit(32, u, unit_bytes) for u in range(n_units)])
+    d_in = torch.from_numpy(host).cuda()
+    got = _noalloc(torch, fn, d_in, unit_bytes, n_units, seg)
+    want = [oracle_mod.direct(host[u * unit_bytes:(u + 1) * unit_bytes], seg) for u in range(n_units)]
+    assert got == want
 
 
 def test_noalloc_refuses_requests_above_the_array(env):
     torch, C, fn = env
-    d_in = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    n_units, seg, unit_bytes = _limit_case()
+    d_in = torch.zeros((n_units + 1) * unit_bytes + 1, dtype=torch.uint8, device="cuda")
     out = torch.zeros(16 * 4096, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
+    # one unit more, or one byte more per unit (one more segment each), than the limit
+    assert fn(d_in.data_ptr(), unit_bytes, n_units + 1, seg, out.data_ptr(), stream) == C.CRYSTAL_EINVAL
+    assert fn(d_in.data_ptr(), unit_bytes + 1, n_units, seg, out.data_ptr(), stream) == C.CRYSTAL_EINVAL
     # 4096 units of 1 MiB at 1 KiB segments need 64 MiB of digests
     assert fn(d_in.data_ptr(), 1 << 20, 4096, 1024, out.data_ptr(), stream) == C.CRYSTAL_EINVAL
     assert fn(d_in.data_ptr(), 1 << 20, 1, 0, out.data_ptr(), stream) == C.CRYSTAL_EINVAL
