@@ -221,7 +221,10 @@ int crystal_task_wait(crystal_task* task, int64_t timeout_ns);
 int crystal_task_wait_many(crystal_task* const* tasks, uint32_t n, int64_t timeout_ns);
 
 /* job_put(), Figure 3: returns the job's buffers to the pool.  EINVAL while
- * the job is queued or running. */
+ * the job is queued or running, except from the job's own completion
+ * callback: there the buffers return to the pools at once (the output must
+ * not be touched after the call) and the handle is freed when the callback
+ * returns. */
 int crystal_task_release(crystal_task* task);
 
 /* Host clock stamps (nanoseconds, CLOCK_MONOTONIC) of the job's last run:

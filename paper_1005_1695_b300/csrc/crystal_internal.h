@@ -12,6 +12,9 @@
 namespace crystal {
 
 extern std::atomic<uint64_t> g_kernel_launches;
+// Set while this thread captures a graph: captured launches are counted when
+// the graph is replayed, not when it is captured.
+extern thread_local bool tl_capturing;
 
 // Grid and CTA shape of each kernel of a batch (kernels.cu): resolved from a
 // crystal_geometry against the kernels' occupancy on the current device.

@@ -33,6 +33,7 @@
 namespace crystal {
 
 std::atomic<uint64_t> g_kernel_launches{0};
+thread_local bool tl_capturing = false;
 
 namespace {
 
@@ -912,7 +913,7 @@ uint32_t g_one = 1;
 
 int launched(int kernels) {
     if (cudaGetLastError() != cudaSuccess) return CRYSTAL_EDEVICE;
-    g_kernel_launches.fetch_add((uint64_t)kernels, std::memory_order_relaxed);
+    if (!tl_capturing) g_kernel_launches.fetch_add((uint64_t)kernels, std::memory_order_relaxed);
     return CRYSTAL_OK;
 }
 

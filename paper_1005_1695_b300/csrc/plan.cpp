@@ -20,22 +20,68 @@
 
 using namespace crystal;
 
+// Free blocks are indexed three ways: by offset (to merge neighbours), by
+// (length, offset) (best fit), and in 64 buckets of lengths [2^k, 2^(k+1)),
+// each ordered by offset, so that the lowest or highest block that fits is
+// found from the first or last entry of the buckets that surely fit plus a
+// short walk of the one bucket that may not -- not by walking every free
+// block in address order.
 struct crystal_arena {
     uint64_t size = 0;
     uint64_t align = 256;
     uint64_t used = 0;
     std::map<uint64_t, uint64_t> free_by_off;             // offset -> length
     std::set<std::pair<uint64_t, uint64_t>> free_by_len;  // (length, offset)
+    std::set<uint64_t> bucket[64];                        // offsets of free blocks, by floor(log2 length)
     std::unordered_map<uint64_t, uint64_t> live;          // offset -> length
     std::mutex mu;
 
+    static int bucket_of(uint64_t len) { return 63 - __builtin_clzll(len); }
     void insert_free(uint64_t off, uint64_t len) {
         free_by_off.emplace(off, len);
         free_by_len.emplace(len, off);
+        bucket[bucket_of(len)].insert(off);
     }
     void erase_free(std::map<uint64_t, uint64_t>::iterator it) {
         free_by_len.erase({it->second, it->first});
+        bucket[bucket_of(it->second)].erase(it->first);
         free_by_off.erase(it);
+    }
+    // Lowest (highest) free block of at least `want` bytes: buckets above
+    // want's own hold only blocks that fit, so their first (last) offset is a
+    // candidate; in want's own bucket, walk in offset order to the first block
+    // that fits, stopping once past the best candidate.  false: none fits.
+    bool extreme_fit(uint64_t want, bool lowest, uint64_t* off) const {
+        const int kw = bucket_of(want);
+        bool found = false;
+        uint64_t best = 0;
+        auto better = [&](uint64_t o) { return !found || (lowest ? o < best : o > best); };
+        for (int k = kw + 1; k < 64; ++k) {
+            if (bucket[k].empty()) continue;
+            const uint64_t o = lowest ? *bucket[k].begin() : *bucket[k].rbegin();
+            if (better(o)) {
+                best = o;
+                found = true;
+            }
+        }
+        auto fits = [&](uint64_t o) { return free_by_off.find(o)->second >= want; };
+        if (lowest) {
+            for (auto it = bucket[kw].begin(); it != bucket[kw].end() && better(*it); ++it)
+                if (fits(*it)) {
+                    best = *it;
+                    found = true;
+                    break;
+                }
+        } else {
+            for (auto it = bucket[kw].rbegin(); it != bucket[kw].rend() && better(*it); ++it)
+                if (fits(*it)) {
+                    best = *it;
+                    found = true;
+                    break;
+                }
+        }
+        if (found) *off = best;
+        return found;
     }
 };
 
@@ -66,21 +112,11 @@ int crystal_arena_alloc_at(crystal_arena* a, uint64_t bytes, int placement, uint
         if (it == a->free_by_len.end()) return CRYSTAL_EAGAIN;
         len = it->first;
         off = it->second;
-    } else if (placement == CRYSTAL_ARENA_LOWEST) {
-        auto it = a->free_by_off.begin();
-        while (it != a->free_by_off.end() && it->second < want) ++it;
-        if (it == a->free_by_off.end()) return CRYSTAL_EAGAIN;
-        off = it->first;
-        len = it->second;
     } else {
-        auto it = a->free_by_off.rbegin();
-        while (it != a->free_by_off.rend() && it->second < want) ++it;
-        if (it == a->free_by_off.rend()) return CRYSTAL_EAGAIN;
-        off = it->first;
-        len = it->second;
+        if (!a->extreme_fit(want, placement == CRYSTAL_ARENA_LOWEST, &off)) return CRYSTAL_EAGAIN;
+        len = a->free_by_off.find(off)->second;
     }
-    a->free_by_len.erase({len, off});
-    a->free_by_off.erase(off);
+    a->erase_free(a->free_by_off.find(off));
     uint64_t at = off;
     if (placement == CRYSTAL_ARENA_HIGHEST) {
         at = off + len - want;  // top of the block; the rest stays free below it

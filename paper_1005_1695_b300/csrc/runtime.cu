@@ -53,6 +53,7 @@ constexpr uint64_t kWaitSpinNs = 200000;
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    uint32_t stream_index = 0;
     bool own_stream = false;  // slots beyond the first n_streams share a stream
     cudaEvent_t done = nullptr;
     crystal_batch* h_desc = nullptr;  // pinned
@@ -80,6 +81,7 @@ struct crystal_task {
     uint8_t* d_reserved = nullptr;  // scratch reserved at create (crystal_task_create_ex)
     const uint8_t* h_in_ext = nullptr;  // caller memory bound as the input (crystal_task_bind_input)
     bool external_input = false;        // created without its own pinned input buffer
+    bool one_block = false;             // d_in, d_out and d_reserved are one device allocation at d_in
     uint64_t h_in_off = 0, h_out_off = 0, d_in_off = 0, d_out_off = 0, d_scratch_off = 0, d_reserved_off = 0;
     uint64_t reserved_bytes = 0;
     uint64_t in_cap = 0, out_cap = 0, in_size = 0, out_size = 0, scratch_bytes = 0;
@@ -152,10 +154,12 @@ struct crystal_ctx {
     std::condition_variable cv_done;
     OutstandingQueue outstanding;
     std::deque<uint32_t> running;  // slot indices in dispatch order
-    std::unordered_set<crystal_task*> tasks;
+    std::mutex tasks_mu;           // guards `tasks` only (not the queues), so that creating and
+    std::unordered_set<crystal_task*> tasks;  // freeing jobs does not hold up submits and completion
     std::thread master;
     bool stop = false;
-    bool accepting = true;
+    bool accepting = true;                 // written under mu
+    std::atomic<bool> accepting_fast{true};  // its copy for checks that need no lock
     uint64_t seq = 0;
 
     std::atomic<uint64_t> n_outstanding{0};  // mirrors outstanding.size() for the idle spin
@@ -224,6 +228,10 @@ void free_job_scratch(crystal_ctx* c, crystal_task* t) {
 void free_task_buffers(crystal_task* t) {
     crystal_ctx* c = t->ctx;
     free_job_scratch(c, t);
+    if (t->one_block) {
+        free_device(c, t->d_in, t->d_in_off);
+        t->d_in = t->d_reserved = t->d_out = nullptr;
+    }
     free_device(c, t->d_reserved, t->d_reserved_off);
     t->d_reserved = nullptr;
     free_device(c, t->d_in, t->d_in_off);
@@ -343,12 +351,12 @@ int batch_sequence(crystal_ctx* c, Slot& s, bool direct, bool sliding, const Lau
 // Capture batch_sequence of one slot as a graph.
 int capture_graph(crystal_ctx* c, Slot& s, int cls, int variant) {
     const bool direct = variant & 1, sliding = variant & 2;
-    const uint64_t before = g_kernel_launches.load();
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CRYSTAL_EDEVICE;
+    tl_capturing = true;
     int r = batch_sequence(c, s, direct, sliding, &c->geom[cls]);
+    tl_capturing = false;
     cudaError_t e = cudaStreamEndCapture(s.stream, &g);
-    g_kernel_launches.store(before);
     if (r != CRYSTAL_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
@@ -499,8 +507,24 @@ int job_status(crystal_task* t, uint32_t dev_status) {
     return CRYSTAL_OK;
 }
 
+// Jobs released from their callbacks (their buffers are already back in the
+// pools): out of the registry, handles freed.
+void destroy_released(crystal_ctx* c, const std::vector<crystal_task*>& released) {
+    if (released.empty()) return;
+    {
+        std::lock_guard<std::mutex> lk(c->tasks_mu);
+        for (crystal_task* j : released) c->tasks.erase(j);
+    }
+    for (crystal_task* j : released) {
+        free_task_buffers(j);
+        delete j;
+    }
+}
+
 // Finish the jobs of a slot: statuses, scratch back to the pool, callbacks,
-// waiters.  Called by the master thread without the lock held.
+// then the jobs' final states in one locked step, waiters, and the buffers
+// of jobs released from their callbacks.  Called by the master thread
+// without the lock held.
 void finish_slot(crystal_ctx* c, Slot& s, int issue_status) {
     const uint64_t t = now_ns();
     const uint32_t dev_status = s.h_desc ? s.h_desc->status : 0;
@@ -517,22 +541,20 @@ void finish_slot(crystal_ctx* c, Slot& s, int issue_status) {
             j->cb(j, j->status, j->user);
             tl_callback_ctx = nullptr;
         }
-        std::lock_guard<std::mutex> lk(c->mu);
-        c->n_running_jobs--;
-        c->jobs_completed.fetch_add(1);
-        if (j->release_in_callback) {
-            c->tasks.erase(j);
-            free_task_buffers(j);
-            delete j;
-        } else {
-            j->state = T_DONE;
-        }
     }
+    std::vector<crystal_task*> released;
     {
         std::lock_guard<std::mutex> lk(c->mu);
+        for (crystal_task* j : jobs) {
+            c->n_running_jobs--;
+            if (j->release_in_callback) released.push_back(j);
+            else j->state = T_DONE;
+        }
         s.busy = false;
     }
+    c->jobs_completed.fetch_add(jobs.size());
     c->cv_done.notify_all();
+    destroy_released(c, released);
 }
 
 bool take_batch(crystal_ctx* c, Slot& s) {
@@ -570,16 +592,17 @@ void cancel_outstanding(crystal_ctx* c) {
             t->cb(t, t->status, t->user);
             tl_callback_ctx = nullptr;
         }
+    }
+    std::vector<crystal_task*> released;
+    {
         std::lock_guard<std::mutex> g(c->mu);
-        if (t->release_in_callback) {
-            c->tasks.erase(t);
-            free_task_buffers(t);
-            delete t;
-        } else {
-            t->state = T_DONE;
+        for (crystal_task* t : cancel) {
+            if (t->release_in_callback) released.push_back(t);
+            else t->state = T_DONE;
         }
     }
     c->cv_done.notify_all();
+    destroy_released(c, released);
 }
 
 // The master thread (Section 4.2).  The running list and the slots' busy
@@ -592,11 +615,21 @@ void master_loop(crystal_ctx* c) {
     const bool sequential = c->cfg.flags & CRYSTAL_FLAG_NO_OVERLAP;
     for (;;) {
         bool progressed = false;
-        // completion: every running slot whose event has fired
+        // completion: every running slot whose event has fired.  A stream
+        // completes its slots in dispatch order, so once a slot is not done
+        // the later slots of its stream are not queried this pass (each query
+        // takes the driver's context lock).
+        uint64_t blocked = 0;  // streams with a slot still running, as bits (at most 64 streams)
         for (size_t i = 0; i < c->running.size();) {
             Slot& s = c->slots[c->running[i]];
+            const uint64_t bit = 1ull << s.stream_index;
+            if (blocked & bit) {
+                ++i;
+                continue;
+            }
             const cudaError_t e = cudaEventQuery(s.done);
             if (e == cudaErrorNotReady) {
+                blocked |= bit;
                 ++i;
                 continue;
             }
@@ -814,6 +847,7 @@ int crystal_init(const crystal_config* user_cfg, crystal_ctx** out) {
         } else {
             s.stream = c->slots[i % c->cfg.n_streams].stream;
         }
+        s.stream_index = i % (uint32_t)c->cfg.n_streams;
         if (cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             destroy_ctx(c);
@@ -852,6 +886,7 @@ int crystal_shutdown(crystal_ctx* c) {
     {
         std::lock_guard<std::mutex> lk(c->mu);
         c->accepting = false;
+        c->accepting_fast.store(false);
         c->stop = true;
     }
     c->cv_master.notify_all();
@@ -892,10 +927,7 @@ int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scr
     if (flags & ~(uint32_t)CRYSTAL_TASK_EXTERNAL_INPUT) return CRYSTAL_EINVAL;
     *out = nullptr;
     if (in_size > c->cfg.max_in_bytes || out_size > c->cfg.max_out_bytes) return CRYSTAL_EINVAL;
-    {
-        std::lock_guard<std::mutex> lk(c->mu);
-        if (!c->accepting) return CRYSTAL_ESHUTDOWN;
-    }
+    if (!c->accepting_fast.load()) return CRYSTAL_ESHUTDOWN;
     if (!c->pooled) cudaSetDevice(c->device);
     crystal_task* t = new (std::nothrow) crystal_task;
     if (!t) return CRYSTAL_ENOMEM;
@@ -906,18 +938,34 @@ int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scr
     // inputs from the bottom of the arenas, outputs and scratch from the top
     int st = t->external_input ? CRYSTAL_OK : alloc_host(c, in_size, &t->h_in, &t->h_in_off, CRYSTAL_ARENA_LOWEST);
     if (st == CRYSTAL_OK) st = alloc_host(c, out_size, &t->h_out, &t->h_out_off, CRYSTAL_ARENA_HIGHEST);
-    if (st == CRYSTAL_OK) st = alloc_device(c, in_size, &t->d_in, &t->d_in_off, CRYSTAL_ARENA_LOWEST);
-    if (st == CRYSTAL_OK) st = alloc_device(c, out_size, &t->d_out, &t->d_out_off, CRYSTAL_ARENA_HIGHEST);
-    if (st == CRYSTAL_OK && scratch_bytes) {
-        st = alloc_device(c, scratch_bytes, &t->d_reserved, &t->d_reserved_off);
-        if (st == CRYSTAL_OK) t->reserved_bytes = scratch_bytes;
+    if (st == CRYSTAL_OK && t->external_input && c->pooled) {
+        // an external input is copied on its own (never merged with its
+        // neighbours), so the job's device input, output and scratch are one
+        // block: one allocation and one free instead of three
+        const uint64_t in_b = align_up(in_size ? in_size : 1, 256), out_b = align_up(out_size ? out_size : 1, 256);
+        st = alloc_device(c, in_b + out_b + scratch_bytes, &t->d_in, &t->d_in_off, CRYSTAL_ARENA_HIGHEST);
+        if (st == CRYSTAL_OK) {
+            t->one_block = true;
+            t->d_out = t->d_in + in_b;
+            if (scratch_bytes) {
+                t->d_reserved = t->d_out + out_b;
+                t->reserved_bytes = scratch_bytes;
+            }
+        }
+    } else {
+        if (st == CRYSTAL_OK) st = alloc_device(c, in_size, &t->d_in, &t->d_in_off, CRYSTAL_ARENA_LOWEST);
+        if (st == CRYSTAL_OK) st = alloc_device(c, out_size, &t->d_out, &t->d_out_off, CRYSTAL_ARENA_HIGHEST);
+        if (st == CRYSTAL_OK && scratch_bytes) {
+            st = alloc_device(c, scratch_bytes, &t->d_reserved, &t->d_reserved_off);
+            if (st == CRYSTAL_OK) t->reserved_bytes = scratch_bytes;
+        }
     }
     if (st != CRYSTAL_OK) {
         free_task_buffers(t);
         delete t;
         return st;
     }
-    std::lock_guard<std::mutex> lk(c->mu);
+    std::lock_guard<std::mutex> lk(c->tasks_mu);
     c->tasks.insert(t);
     *out = t;
     return CRYSTAL_OK;
@@ -1175,12 +1223,20 @@ int crystal_task_release(crystal_task* t) {
     crystal_ctx* c = t->ctx;
     std::unique_lock<std::mutex> lk(c->mu);
     if (t->state == T_RUNNING && tl_callback_ctx == c) {
-        t->release_in_callback = true;  // freed by the master after the callback returns
+        // from the job's own callback: its buffers go back to the pools now
+        // (the caller may count on the room, e.g. to admit the next job); the
+        // handle itself is freed by the master after the callback returns
+        t->release_in_callback = true;
+        lk.unlock();
+        free_task_buffers(t);
         return CRYSTAL_OK;
     }
     if (t->state == T_OUTSTANDING || t->state == T_RUNNING) return CRYSTAL_EINVAL;
-    c->tasks.erase(t);
     lk.unlock();
+    {
+        std::lock_guard<std::mutex> g(c->tasks_mu);
+        c->tasks.erase(t);
+    }
     if (!c->pooled) cudaSetDevice(c->device);
     free_task_buffers(t);
     delete t;

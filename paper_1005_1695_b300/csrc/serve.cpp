@@ -65,21 +65,26 @@ struct Serve {
     uint32_t finished = 0;
     uint64_t last_done = 0;
     bool workers_stop = false;
+    bool loop_waits = false;  // the admission loop is waiting on cv_done (under mu)
 
     const crystal_hash_params* params_for(int kind) const {
         return kind == CRYSTAL_KIND_MD5_SLIDING || kind == CRYSTAL_KIND_SHA1_SLIDING ? &ps : &pd;
     }
 
+    // A request is done; wake the admission loop only if it waits for one
+    // (a wake-up is a system call on the master thread's completion path).
     void finish(uint32_t i, int status) {
         const uint64_t t = mono_ns() - t0;
+        bool wake;
         {
             std::lock_guard<std::mutex> lk(mu);
             res[i].status = status;
             res[i].done_ns = t;
             ++finished;
             if (t > last_done) last_done = t;
+            wake = loop_waits;
         }
-        cv_done.notify_all();
+        if (wake) cv_done.notify_all();
     }
 };
 
@@ -258,8 +263,10 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
             // blocked on pool room: wake on a completion or the next arrival
             const uint32_t before = s.finished;
             const uint64_t wait = next < n && req[next].arrival_ns > now ? req[next].arrival_ns - now : 200000;
+            s.loop_waits = true;
             s.cv_done.wait_for(lk, std::chrono::nanoseconds(wait < 200000 ? wait : 200000),
                                [&] { return s.finished != before; });
+            s.loop_waits = false;
         } else if (next < n) {
             const uint64_t due = req[next].arrival_ns;
             lk.unlock();
@@ -270,7 +277,9 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
                 while (mono_ns() - s.t0 < due) std::this_thread::yield();
             }
         } else {
+            s.loop_waits = true;
             s.cv_done.wait(lk, [&] { return s.finished == n; });
+            s.loop_waits = false;
             break;
         }
     }

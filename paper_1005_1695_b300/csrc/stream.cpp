@@ -68,6 +68,7 @@ struct Ring {
     std::deque<uint32_t> free_jobs;  // FIFO: jobs rotate in creation order, so
                                      // consecutive submits have adjacent buffers
     uint32_t finished = 0;
+    uint32_t waiting = 0;  // copy threads waiting for a free job
 };
 
 // Used output bytes of a finished unit (never more than the job's buffer).
@@ -95,14 +96,19 @@ void retire(Ring* r, uint32_t j) {
     if (r->outputs) memcpy(r->outputs + (uint64_t)u * r->out_stride, out, std::min(x.used_bytes, r->out_stride));
 }
 
+// A job back in the ring: wake a copy thread only if one waits, the caller
+// only after the last unit (wake-ups cost system calls on the master thread).
 void give_back(Ring* r, uint32_t j) {
+    bool wake_copy, all_done;
     {
         std::lock_guard<std::mutex> lk(r->mu);
         r->free_jobs.push_back(j);
         ++r->finished;
+        wake_copy = r->waiting > 0;
+        all_done = r->finished == r->n;
     }
-    r->cv_free.notify_one();
-    r->cv_done.notify_all();
+    if (wake_copy) r->cv_free.notify_one();
+    if (all_done) r->cv_done.notify_all();
 }
 
 // Completion callback, on the master thread: record, hand the job back.  The
@@ -124,7 +130,9 @@ void copy_thread(Ring* r) {
         uint32_t j;
         {
             std::unique_lock<std::mutex> lk(r->mu);
+            ++r->waiting;
             r->cv_free.wait(lk, [r] { return !r->free_jobs.empty(); });
+            --r->waiting;
             j = r->free_jobs.front();
             r->free_jobs.pop_front();
         }

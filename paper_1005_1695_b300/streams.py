@@ -208,7 +208,7 @@ def assign_capture(req, every: int = 1) -> int:
 
 
 def serve_trace(req, source, *, device_pool_bytes: int, host_pool_bytes: int, streams: int = 8,
-                batch_jobs: int = 8, copy_threads: int = 8, device: int = 0, capture_bytes: int = 0,
+                batch_jobs: int = 8, copy_threads: int = 4, device: int = 0, capture_bytes: int = 0,
                 graphs: bool = True, direct=None, sliding=None, source_pinned: bool = False,
                 arrival_order: bool = False, bypass_ns: int = 0):
     """Run a trace through crystal_serve on a fresh context sized to the pools.

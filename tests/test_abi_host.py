@@ -113,6 +113,70 @@ def test_arena_alignment_and_random_churn(C):
     L.crystal_arena_destroy(h)
 
 
+def _alloc_at(L, h, n, placement):
+    off = ctypes.c_uint64()
+    st = L.crystal_arena_alloc_at(h, n, placement, ctypes.byref(off))
+    return st, off.value
+
+
+def test_arena_placement_matches_a_model(C):
+    """Random churn with all three placements against a plain model of the
+    free list: best fit takes the smallest block that fits (lowest offset on a
+    tie) from its bottom, LOWEST the lowest-addressed block that fits from its
+    bottom, HIGHEST the highest-addressed one from its top; freed blocks merge
+    with free neighbours."""
+    L, h = _arena(C, 32 << 20, 256)
+    free = {0: 32 << 20}  # offset -> length
+    live = {}
+    rng = np.random.default_rng(5)
+
+    def model_alloc(want, placement):
+        fits = [(o, n) for o, n in free.items() if n >= want]
+        if not fits:
+            return None
+        if placement == 0:
+            o, n = min(fits, key=lambda x: (x[1], x[0]))
+        elif placement == 1:
+            o, n = min(fits)
+        else:
+            o, n = max(fits)
+        del free[o]
+        at = o + n - want if placement == 2 else o
+        rest = (o, n - want) if placement == 2 else (o + want, n - want)
+        if rest[1]:
+            free[rest[0]] = rest[1]
+        return at
+
+    def model_free(o):
+        n = live.pop(o)
+        nxt = o + n
+        if nxt in free:
+            n += free.pop(nxt)
+        prev = [p for p, m in free.items() if p + m == o]
+        if prev:
+            o, n = prev[0], n + free.pop(prev[0])
+        free[o] = n
+
+    for step in range(3000):
+        if live and (rng.random() < 0.45 or len(live) > 150):
+            o = int(rng.choice(sorted(live)))
+            assert L.crystal_arena_free(h, o) == 0
+            model_free(o)
+        else:
+            n = int(rng.integers(1, 1 << 19)) if rng.random() < 0.9 else int(rng.integers(1, 600))
+            placement = int(rng.integers(0, 3))
+            want = (n + 255) // 256 * 256
+            expect = model_alloc(want, placement)
+            st, o = _alloc_at(L, h, n, placement)
+            if expect is None:
+                assert st == C.CRYSTAL_EAGAIN
+            else:
+                assert st == 0 and o == expect, (step, placement, n, o, expect)
+                live[o] = want
+        assert L.crystal_arena_largest_free(h) == max(free.values(), default=0)
+    L.crystal_arena_destroy(h)
+
+
 def test_sizes(C):
     p = C.params()
     assert C.out_bytes(C.CRYSTAL_KIND_MD5_DIRECT, 12345, p) == 16

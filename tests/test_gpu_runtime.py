@@ -516,7 +516,7 @@ def test_launch_geometry_per_size_class_bit_exact(C, oracle_mod, graphs):
             _check(C, tasks, jobs, want)
             for t in tasks:
                 assert t.release() == C.CRYSTAL_OK
-        got = ctx.get_geometry(0)
+        got = ctx.get_geometry(2)  # the last round set class 2 to geoms[(2 + 2) % 3]
         assert (got.seg_threads, got.seg_ctas_per_sm, got.win_ctas_per_sm) == (256, 2, 3)
         L = C.load()
         for bad in (C.geometry(seg_threads=96), C.geometry(win_registers=48), C.geometry(reserved=1),
