@@ -62,8 +62,8 @@ INT_LANES_PER_SM = 128  # 4 schedulers x one 32-lane instruction per clock
 # DRAM bytes (read + write) of the window kernel per 1 MiB sliding unit, from one
 # ncu capture of 160 units (traffic grows with the units processed), valid only
 # for the kernel sources it was taken on (checked by hash; otherwise null).
-WINDOW_TRAFFIC_PER_UNIT = (167.863552e6 + 14.007296e6) / 160
-WINDOW_TRAFFIC_SOURCES = "01a00e389f12a6e4"
+WINDOW_TRAFFIC_PER_UNIT = (168.187904e6 + 14.510336e6) / 160
+WINDOW_TRAFFIC_SOURCES = "4fb2be82d58950e7"
 
 
 def _kernel_sources_hash() -> str:
@@ -920,6 +920,34 @@ def run_config_records(args, local, link):
     return out
 
 
+def _capture_sample(C, req, every: int = 100):
+    """Capture slots for a seeded sample of ``req`` (``_sample``); other
+    requests are not captured.  Returns the capture buffer."""
+    sample = _sample(req["size"], req["kind"], every)
+    req["capture_offset"] = C.NO_CAPTURE
+    cap = 0
+    for i in sample:
+        req["capture_offset"][i] = cap
+        cap += int(req["out_size"][i] + 15) // 16 * 16
+    return np.zeros(max(cap, 16), dtype=np.uint8)
+
+
+def _add_checks(checks, req, res, src, capture):
+    for i in np.nonzero(req["capture_offset"] != np.uint64((1 << 64) - 1))[0]:
+        o, n, off = int(req["src_offset"][i]), int(req["size"][i]), int(req["capture_offset"][i])
+        checks.add(int(req["kind"][i]), src[o:o + n], int(req["out_size"][i]),
+                   capture[off:off + int(res["used_bytes"][i])])
+
+
+def _verified(args, checks):
+    """--verify: the CPU-baseline leg of a single-workload run -- the oracle
+    timed on the sampled units and compared with the GPU's outputs."""
+    if not args.verify or not checks.items:
+        return {}
+    cpu, ver = checks.run_oracle(len(os.sched_getaffinity(0)))
+    return {"cpu_baseline": cpu, "verified": ver}
+
+
 def run_stream_modes(args, local, kind, unit_bytes, n_units, modes, subset=None, unit=None):
     """One stream of jobs per mode through the job API; digests of every mode
     must agree.  ``unit(i)`` gives unit i's bytes (default: seeded uniform
@@ -960,6 +988,11 @@ def run_stream_modes(args, local, kind, unit_bytes, n_units, modes, subset=None,
         for i, o in outs[mode].items():
             if i in ref:
                 assert o == ref[i], f"mode {mode} differs from {modes[0]} on unit {i}"
+    if args.verify:  # every mode agrees with the first on these units; the first against the oracle
+        checks = Checks()
+        for i, o in ref.items():
+            checks.add(kind, unit(i), out_size, o, {"seg_bytes": 4096})
+        results["_verify"] = _verified(args, checks)
     return results
 
 
@@ -993,9 +1026,10 @@ def run_pipelined(args, ws, rank, local):
                            unit=lambda i: arena[int(offs[i]):int(offs[i]) + N])
     link = measure_link(torch, torch.device("cuda", local), 256 << 20)
     h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
+    ver = res.pop("_verify", {})
     for m in res.values():
         m["frac_of_link"] = round(m["GB_per_s"] / h2d, 4)
-    print(json.dumps({"metric": "end-to-end hashed GB/s through the job API", "unit": "GB/s",
+    print(json.dumps({"metric": "end-to-end hashed GB/s through the job API", "unit": "GB/s", **ver,
                       "workload": f"pipelined direct hashing, {U} units x {N >> 20} MiB (windows of a 2 GiB "
                                   f"pageable arena), S=4 KiB, {args.streams} streams, {args.batch_jobs} jobs per "
                                   f"batch; staged: {args.stage_threads} copy threads, {args.ring_jobs} ring jobs",
@@ -1023,6 +1057,7 @@ def run_serving(args, ws, rank, local):
                     max_batch_jobs=args.batch_jobs, max_batch_bytes=32 << 20,
                     flags=C.CRYSTAL_FLAG_GRAPHS)
     out = {}
+    checks = Checks()
     pinned = args.source == "pinned"
     if pinned:
         C.host_register(src)
@@ -1034,9 +1069,13 @@ def run_serving(args, ws, rank, local):
         for rate in rates:
             n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
             req, _ = S.make_trace(args.seed, n, rate, src.nbytes)
+            capture = _capture_sample(C, req) if args.verify else None
             s0 = ctx.stats()
-            st, res, wall = ctx.serve(src, req, copy_threads=args.copy_threads, source_pinned=pinned)
+            st, res, wall = ctx.serve(src, req, copy_threads=args.copy_threads, source_pinned=pinned,
+                                      capture=capture)
             s1 = ctx.stats()
+            if args.verify:
+                _add_checks(checks, req, res, src, capture)
             ok = res["status"] == 0
             lat = S.latency_ms(req, res)[ok]
             wait = (res["admit_ns"].astype(np.float64) - req["arrival_ns"].astype(np.float64))[ok] / 1e6
@@ -1066,7 +1105,7 @@ def run_serving(args, ws, rank, local):
                                   f"cap 64 MiB), 70/30 direct/sliding, {pool >> 30} GiB device pool, "
                                   f"{args.streams} streams, {args.batch_jobs} jobs per batch, "
                                   f"{args.copy_threads} staging threads",
-                      "rates_per_s": out, "data": "synthetic"}))
+                      "rates_per_s": out, "data": "synthetic", **_verified(args, checks)}))
 
 
 def run_batched(args, ws, rank, local):
@@ -1087,15 +1126,23 @@ def run_batched(args, ws, rank, local):
     U = args.units or 100_000
     req, _ = S.make_batch(args.seed, U, src.nbytes)
     pool = args.pool_bytes
+    capture = _capture_sample(C, req) if args.verify else None
+    checks = Checks()
     C.host_register(src)
     try:
-        sample = req[:min(U, args.tune_units)]
+        sample = req[:min(U, args.tune_units)].copy()
+        sample["capture_offset"] = C.NO_CAPTURE
         xf = C.CRYSTAL_FLAG_GRAPHS
-        best, table = A.tune(sample, src, device_pool_bytes=pool, device=local, flags=xf)
-        st, res, wall = A.run_batch(req, src, best, device_pool_bytes=pool, device=local, flags=xf)
+        shape, table = A.tune(sample, src, device_pool_bytes=pool, device=local, flags=xf)
+        best, gtable = A.tune_geometry(sample, src, shape, device_pool_bytes=pool, device=local, flags=xf)
+        st, res, wall = A.run_batch(req, src, best, device_pool_bytes=pool, device=local, flags=xf, capture=capture)
         C.check(st, "crystal_serve")
+        if args.verify:
+            _add_checks(checks, req, res, src, capture)
         plain_n = min(U, args.malloc_units)
-        stp, resp, wallp = A.run_batch(req[:plain_n], src, A.Setting(1, 1, 64 << 20), device_pool_bytes=pool,
+        plain_req = req[:plain_n].copy()
+        plain_req["capture_offset"] = C.NO_CAPTURE
+        stp, resp, wallp = A.run_batch(plain_req, src, A.Setting(1, 1, 64 << 20), device_pool_bytes=pool,
                                        device=local, submit_threads=1,
                                        flags=C.CRYSTAL_FLAG_NO_OVERLAP | C.CRYSTAL_FLAG_NO_BATCH)
         C.check(stp, "crystal_serve")
@@ -1111,10 +1158,10 @@ def run_batched(args, ws, rank, local):
                                   "CUDA graphs, autotuned",
                       "GB": round(total / GB, 2), "value": round(gbs, 3), "frac_of_link": round(gbs / h2d, 4),
                       "host_link": link, "chosen": best.as_dict(), "tuning_table": table,
-                      "tuning_sample_units": len(sample),
+                      "geometry_table": gtable, "tuning_sample_units": len(sample),
                       "plain_single_stream": {"units": plain_n,
                                               "GB_per_s": round(float(req["size"][:plain_n].sum()) / (wallp / 1e9) / GB, 3)},
-                      "data": "synthetic"}))
+                      "data": "synthetic", **_verified(args, checks)}))
 
 
 def run_overhead(args, ws, rank, local):
@@ -1232,6 +1279,9 @@ def main():
     ap.add_argument("--copy-threads", type=int, default=4,
                     help="serving: threads that bind or stage each admitted request and submit it")
     ap.add_argument("--c5-repeats", type=int, default=3)
+    ap.add_argument("--verify", action="store_true",
+                    help="single-workload runs (pipelined, serving, batched): time the oracle on a seeded sample "
+                         "of the units (at least 1%%, always the largest) and compare every output byte")
     ap.add_argument("--source", default="pinned", choices=["pinned", "pageable"])
     ap.add_argument("--depth", type=int, default=24, help="jobs in flight for staged / per-job-allocation modes")
     ap.add_argument("--malloc-units", type=int, default=512, help="units for the per-job-allocation modes")
