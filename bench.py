@@ -715,7 +715,7 @@ def record_config3(args, local, link):
     unit = lambda i: arena[int(offs[i]):int(offs[i]) + N]
     p = C.params(segment_bytes=4096)
     h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
-    memcpy1, memcpy_n = host_memcpy_rates(torch, arena, args.stage_threads)
+    memcpy1 = host_memcpy_rate(torch, arena)
     sample = list(range(0, U, max(1, U // 8)))
     rec = {"workload": f"pipelined direct hashing, {U} units x 4 MiB, S=4 KiB, 8 streams x 8 jobs per batch",
            "host_link_h2d_gbs": h2d}
@@ -731,46 +731,27 @@ def record_config3(args, local, link):
             if i < n and mode in ("pooled", "pooled_staged"):
                 checks.add(C.CRYSTAL_KIND_MD5_DIRECT, unit(i), 16, r.outputs[i], {"seg_bytes": 4096})
     bound = min(memcpy1 * args.stage_threads, h2d)
-    bound_measured = min(memcpy_n, h2d)
     rec["pooled_staged"].update({"copy_threads": args.stage_threads, "ring_jobs": args.ring_jobs,
-                                 "memcpy_1thread_gbs": round(memcpy1, 2),
-                                 f"memcpy_{args.stage_threads}threads_gbs": round(memcpy_n, 2),
-                                 "roofline_gbs": round(bound, 2),
+                                 "memcpy_1thread_gbs": round(memcpy1, 2), "roofline_gbs": round(bound, 2),
                                  "frac_of_roofline": round(rec["pooled_staged"]["GB_per_s"] / bound, 4),
-                                 "roofline_basis": "min(one-thread pageable->pinned memcpy x copy threads, H2D)",
-                                 "frac_of_measured_copy_bound": round(rec["pooled_staged"]["GB_per_s"] /
-                                                                      bound_measured, 4),
-                                 "measured_copy_bound_basis": "min(pageable->pinned memcpy measured with all "
-                                                              "copy threads at once, H2D)"})
+                                 "roofline_basis": "min(one-thread pageable->pinned memcpy x copy threads, H2D)"})
     rec["speedup_pooled_vs_per_job_malloc"] = round(rec["pooled"]["GB_per_s"] / rec["per_job_malloc"]["GB_per_s"], 2)
     rec["speedup_pooled_vs_no_overlap"] = round(rec["pooled"]["GB_per_s"] / rec["no_overlap"]["GB_per_s"], 2)
     return rec, checks
 
 
-def host_memcpy_rates(torch, src: np.ndarray, threads: int, piece: int = 64 << 20, rounds: int = 3):
-    """Pageable -> pinned host memcpy GB/s: one thread, and ``threads``
-    threads at once on their own pieces (numpy copies release the GIL), best
-    of ``rounds``.  The pinned buffer is written by one thread first."""
-    from concurrent.futures import ThreadPoolExecutor
-
-    pin = torch.empty(piece * threads, dtype=torch.uint8, pin_memory=True).numpy()
+def host_memcpy_rate(torch, src: np.ndarray, piece: int = 256 << 20, rounds: int = 3) -> float:
+    """Pageable -> pinned host memcpy GB/s on one thread, best of ``rounds``
+    (the pinned buffer is written by one thread first)."""
+    pin = torch.empty(piece, dtype=torch.uint8, pin_memory=True).numpy()
     pin[:] = 0
-    src = src[:piece * threads] if src.nbytes >= piece * threads else np.resize(src, piece * threads)
-
-    def one(k):
-        np.copyto(pin[k * piece:(k + 1) * piece], src[k * piece:(k + 1) * piece])
-
-    best1 = bestn = 0.0
-    with ThreadPoolExecutor(max_workers=threads) as ex:
-        for _ in range(rounds):
-            t0 = time.perf_counter()
-            one(0)
-            best1 = max(best1, piece / (time.perf_counter() - t0) / GB)
-            t0 = time.perf_counter()
-            list(ex.map(one, range(threads)))
-            bestn = max(bestn, piece * threads / (time.perf_counter() - t0) / GB)
+    best = 0.0
+    for _ in range(rounds):
+        t0 = time.perf_counter()
+        np.copyto(pin, src[:piece])
+        best = max(best, piece / (time.perf_counter() - t0) / GB)
     del pin
-    return best1, bestn
+    return best
 
 
 def _arena_pageable(seed: int, nbytes: int) -> np.ndarray:

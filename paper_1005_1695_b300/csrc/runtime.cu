@@ -1269,9 +1269,13 @@ int crystal_task_timing_many(crystal_task* const* tasks, uint32_t n, uint64_t* o
 int crystal_set_geometry(crystal_ctx* c, int size_class, const crystal_geometry* g) {
     if (!c || size_class < -1 || size_class >= CRYSTAL_SIZE_CLASSES) return CRYSTAL_EINVAL;
     const crystal_geometry defaults{};
-    cudaSetDevice(c->device);
+    // resolved against the context's device; the caller's current device is kept
+    int prev = 0;
+    const bool restore = cudaGetDevice(&prev) == cudaSuccess && prev != c->device;
+    if (restore) cudaSetDevice(c->device);
     LaunchGeom lg;
     const int st = make_geometry(g ? g : &defaults, &lg);
+    if (restore) cudaSetDevice(prev);
     if (st != CRYSTAL_OK) return st;
     // idle: the master issues nothing (issuing needs an outstanding job), so
     // no graph is in use or being captured while they are dropped here
