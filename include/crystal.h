@@ -589,6 +589,11 @@ int crystal_arena_alloc(crystal_arena* a, uint64_t bytes, uint64_t* offset);  /*
  * outputs and a batch's copies can be merged. */
 enum { CRYSTAL_ARENA_BEST_FIT = 0, CRYSTAL_ARENA_LOWEST = 1, CRYSTAL_ARENA_HIGHEST = 2 };
 int crystal_arena_alloc_at(crystal_arena* a, uint64_t bytes, int placement, uint64_t* offset);
+/* Allocate exactly [offset, offset + bytes rounded up): CRYSTAL_OK if that
+ * range is free, else EAGAIN (EINVAL for an offset off the alignment).  The
+ * runtime places a job's pinned input at the offset of its device input, so
+ * that jobs with adjacent inputs can be copied by one transfer. */
+int crystal_arena_alloc_exact(crystal_arena* a, uint64_t offset, uint64_t bytes);
 int crystal_arena_free(crystal_arena* a, uint64_t offset);
 uint64_t crystal_arena_used(crystal_arena* a);
 uint64_t crystal_arena_largest_free(crystal_arena* a);

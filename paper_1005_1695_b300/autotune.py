@@ -67,7 +67,7 @@ def size_classes(sizes: np.ndarray) -> np.ndarray:
 def _context(req: np.ndarray, setting: Setting, device_pool_bytes: int, device: int, flags: int) -> C.Context:
     max_in = int(req["size"].max())
     max_out = int(req["out_size"].max())
-    host_pool = int(req["out_size"].astype(np.int64).sum()) + len(req) * 512 + (64 << 20)
+    host_pool = int(req["out_size"].astype(np.int64).sum()) + len(req) * 768 + (64 << 20)
     ctx = C.Context(max_in_bytes=max_in, max_out_bytes=max_out, device_pool_bytes=device_pool_bytes,
                     host_pool_bytes=min(host_pool, 2 << 30), n_streams=setting.streams, device=device,
                     max_batch_jobs=setting.batch_jobs, max_batch_bytes=setting.batch_bytes, flags=flags)

@@ -208,6 +208,7 @@ def load() -> ctypes.CDLL:
         "crystal_arena_create": (ctypes.c_int, [_u64, _u64, ctypes.POINTER(_vp)]),
         "crystal_arena_alloc": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(_u64)]),
         "crystal_arena_alloc_at": (ctypes.c_int, [_vp, _u64, ctypes.c_int, ctypes.POINTER(_u64)]),
+        "crystal_arena_alloc_exact": (ctypes.c_int, [_vp, _u64, _u64]),
         "crystal_arena_free": (ctypes.c_int, [_vp, _u64]),
         "crystal_arena_used": (_u64, [_vp]),
         "crystal_arena_largest_free": (_u64, [_vp]),

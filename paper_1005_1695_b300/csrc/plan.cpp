@@ -130,6 +130,24 @@ int crystal_arena_alloc_at(crystal_arena* a, uint64_t bytes, int placement, uint
     return CRYSTAL_OK;
 }
 
+int crystal_arena_alloc_exact(crystal_arena* a, uint64_t offset, uint64_t bytes) {
+    if (!a || (offset & (a->align - 1))) return CRYSTAL_EINVAL;
+    const uint64_t want = align_up(bytes ? bytes : 1, a->align);
+    if (want < bytes || offset > a->size || want > a->size - offset) return CRYSTAL_EAGAIN;
+    std::lock_guard<std::mutex> lk(a->mu);
+    auto it = a->free_by_off.upper_bound(offset);  // the free block starting at or below offset
+    if (it == a->free_by_off.begin()) return CRYSTAL_EAGAIN;
+    --it;
+    const uint64_t off = it->first, len = it->second;
+    if (off + len < offset + want) return CRYSTAL_EAGAIN;
+    a->erase_free(it);
+    if (offset > off) a->insert_free(off, offset - off);
+    if (off + len > offset + want) a->insert_free(offset + want, off + len - offset - want);
+    a->live.emplace(offset, want);
+    a->used += want;
+    return CRYSTAL_OK;
+}
+
 int crystal_arena_alloc(crystal_arena* a, uint64_t bytes, uint64_t* offset) {
     return crystal_arena_alloc_at(a, bytes, CRYSTAL_ARENA_BEST_FIT, offset);
 }

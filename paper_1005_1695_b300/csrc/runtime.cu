@@ -936,7 +936,24 @@ int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scr
     t->out_cap = t->out_size = out_size;
     t->external_input = flags & CRYSTAL_TASK_EXTERNAL_INPUT;
     // inputs from the bottom of the arenas, outputs and scratch from the top
-    int st = t->external_input ? CRYSTAL_OK : alloc_host(c, in_size, &t->h_in, &t->h_in_off, CRYSTAL_ARENA_LOWEST);
+    int st = CRYSTAL_OK;
+    if (!t->external_input && c->pooled) {
+        // the pinned input at the same arena offset as the device input when
+        // that range is free: jobs with adjacent device inputs then have
+        // adjacent pinned inputs too, at one host-to-device distance, and a
+        // batch copies them in one transfer whatever order they were made in
+        st = alloc_device(c, in_size, &t->d_in, &t->d_in_off, CRYSTAL_ARENA_LOWEST);
+        if (st == CRYSTAL_OK) {
+            if (crystal_arena_alloc_exact(c->h_arena, t->d_in_off, in_size) == CRYSTAL_OK) {
+                t->h_in_off = t->d_in_off;
+                t->h_in = c->h_base + t->h_in_off;
+            } else {
+                st = alloc_host(c, in_size, &t->h_in, &t->h_in_off, CRYSTAL_ARENA_LOWEST);
+            }
+        }
+    } else if (!t->external_input) {
+        st = alloc_host(c, in_size, &t->h_in, &t->h_in_off, CRYSTAL_ARENA_LOWEST);
+    }
     if (st == CRYSTAL_OK) st = alloc_host(c, out_size, &t->h_out, &t->h_out_off, CRYSTAL_ARENA_HIGHEST);
     if (st == CRYSTAL_OK && t->external_input && c->pooled) {
         // an external input is copied on its own (never merged with its
@@ -953,7 +970,7 @@ int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scr
             }
         }
     } else {
-        if (st == CRYSTAL_OK) st = alloc_device(c, in_size, &t->d_in, &t->d_in_off, CRYSTAL_ARENA_LOWEST);
+        if (st == CRYSTAL_OK && !t->d_in) st = alloc_device(c, in_size, &t->d_in, &t->d_in_off, CRYSTAL_ARENA_LOWEST);
         if (st == CRYSTAL_OK) st = alloc_device(c, out_size, &t->d_out, &t->d_out_off, CRYSTAL_ARENA_HIGHEST);
         if (st == CRYSTAL_OK && scratch_bytes) {
             st = alloc_device(c, scratch_bytes, &t->d_reserved, &t->d_reserved_off);

@@ -164,8 +164,24 @@ def test_arena_placement_matches_a_model(C):
             model_free(o)
         else:
             n = int(rng.integers(1, 1 << 19)) if rng.random() < 0.9 else int(rng.integers(1, 600))
-            placement = int(rng.integers(0, 3))
+            placement = int(rng.integers(0, 4))
             want = (n + 255) // 256 * 256
+            if placement == 3:  # exactly at an offset: inside one free block, or refused
+                at = int(rng.integers(0, (32 << 20) // 256)) * 256
+                holder = [(fo, fn) for fo, fn in free.items() if fo <= at and at + want <= fo + fn]
+                st = L.crystal_arena_alloc_exact(h, at, n)
+                if not holder:
+                    assert st == C.CRYSTAL_EAGAIN
+                    continue
+                assert st == 0
+                fo, fn = holder[0]
+                del free[fo]
+                if at > fo:
+                    free[fo] = at - fo
+                if fo + fn > at + want:
+                    free[at + want] = fo + fn - at - want
+                live[at] = want
+                continue
             expect = model_alloc(want, placement)
             st, o = _alloc_at(L, h, n, placement)
             if expect is None:
@@ -174,6 +190,8 @@ def test_arena_placement_matches_a_model(C):
                 assert st == 0 and o == expect, (step, placement, n, o, expect)
                 live[o] = want
         assert L.crystal_arena_largest_free(h) == max(free.values(), default=0)
+    assert L.crystal_arena_alloc_exact(h, 100, 10) == C.CRYSTAL_EINVAL  # off the 256-byte alignment
+    assert L.crystal_arena_alloc_exact(h, 32 << 20, 1) == C.CRYSTAL_EAGAIN  # past the end
     L.crystal_arena_destroy(h)
 
 

@@ -525,3 +525,27 @@ def test_launch_geometry_per_size_class_bit_exact(C, oracle_mod, graphs):
         assert L.crystal_set_geometry(ctx.handle, 3, None) == C.CRYSTAL_EINVAL
         ctx.set_geometry(-1, None)
         assert ctx.get_geometry(2).seg_threads == 128
+
+
+def test_adjacent_inputs_merge_into_one_copy_in_any_order(C, oracle_mod):
+    """Jobs created one after another get adjacent pinned inputs at the same
+    arena offsets as their device inputs; submitted in reverse order in one
+    batch, their inputs still reach the GPU in one transfer (direct digests are
+    written in place, so the batch has no copy back), and every digest is the
+    oracle's."""
+    from paper_1005_1695_b300 import inputs
+
+    n, k = 65536 + 1000, 16
+    with C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 10, device_pool_bytes=64 << 20,
+                   host_pool_bytes=64 << 20, n_streams=1, max_batch_jobs=k, max_batch_bytes=64 << 20) as ctx:
+        tasks = [ctx.task_create(n, 16) for _ in range(k)]
+        data = [inputs.uniform_unit(21, i, n) for i in range(k)]
+        for t, d in zip(tasks, data):
+            t.h_in[:] = d
+        before = ctx.stats().copies_dma
+        assert ctx.submit_many(list(reversed(tasks)), DIRECT, C.params()) == C.CRYSTAL_OK
+        assert ctx.wait_many(tasks, 30 * SEC) == C.CRYSTAL_OK
+        s = ctx.stats()
+        assert s.batches_launched == 1 and s.copies_dma - before == 1
+        for t, d in zip(tasks, data):
+            assert t.output()[:16] == oracle_mod.direct(d, 4096)
