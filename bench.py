@@ -888,12 +888,26 @@ def record_config5(args, local, link):
     return rec, checks
 
 
+def record_overhead(args, local, link):
+    sizes = [4096, 65536, 1 << 20, 16 << 20]
+    return {"metric": "framework overhead per job (dummy kernel, equal bytes in and out), microseconds",
+            "sizes": measure_overhead(local, sizes, 30),
+            "paper_context": "slightly under 70 us per job on a 9800 GX2 host (Section 5.1)"}, Checks()
+
+
+def record_streamlen(args, local, link):
+    return {"metric": "GB/s per stream length, 1 MiB direct-hash jobs (Figure 8's shape)",
+            "stream_lengths": measure_streamlen(local, args.seed, (1, 2, 4, 10), 3)}, Checks()
+
+
 def run_config_records(args, local, link):
     """Records of configurations 1, 3, 4 and 5 (GPU part); returns
     {name: (record, checks)}."""
     out = {}
     for name, fn in (("config1_plain", record_config1), ("config3_pipelined", record_config3),
-                     ("config4_batched", record_config4), ("config5_served", record_config5)):
+                     ("config4_batched", record_config4), ("config5_served", record_config5),
+                     ("sha1_sliding", record_sha1), ("overhead_per_job", record_overhead),
+                     ("stream_length", record_streamlen)):
         t0 = time.perf_counter()
         rec, checks = fn(args, local, link)
         rec["wall_s"] = round(time.perf_counter() - t0, 1)
@@ -1145,20 +1159,16 @@ def run_batched(args, ws, rank, local):
                       "data": "synthetic", **_verified(args, checks)}))
 
 
-def run_overhead(args, ws, rank, local):
+def measure_overhead(local: int, sizes, reps: int) -> dict:
     """Framework overhead of one job (Section 5.1, Figure 5): copy in n bytes,
     dummy kernel, copy out n bytes, issued directly vs through the job
-    runtime; the difference is the framework's own cost."""
-    import ctypes
-
+    runtime; the difference is the framework's own cost (medians)."""
     import torch
 
     from paper_1005_1695_b300 import crystal as C
 
     torch.cuda.set_device(local)
     L = C.load()
-    sizes = [int(x) for x in args.sizes.split(",")]
-    reps = max(30, args.steps)
     stream = torch.cuda.Stream()
     out = {}
     with C.Context(max_in_bytes=max(sizes), max_out_bytes=max(sizes), device_pool_bytes=2 * max(sizes) + (64 << 20),
@@ -1175,7 +1185,7 @@ def run_overhead(args, ws, rank, local):
                         "crystal_direct_job")
                 if i >= 5:
                     raw.append(time.perf_counter() - t0)
-            fw, disp, run, ret = [], [], [], []
+            fw, disp, run = [], [], []
             for i in range(reps + 5):
                 t0 = time.perf_counter()
                 C.check(t.submit(C.CRYSTAL_KIND_NOP), "submit")
@@ -1192,14 +1202,21 @@ def run_overhead(args, ws, rank, local):
                            "overhead_pct": round(100 * (f - r) / f, 1),
                            "submit_to_dispatch_us": round(float(np.median(disp)), 1),
                            "dispatch_to_done_us": round(float(np.median(run)), 1)}
+    return out
+
+
+def run_overhead(args, ws, rank, local):
+    sizes = [int(x) for x in args.sizes.split(",")]
+    reps = max(30, args.steps)
     print(json.dumps({"metric": "framework overhead per job (dummy kernel, equal bytes in and out)",
-                      "unit": "us", "sizes": out, "reps": reps,
+                      "unit": "us", "sizes": measure_overhead(local, sizes, reps), "reps": reps,
                       "paper_context": "slightly under 70 us per job on a 9800 GX2 host (Section 5.1)"}))
 
 
-def run_streamlen(args, ws, rank, local):
+def measure_streamlen(local: int, seed: int, lengths, reps: int) -> dict:
     """Streams of 1..10 jobs of 1 MiB (direct hashing, Figure 8's shape): the
-    plain form against no-overlap and pooled + overlap, per stream length."""
+    plain form against no-overlap and pooled + overlap, per stream length
+    (median of ``reps`` streams each)."""
     import torch
 
     from paper_1005_1695_b300 import crystal as C
@@ -1210,21 +1227,108 @@ def run_streamlen(args, ws, rank, local):
     C.load()
     N = 1 << 20
     p = C.params()
-
-    def unit(i):
-        return inputs.uniform_unit(args.seed, i, N)
-
+    data = [inputs.uniform_unit(seed, i, N) for i in range(max(lengths))]
     out = {}
-    for L in range(1, 11):
+    for L in lengths:
         row = {}
         for mode in ("plain", "no_overlap", "pooled"):
-            runs = [S.run_stream(mode, unit, L, N, C.CRYSTAL_KIND_MD5_DIRECT, p, 16, streams=8, batch_jobs=8,
-                                 depth=24, device=local).seconds for _ in range(max(3, args.steps))]
+            runs = [S.run_stream(mode, lambda i: data[i], L, N, C.CRYSTAL_KIND_MD5_DIRECT, p, 16, streams=8,
+                                 batch_jobs=8, depth=24, device=local).seconds for _ in range(reps)]
             row[mode] = round(L * N / float(np.median(runs)) / GB, 3)
         row["speedup_pooled_vs_plain"] = round(row["pooled"] / row["plain"], 2)
         out[str(L)] = row
+    return out
+
+
+def run_streamlen(args, ws, rank, local):
     print(json.dumps({"metric": "GB/s per stream length, 1 MiB direct-hash jobs", "unit": "GB/s",
-                      "stream_lengths": out, "data": "synthetic"}))
+                      "stream_lengths": measure_streamlen(local, args.seed, range(1, 11), max(3, args.steps)),
+                      "data": "synthetic"}))
+
+
+def record_sha1(args, local, link):
+    """The headline sliding workload with SHA-1, the hash of the paper's own
+    runs (Section 5.2): device-resident kernel chain and the job API, the
+    window kernel against its ALU-pipe bound (432 ALU-only operations per
+    window at the measured single-pipe rate)."""
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+
+    dev = torch.device("cuda", local)
+    U, N = 256, 1 << 20
+    KIND = C.CRYSTAL_KIND_SHA1_SLIDING
+    p = C.params(window_bytes=20, mask=0x1FFF, target=0x1FFF, chunk_segment_bytes=4096)
+    out_size = C.sliding_out_bytes(N, args.max_chunks, KIND)
+    host = sliding_workload(args.seed, U, N)
+    d_in = torch.from_numpy(host).to(dev)
+    batch = C.DeviceBatch(d_in, [u * N for u in range(U)], [N] * U, [KIND] * U, p, out_sizes=[out_size] * U)
+    desc_host = torch.from_numpy(batch.host_desc).pin_memory()
+    stream = torch.cuda.Stream(device=dev)
+    steps = 5
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps + 2)]
+    for i in range(steps + 2):
+        with torch.cuda.stream(stream):
+            batch.d_desc.copy_(desc_host, non_blocking=True)
+            ev[i][0].record(stream)
+            batch.launch_sliding_windows(stream)
+            ev[i][1].record(stream)
+            batch.launch_sliding_chunks(stream)
+            batch.launch_sliding_digests(stream)
+            ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    assert batch.device_status() == 0
+    win_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev[2:]]))
+    step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in ev[2:]]))
+    got = batch.outputs()
+    # the job API: two job sets in turn, as the headline e2e leg
+    ctx = C.Context(max_in_bytes=N, max_out_bytes=out_size, device_pool_bytes=2 * U * (N + 2 * out_size) + (256 << 20),
+                    host_pool_bytes=2 * U * (N + out_size + 4096) + (16 << 20), n_streams=args.streams,
+                    max_batch_jobs=args.batch_jobs, max_batch_bytes=args.batch_jobs * N, device=local,
+                    flags=C.CRYSTAL_FLAG_GRAPHS)
+    try:
+        sets = []
+        for _ in range(2):
+            tasks = [ctx.task_create(N, out_size) for _ in range(U)]
+            for u, t in enumerate(tasks):
+                t.h_in[:] = host[u * N:(u + 1) * N]
+            sets.append((tasks, ctx.task_array(tasks)))
+        for k in range(2):  # warm-up: graphs captured
+            C.check(ctx.submit_many(sets[k][1], KIND, p), "submit_many")
+        for k in range(2):
+            C.check(ctx.wait_many(sets[k][1], 60_000_000_000), "wait_many")
+        t0 = time.perf_counter()
+        C.check(ctx.submit_many(sets[0][1], KIND, p), "submit_many")
+        for i in range(steps):
+            if i + 1 < steps:
+                C.check(ctx.submit_many(sets[(i + 1) % 2][1], KIND, p), "submit_many")
+            C.check(ctx.wait_many(sets[i % 2][1], 60_000_000_000), "wait_many")
+        e2e_s = time.perf_counter() - t0
+        job_out = [sets[0][0][u].output() for u in range(U)]
+    finally:
+        ctx.shutdown()
+    checks = Checks()
+    prm = dict(window=20, mask=0x1FFF, target=0x1FFF, chunk_seg_bytes=4096)
+    for u in range(0, U, 16):
+        n_chunks = int.from_bytes(got[u][:4], "little")
+        used = 8 + 4 * (N // 32) + 24 * n_chunks
+        assert job_out[u][:used] == got[u][:used], "job output differs from the device batch output"
+        checks.add(KIND, host[u * N:(u + 1) * N], out_size, got[u][:used], prm)
+    windows = U * (N - 19)
+    alu_pipe = link.get("_alu_pipe_Tops", 0.0)
+    bound_wps = alu_pipe * 1e12 / 432 if alu_pipe else None
+    h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
+    rec = {"workload": f"sliding-window SHA-1, {U} units x 1 MiB, w=20, mask=target=0x1FFF, chunk direct hash S=4 KiB",
+           "device_resident_GB_per_s": round(U * N / step_ms / 1e6, 3),
+           "window_kernel_ms": round(win_ms, 4), "windows_per_s_G": round(windows / win_ms / 1e6, 2),
+           "e2e_GB_per_s": round(steps * U * N / e2e_s / GB, 3), "e2e_frac_of_h2d": round(steps * U * N / e2e_s / GB / h2d, 4)}
+    if bound_wps:
+        rec.update({"alu_pipe_bound_windows_per_s_G": round(bound_wps / 1e9, 2),
+                    "frac_of_alu_pipe_bound": round(windows / win_ms * 1e3 / bound_wps, 4),
+                    "alu_pipe_bound_basis": "measured single-pipe rate (LOP3 chains) / 432 ALU-only operations per "
+                                            "window (per step two rotates and the logic op, per schedule word two "
+                                            "XORs and a rotate)"})
+    return rec, checks
 
 
 def main():
@@ -1328,13 +1432,14 @@ def main():
     args.c5_rates = [float(r) for r in args.c5_rates.split(",")] if isinstance(args.c5_rates, str) else args.c5_rates
     out = run_ours(args, ws, rank, local)
     gpu_results = out.pop("_gpu_results")
-    link = out["host_link"]
+    link = dict(out["host_link"])
+    link["_alu_pipe_Tops"] = out["roofline"]["pipes_measured_Tops"]["lop3"]  # for the SHA-1 record's bound
     records = run_config_records(args, local, link) if (args.configs and rank == 0) else {}
     if rank == 0:
         if records:
             out["configs"] = {}
             for name, (rec, checks) in records.items():
-                if not args.no_cpu_baseline:
+                if not args.no_cpu_baseline and checks.items:
                     rec["cpu_baseline"], rec["verified"] = checks.run_oracle(cores)
                 out["configs"][name] = rec
         if not args.no_cpu_baseline:

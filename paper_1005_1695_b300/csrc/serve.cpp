@@ -118,7 +118,7 @@ void on_done(crystal_task* t, int status, void* user) {
     if (used && r.capture_offset != UINT64_MAX && s->capture && r.capture_offset <= s->capture_bytes &&
         used <= s->capture_bytes - r.capture_offset)
         memcpy(s->capture + r.capture_offset, out, used);
-    crystal_task_release(t);  // freed by the master once this callback returns
+    crystal_task_release(t);  // buffers back to the pools now (room for the next admission); handle later
     s->finish(i, status);
 }
 
