@@ -260,3 +260,35 @@ def test_config5_served_lognormal_with_capped_requests(C, config5, pinned):
                                            source_pinned=pinned)
         assert st1 == C.CRYSTAL_OK
         assert cap1[:int(res1["used_bytes"][0])].tobytes() == mix[i], i
+
+
+# ---- the headline workload with SHA-1 (the hash of the paper's own runs) ----------
+
+def test_config2_sha1_every_unit(C, oracle_mod):
+    """Configuration 2's 256 x 1 MiB units hashed with SHA-1 (Section 5.2's hash):
+    the device-resident launches the benchmark times, every unit against the
+    oracle."""
+    import torch
+
+    from paper_1005_1695_b300 import inputs
+
+    U, N = 256, 1 << 20
+    SHA1_SLIDING = C.CRYSTAL_KIND_SHA1_SLIDING
+    pool = inputs.dedup_pool(2)
+    host = np.empty(U * N, dtype=np.uint8)
+    for u in range(U):
+        inputs.dedup_unit(2, u, N, pool=pool, out=host[u * N:(u + 1) * N])
+    p = C.params(window_bytes=20, mask=0x1FFF, target=0x1FFF, chunk_segment_bytes=4096)
+    out_size = C.sliding_out_bytes(N, 1024, SHA1_SLIDING)
+    d_in = torch.from_numpy(host).cuda()
+    b = C.DeviceBatch(d_in, [u * N for u in range(U)], [N] * U, [SHA1_SLIDING] * U, p, out_sizes=[out_size] * U)
+    b.launch_sliding_windows()
+    b.launch_sliding_chunks()
+    b.launch_sliding_digests()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    got = b.outputs()
+    want = _oracle_many(oracle_mod, [(SHA1_SLIDING, host[u * N:(u + 1) * N], out_size, p) for u in range(U)])
+    for u in range(U):
+        assert want[u][0] == 0
+        _assert_same(SHA1_SLIDING, N, got[u], want[u][1], f"unit {u}")
