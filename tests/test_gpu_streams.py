@@ -1,5 +1,6 @@
 """Job streams in every form the runtime offers (pooled / staged / no overlap /
 per-job allocation / plain), bit-exact against the CPU oracle."""
+import numpy as np
 import pytest
 
 from helpers import first_difference, same_result
