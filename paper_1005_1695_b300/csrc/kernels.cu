@@ -911,6 +911,8 @@ const LaunchGeom* default_geometry() {
 // Passed to every hashing kernel as its `one` argument (see md5::add_on_fma).
 uint32_t g_one = 1;
 
+// After each launch: a launch error stops the sequence, so a kernel that
+// depends on a failed one is never queued behind it.
 int launched(int kernels) {
     if (cudaGetLastError() != cudaSuccess) return CRYSTAL_EDEVICE;
     if (!tl_capturing) g_kernel_launches.fetch_add((uint64_t)kernels, std::memory_order_relaxed);
@@ -988,8 +990,9 @@ int launch_direct_segments(crystal_batch* b, cudaStream_t s, const LaunchGeom* g
     const LaunchGeom* g = resolve(geom);
     if (!g) return CRYSTAL_EDEVICE;
     launch_seg<MD5Hash>(g, g->seg_blocks, b, s);
+    if (launched(1) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     launch_seg<SHA1Hash>(g, g->seg_sha1_blocks, b, s);
-    return launched(2);
+    return launched(1);
 }
 
 int launch_direct_outer(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom) {
@@ -1004,25 +1007,29 @@ int launch_sliding_windows(crystal_batch* b, cudaStream_t s, const LaunchGeom* g
     if (!g) return CRYSTAL_EDEVICE;
     if (g->win20_wide) kWin20Wide<<<g->win20_blocks, kWinThreads, 0, s>>>(b, g_one);
     else kWin20<<<g->win20_blocks, kWinThreads, 0, s>>>(b, g_one);
+    if (launched(1) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     kWinAny<<<g->win_blocks, kWinThreads, 0, s>>>(b, g_one);
+    if (launched(1) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     kWinSha1<<<g->win_sha1_blocks, kWinThreads, 0, s>>>(b, g_one);
-    return launched(3);
+    return launched(1);
 }
 
 int launch_sliding_chunks(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom) {
     const LaunchGeom* g = resolve(geom);
     if (!g) return CRYSTAL_EDEVICE;
     k_sliding_chunks<<<g->unit_blocks, kChunkThreads, 0, s>>>(b);
+    if (launched(1) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     k_chunk_seg_scan<<<1, kScanThreads, 0, s>>>(b);
-    return launched(2);
+    return launched(1);
 }
 
 int launch_sliding_digests(crystal_batch* b, cudaStream_t s, const LaunchGeom* geom) {
     const LaunchGeom* g = resolve(geom);
     if (!g) return CRYSTAL_EDEVICE;
     k_chunk_segments<<<g->digest_blocks, kChunkSegThreads, 0, s>>>(b, g_one);
+    if (launched(1) != CRYSTAL_OK) return CRYSTAL_EDEVICE;
     k_chunk_outer<<<g->unit_blocks, kDigestThreads, 0, s>>>(b, g_one);
-    return launched(2);
+    return launched(1);
 }
 
 // ---- direct hashing that allocates nothing ------------------------------------
