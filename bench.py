@@ -62,8 +62,8 @@ INT_LANES_PER_SM = 128  # 4 schedulers x one 32-lane instruction per clock
 # DRAM bytes (read + write) of the window kernel per 1 MiB sliding unit, from one
 # ncu capture of 160 units (traffic grows with the units processed), valid only
 # for the kernel sources it was taken on (checked by hash; otherwise null).
-WINDOW_TRAFFIC_PER_UNIT = (168.187904e6 + 14.510336e6) / 160
-WINDOW_TRAFFIC_SOURCES = "4fb2be82d58950e7"
+WINDOW_TRAFFIC_PER_UNIT = (168.245760e6 + 14.485248e6) / 160
+WINDOW_TRAFFIC_SOURCES = "3c7f11974f75cdc9"
 
 
 def _kernel_sources_hash() -> str:

@@ -239,8 +239,9 @@ int crystal_task_timing(crystal_task* task, uint64_t* submit_ns, uint64_t* dispa
  * then partly written). */
 int crystal_task_timing_many(crystal_task* const* tasks, uint32_t n, uint64_t* out);
 
-/* The configuration a context runs with (defaults filled in; n_streams is 1
- * under CRYSTAL_FLAG_NO_OVERLAP). */
+/* The configuration a context runs with, written to *out (defaults filled
+ * in; n_streams is 1 under CRYSTAL_FLAG_NO_OVERLAP, max_batch_jobs 1 under
+ * CRYSTAL_FLAG_NO_BATCH or CRYSTAL_FLAG_NO_OVERLAP).  EINVAL for NULL. */
 int crystal_get_config(crystal_ctx* ctx, crystal_config* out);
 
 /* Launch geometry of the hashing kernels (the paper has no counterpart: it
@@ -266,7 +267,9 @@ typedef struct crystal_geometry {
  * the class's captured graphs are dropped and re-captured on next use. */
 int crystal_set_geometry(crystal_ctx* ctx, int size_class, const crystal_geometry* g);
 
-/* The geometry a class runs with, resolved (CTAs per SM as launched). */
+/* The geometry class size_class (0..2) runs with, resolved (threads per CTA
+ * and CTAs per SM as launched, register budget 32 or 64), written to *out.
+ * EINVAL for NULL or a bad class. */
 int crystal_get_geometry(crystal_ctx* ctx, int size_class, crystal_geometry* out);
 
 /* Counters of a context. */
