@@ -838,15 +838,35 @@ def record_config5(args, local, link):
     ctx = C.Context(max_in_bytes=64 << 20, max_out_bytes=C.sliding_out_bytes(64 << 20, 4 * 8192 + 64),
                     device_pool_bytes=pool, host_pool_bytes=1 << 30, n_streams=args.streams, device=local,
                     max_batch_jobs=args.batch_jobs, max_batch_bytes=32 << 20, flags=C.CRYSTAL_FLAG_GRAPHS)
+    ring = dict(ring_bytes=args.input_ring, ring_max_request=args.ring_max)
     rec = {"workload": "open-loop Poisson requests, lognormal sizes (median 256 KiB, sigma 1.5, cap 64 MiB), "
                        f"70/30 direct/sliding, {pool >> 30} GiB device pool, {args.streams} streams, "
-                       f"{args.batch_jobs} jobs per batch, inputs read in place from a page-locked arena",
+                       f"{args.batch_jobs} jobs per batch, inputs read in place from a page-locked arena, "
+                       + (f"requests up to {args.ring_max >> 10} KiB copied into a {args.input_ring >> 20} MiB "
+                          "input ring (merged transfers)" if args.input_ring else "no input ring"),
            "rates_per_s": {}}
     checks = Checks()
     C.host_register(src)
+
+    def median_run(req, capture_bytes, **kw):
+        # the host side of serving (admission, staging threads, the master)
+        # shares the machine's cores with other work: each rate runs three times
+        # and the run with the median throughput is reported, all three listed
+        runs = []
+        for _ in range(args.c5_repeats):
+            capture = np.zeros(capture_bytes, dtype=np.uint8)
+            s0 = ctx.stats()
+            st, res, wall = ctx.serve(src, req, capture=capture, copy_threads=args.copy_threads,
+                                      source_pinned=True, **kw)
+            C.check(st, "crystal_serve")
+            runs.append((wall, res, capture, int(ctx.stats().copies_dma - s0.copies_dma)))
+        order = sorted(runs, key=lambda r: r[0])
+        return order[len(order) // 2], [r[0] for r in runs]
+
     try:
         warm, _ = S.make_trace(args.seed + 1, 2000, 10000.0, src.nbytes)
-        C.check(ctx.serve(src, warm, copy_threads=args.copy_threads, source_pinned=True)[0], "crystal_serve")
+        C.check(ctx.serve(src, warm, copy_threads=args.copy_threads, source_pinned=True, **ring)[0],
+                "crystal_serve")
         for rate in args.c5_rates:
             n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
             req, _ = S.make_trace(args.seed, n, rate, src.nbytes)
@@ -856,28 +876,27 @@ def record_config5(args, local, link):
             for i in sample:
                 req["capture_offset"][i] = cap
                 cap += int(req["out_size"][i] + 15) // 16 * 16
-            # the host side of serving (admission, staging threads, the master)
-            # shares the machine's cores with other work: each rate runs three times
-            # and the run with the median throughput is reported, all three listed
-            runs = []
-            for _ in range(args.c5_repeats):
-                capture = np.zeros(cap, dtype=np.uint8)
-                st, res, wall = ctx.serve(src, req, capture=capture, copy_threads=args.copy_threads,
-                                          source_pinned=True)
-                C.check(st, "crystal_serve")
-                runs.append((wall, res, capture))
-            runs.sort(key=lambda r: r[0])
-            wall, res, capture = runs[len(runs) // 2]
+            (wall, res, capture, copies), walls = median_run(req, cap, **ring)
             lat = S.latency_ms(req, res)
             total = int(req["size"].sum())
             span = float(req["arrival_ns"][-1]) / 1e9
             gbs = total / (wall / 1e9) / GB
-            rec["rates_per_s"][str(int(rate))] = {
+            entry = {
                 "requests": n, "offered_GB_per_s": round(total / max(span, 1e-9) / GB, 3),
                 "GB_per_s": round(gbs, 3), "frac_of_link": round(gbs / h2d, 4),
                 "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                                "p99": round(float(np.percentile(lat, 99)), 3)},
-                "runs_GB_per_s": [round(total / (r[0] / 1e9) / GB, 3) for r in runs]}
+                "runs_GB_per_s": [round(total / (w / 1e9) / GB, 3) for w in walls], "dma_copies": copies}
+            if args.input_ring and rate == max(args.c5_rates):
+                # the same requests with every input read in place (one transfer each)
+                (w0, res0, _, copies0), walls0 = median_run(req, cap)
+                lat0 = S.latency_ms(req, res0)
+                entry["without_input_ring"] = {
+                    "GB_per_s": round(total / (w0 / 1e9) / GB, 3),
+                    "latency_ms": {"p50": round(float(np.percentile(lat0, 50)), 3),
+                                   "p99": round(float(np.percentile(lat0, 99)), 3)},
+                    "runs_GB_per_s": [round(total / (w / 1e9) / GB, 3) for w in walls0], "dma_copies": copies0}
+            rec["rates_per_s"][str(int(rate))] = entry
             for i in sample:
                 o, nb, off = int(req["src_offset"][i]), int(req["size"][i]), int(req["capture_offset"][i])
                 checks.add(int(req["kind"][i]), src[o:o + nb], int(req["out_size"][i]),
@@ -1060,14 +1079,15 @@ def run_serving(args, ws, rank, local):
         # untimed warm-up: each stream slot captures its graphs and the pools
         # are touched before the first measured rate
         warm, _ = S.make_trace(args.seed + 1, 2000, rates[0], src.nbytes)
-        C.check(ctx.serve(src, warm, copy_threads=args.copy_threads, source_pinned=pinned)[0], "crystal_serve")
+        C.check(ctx.serve(src, warm, copy_threads=args.copy_threads, source_pinned=pinned,
+                          ring_bytes=args.input_ring, ring_max_request=args.ring_max)[0], "crystal_serve")
         for rate in rates:
             n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
             req, _ = S.make_trace(args.seed, n, rate, src.nbytes)
             capture = _capture_sample(C, req) if args.verify else None
             s0 = ctx.stats()
             st, res, wall = ctx.serve(src, req, copy_threads=args.copy_threads, source_pinned=pinned,
-                                      capture=capture)
+                                      capture=capture, ring_bytes=args.input_ring, ring_max_request=args.ring_max)
             s1 = ctx.stats()
             if args.verify:
                 _add_checks(checks, req, res, src, capture)
@@ -1099,7 +1119,9 @@ def run_serving(args, ws, rank, local):
                       "workload": "open-loop Poisson requests, lognormal sizes (median 256 KiB, sigma 1.5, "
                                   f"cap 64 MiB), 70/30 direct/sliding, {pool >> 30} GiB device pool, "
                                   f"{args.streams} streams, {args.batch_jobs} jobs per batch, "
-                                  f"{args.copy_threads} staging threads",
+                                  f"{args.copy_threads} staging threads, "
+                                  + (f"requests up to {args.ring_max >> 10} KiB through a {args.input_ring >> 20} MiB "
+                                     "input ring" if args.input_ring else "no input ring"),
                       "rates_per_s": out, "data": "synthetic", **_verified(args, checks)}))
 
 
@@ -1364,6 +1386,10 @@ def main():
     ap.add_argument("--copy-threads", type=int, default=4,
                     help="serving: threads that bind or stage each admitted request and submit it")
     ap.add_argument("--c5-repeats", type=int, default=3)
+    ap.add_argument("--input-ring", type=int, default=256 << 20,
+                    help="served requests: bytes of the input ring for small requests (0: none)")
+    ap.add_argument("--ring-max", type=int, default=256 << 10,
+                    help="served requests: largest request staged through the input ring")
     ap.add_argument("--verify", action="store_true",
                     help="single-workload runs (pipelined, serving, batched): time the oracle on a seeded sample "
                          "of the units (at least 1%%, always the largest) and compare every output byte")

@@ -455,7 +455,12 @@ int crystal_launch_batch(const crystal_batch* batch_dev, void* stream);
  * CRYSTAL_SERVE_ARRIVAL_ORDER admits strictly in arrival order instead.
  * Copy threads stage the request's bytes from
  * `source` into the job's pinned input (or, with CRYSTAL_SERVE_SOURCE_PINNED,
- * bind the job's input to them) and submit it; the master thread
+ * bind the job's input to them) and submit it; with ring_bytes > 0, requests
+ * of at most ring_max_request bytes are instead copied into an input ring
+ * (ring_bytes of pinned host pool and ring_bytes of device pool, reserved for
+ * the call; EAGAIN / ENOMEM if the pools cannot hold it) in admission order,
+ * so neighbouring requests' copies merge into one DMA transfer -- a request
+ * that finds the ring full gets buffers of its own as before; the master thread
  * batches whatever is outstanding (continuous batching).  On completion the
  * used output bytes of a request with capture_offset != UINT64_MAX are copied
  * to capture + capture_offset (if they fit), and the job is released.  A
@@ -495,6 +500,9 @@ typedef struct crystal_serve_config {
     uint64_t capture_bytes;
     uint64_t bypass_ns;                         /* how long later requests may pass a blocked oldest
                                                    request; default (0) 2 ms */
+    uint64_t ring_bytes;                        /* input ring for small requests; 0 = none */
+    uint64_t ring_max_request;                  /* largest request staged in the ring; default (0)
+                                                   256 KiB */
 } crystal_serve_config;
 
 int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, const crystal_request* requests,

@@ -139,7 +139,8 @@ class crystal_stream_config(ctypes.Structure):
 class crystal_serve_config(ctypes.Structure):
     _fields_ = [("copy_threads", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("direct_params", ctypes.c_void_p), ("sliding_params", ctypes.c_void_p),
-                ("capture", ctypes.c_void_p), ("capture_bytes", ctypes.c_uint64), ("bypass_ns", ctypes.c_uint64)]
+                ("capture", ctypes.c_void_p), ("capture_bytes", ctypes.c_uint64), ("bypass_ns", ctypes.c_uint64),
+                ("ring_bytes", ctypes.c_uint64), ("ring_max_request", ctypes.c_uint64)]
 
 _lib = None
 _u64 = ctypes.c_uint64
@@ -391,12 +392,14 @@ class Context:
     def serve(self, source: np.ndarray, requests: np.ndarray, direct: Optional[crystal_hash_params] = None,
               sliding: Optional[crystal_hash_params] = None, capture: Optional[np.ndarray] = None,
               copy_threads: int = 4, source_pinned: bool = False, arrival_order: bool = False,
-              bypass_ns: int = 0):
+              bypass_ns: int = 0, ring_bytes: int = 0, ring_max_request: int = 0):
         """crystal_serve: play ``requests`` (REQUEST_DTYPE, arrival order)
         against this context.  ``arrival_order`` admits strictly in arrival
         order; otherwise later requests that fit may pass a blocked oldest one
-        for ``bypass_ns`` (0: the library's default).  Returns (status,
-        results, wall_ns)."""
+        for ``bypass_ns`` (0: the library's default).  ``ring_bytes`` > 0
+        stages requests of at most ``ring_max_request`` bytes (0: the
+        library's default) through an input ring so that their copies merge.
+        Returns (status, results, wall_ns)."""
         src = np.ascontiguousarray(source, dtype=np.uint8)
         req = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
         res = np.zeros(len(req), dtype=RESULT_DTYPE)
@@ -405,6 +408,7 @@ class Context:
         cfg.flags = (CRYSTAL_SERVE_SOURCE_PINNED if source_pinned else 0) | \
             (CRYSTAL_SERVE_ARRIVAL_ORDER if arrival_order else 0)
         cfg.bypass_ns = bypass_ns
+        cfg.ring_bytes, cfg.ring_max_request = ring_bytes, ring_max_request
         cfg.direct_params = ctypes.cast(ctypes.pointer(direct), ctypes.c_void_p) if direct is not None else None
         cfg.sliding_params = ctypes.cast(ctypes.pointer(sliding), ctypes.c_void_p) if sliding is not None else None
         if capture is not None:

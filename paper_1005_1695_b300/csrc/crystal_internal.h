@@ -49,6 +49,28 @@ inline crystal_unit* batch_units(crystal_batch* b) {
     return reinterpret_cast<crystal_unit*>(reinterpret_cast<uint8_t*>(b) + sizeof(crystal_batch));
 }
 
+// A pinned-host block and a device block of the same size, both taken from
+// the context's pools (host from the pinned arena, device from the device
+// arena); given back with release_pool_pair.  EINVAL for a context without
+// pools.
+struct PoolPair {
+    uint8_t* host = nullptr;
+    uint8_t* dev = nullptr;
+    uint64_t host_off = 0, dev_off = 0, bytes = 0;
+};
+int reserve_pool_pair(crystal_ctx* c, uint64_t bytes, PoolPair* out);
+void release_pool_pair(crystal_ctx* c, const PoolPair& p);
+
+// A job whose input lies in memory the caller keeps (h_in page-locked, d_in
+// device memory, in_size bytes each; e.g. slots of an input ring made from a
+// PoolPair): only its output and scratch come from the pools, and releasing
+// it leaves the input memory alone.  Jobs whose inputs sit next to each other
+// at one host-to-device distance have their copies merged like pooled jobs
+// (a job's block is in_size rounded up to 256 bytes, so the caller keeps the
+// inputs 256-byte aligned and the padding its own).
+int task_create_borrowed(crystal_ctx* c, uint8_t* h_in, uint8_t* d_in, uint64_t in_size, uint64_t out_size,
+                         uint64_t scratch_bytes, crystal_task** out);
+
 constexpr uint32_t kMaxWindow = 55;  // a window message fits one MD5 block
 
 inline bool kind_is_direct(int k) { return k == CRYSTAL_KIND_MD5_DIRECT || k == CRYSTAL_KIND_SHA1_DIRECT; }

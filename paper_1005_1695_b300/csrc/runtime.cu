@@ -81,6 +81,7 @@ struct crystal_task {
     uint8_t* d_reserved = nullptr;  // scratch reserved at create (crystal_task_create_ex)
     const uint8_t* h_in_ext = nullptr;  // caller memory bound as the input (crystal_task_bind_input)
     bool external_input = false;        // created without its own pinned input buffer
+    bool borrowed_input = false;        // h_in / d_in lie in memory the job does not own (an input ring)
     bool one_block = false;             // d_in, d_out and d_reserved are one device allocation at d_in
     uint64_t h_in_off = 0, h_out_off = 0, d_in_off = 0, d_out_off = 0, d_scratch_off = 0, d_reserved_off = 0;
     uint64_t reserved_bytes = 0;
@@ -228,6 +229,7 @@ void free_job_scratch(crystal_ctx* c, crystal_task* t) {
 void free_task_buffers(crystal_task* t) {
     crystal_ctx* c = t->ctx;
     free_job_scratch(c, t);
+    if (t->borrowed_input) t->h_in = t->d_in = nullptr;  // the ring's owner frees them
     if (t->one_block) {
         free_device(c, t->d_in, t->d_in_off);
         t->d_in = t->d_reserved = t->d_out = nullptr;
@@ -903,7 +905,7 @@ int crystal_task_create(crystal_ctx* c, uint64_t in_size, uint64_t out_size, cry
 
 namespace {
 int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes, uint32_t flags,
-               crystal_task** out);
+               crystal_task** out, uint8_t* borrowed_h_in = nullptr, uint8_t* borrowed_d_in = nullptr);
 }
 
 int crystal_task_create_ex(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes,
@@ -922,8 +924,9 @@ int crystal_task_create_ex(crystal_ctx* c, uint64_t in_size, uint64_t out_size, 
 namespace {
 
 int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes, uint32_t flags,
-               crystal_task** out) {
+               crystal_task** out, uint8_t* borrowed_h_in, uint8_t* borrowed_d_in) {
     if (!out) return CRYSTAL_EINVAL;
+    if ((borrowed_d_in != nullptr) != (borrowed_h_in != nullptr) || (borrowed_d_in && flags)) return CRYSTAL_EINVAL;
     if (flags & ~(uint32_t)CRYSTAL_TASK_EXTERNAL_INPUT) return CRYSTAL_EINVAL;
     *out = nullptr;
     if (in_size > c->cfg.max_in_bytes || out_size > c->cfg.max_out_bytes) return CRYSTAL_EINVAL;
@@ -935,9 +938,16 @@ int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scr
     t->in_cap = t->in_size = in_size;
     t->out_cap = t->out_size = out_size;
     t->external_input = flags & CRYSTAL_TASK_EXTERNAL_INPUT;
+    if (borrowed_d_in) {
+        t->borrowed_input = true;
+        t->h_in = borrowed_h_in;
+        t->d_in = borrowed_d_in;
+    }
     // inputs from the bottom of the arenas, outputs and scratch from the top
     int st = CRYSTAL_OK;
-    if (!t->external_input && c->pooled) {
+    if (t->borrowed_input) {
+        // input buffers given; output and scratch below
+    } else if (!t->external_input && c->pooled) {
         // the pinned input at the same arena offset as the device input when
         // that range is free: jobs with adjacent device inputs then have
         // adjacent pinned inputs too, at one host-to-device distance, and a
@@ -1346,3 +1356,39 @@ int crystal_get_stats(crystal_ctx* c, crystal_stats* out) {
 }
 
 }  // extern "C"
+
+namespace crystal {
+
+int reserve_pool_pair(crystal_ctx* c, uint64_t bytes, PoolPair* out) {
+    if (!c || !out || !bytes || !c->pooled) return CRYSTAL_EINVAL;
+    PoolPair p{};
+    p.bytes = bytes;
+    int st = alloc_host(c, bytes, &p.host, &p.host_off, CRYSTAL_ARENA_LOWEST);
+    if (st != CRYSTAL_OK) return st;
+    st = alloc_device(c, bytes, &p.dev, &p.dev_off, CRYSTAL_ARENA_LOWEST);
+    if (st != CRYSTAL_OK) {
+        free_host(c, p.host, p.host_off);
+        return st;
+    }
+    *out = p;
+    return CRYSTAL_OK;
+}
+
+void release_pool_pair(crystal_ctx* c, const PoolPair& p) {
+    if (!c || !p.host) return;
+    free_device(c, p.dev, p.dev_off);
+    free_host(c, p.host, p.host_off);
+}
+
+int task_create_borrowed(crystal_ctx* c, uint8_t* h_in, uint8_t* d_in, uint64_t in_size, uint64_t out_size,
+                         uint64_t scratch_bytes, crystal_task** out) {
+    if (!c || !h_in || !d_in) return CRYSTAL_EINVAL;
+    const uint64_t t0 = now_ns();
+    const int st = create_job(c, in_size, out_size, scratch_bytes, 0, out, h_in, d_in);
+    c->create_ns.fetch_add(now_ns() - t0, std::memory_order_relaxed);
+    c->create_calls.fetch_add(1, std::memory_order_relaxed);
+    if (st == CRYSTAL_EAGAIN) c->create_eagain.fetch_add(1, std::memory_order_relaxed);
+    return st;
+}
+
+}  // namespace crystal

@@ -13,6 +13,14 @@
 // others run join the next batch and overlap on the GPU.
 // Completion callbacks record the times, optionally copy the result out,
 // and release the job, which frees room for the next admission.
+//
+// Small requests can go through an input ring instead: one pinned block and
+// one device block taken from the pools for the whole call, carved in
+// admission order.  Their copy threads copy the bytes into the ring, so
+// requests admitted one after another sit next to each other in host and in
+// device memory, and the master merges their copies into one DMA transfer
+// (each transfer costs a few microseconds beside its bytes, which for
+// requests of a few hundred KiB is as much as the bytes themselves).
 #include <stdint.h>
 #include <string.h>
 #include <time.h>
@@ -25,6 +33,7 @@
 #include <vector>
 
 #include "crystal.h"
+#include "crystal_internal.h"
 
 namespace {
 
@@ -32,12 +41,74 @@ namespace {
 // (crystal_serve_config.bypass_ns), by up to this many candidates per pass.
 constexpr uint64_t kDefaultBypassNs = 2000000;
 constexpr uint32_t kBypassCandidates = 32;
+// Requests up to this size go through the input ring when it is on
+// (crystal_serve_config.ring_max_request = 0).
+constexpr uint64_t kDefaultRingMaxRequest = 256 << 10;
 
 uint64_t mono_ns() {
     timespec ts;
     clock_gettime(CLOCK_MONOTONIC, &ts);
     return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
 }
+
+// Input ring: slots of 256-byte-aligned sizes handed out in admission order
+// (after the newest slot, wrapping to the start when the end is reached) and
+// reclaimed in the same order: a finished slot is reused once every older
+// slot has finished too.  Thread-safe (admission takes, completion frees).
+class InputRing {
+  public:
+    static constexpr uint64_t kNone = UINT64_MAX;
+    void init(uint64_t bytes) { bytes_ = bytes; }
+    bool enabled() const { return bytes_ != 0; }
+    // A slot for `size` bytes: its offset, and its ticket in *seq; kNone when
+    // the ring has no room.
+    uint64_t take(uint64_t size, uint64_t* seq) {
+        const uint64_t b = crystal::align_up(size ? size : 1, 256);
+        std::lock_guard<std::mutex> lk(mu_);
+        uint64_t off = kNone;
+        if (live_.empty()) {
+            if (b <= bytes_) off = 0;
+        } else {
+            const uint64_t first = live_.front().off;
+            const uint64_t end = live_.back().off + live_.back().len;
+            if (live_.back().off >= first) {  // live slots run from first up to end
+                if (end + b <= bytes_) off = end;
+                else if (b <= first) off = 0;
+            } else if (end + b <= first) {    // wrapped: the gap is [end, first)
+                off = end;
+            }
+        }
+        if (off == kNone) return kNone;
+        live_.push_back(Slot{off, b, false});
+        *seq = front_seq_ + live_.size() - 1;
+        return off;
+    }
+    // The slot's job finished (or was never submitted): reclaim it and every
+    // finished slot behind it.
+    void give_back(uint64_t seq) {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (seq < front_seq_ || seq - front_seq_ >= live_.size()) return;
+        if (seq - front_seq_ == live_.size() - 1 && live_.size() > 1) {
+            live_.pop_back();  // the newest slot: its room is free at once
+            return;
+        }
+        live_[seq - front_seq_].done = true;
+        while (!live_.empty() && live_.front().done) {
+            live_.pop_front();
+            ++front_seq_;
+        }
+    }
+
+  private:
+    struct Slot {
+        uint64_t off, len;
+        bool done;
+    };
+    std::mutex mu_;
+    std::deque<Slot> live_;  // slots in use, oldest first
+    uint64_t front_seq_ = 0; // ticket of live_.front()
+    uint64_t bytes_ = 0;
+};
 
 struct Serve;
 
@@ -58,6 +129,12 @@ struct Serve {
     bool pinned_source = false;
     uint64_t bypass_ns = 0;  // how long the oldest waiting request may be passed
     std::vector<Ticket> tickets;
+    // input ring (small requests): the pools' blocks, the size limit, and per
+    // request its slot (offset, ticket) or InputRing::kNone
+    InputRing ring;
+    crystal::PoolPair ring_mem;
+    uint64_t ring_max = 0;
+    std::vector<uint64_t> ring_off, ring_seq;
 
     std::mutex mu;
     std::condition_variable cv_done, cv_work;
@@ -119,6 +196,7 @@ void on_done(crystal_task* t, int status, void* user) {
         used <= s->capture_bytes - r.capture_offset)
         memcpy(s->capture + r.capture_offset, out, used);
     crystal_task_release(t);  // buffers back to the pools now (room for the next admission); handle later
+    if (s->ring_off[i] != InputRing::kNone) s->ring.give_back(s->ring_seq[i]);
     s->finish(i, status);
 }
 
@@ -133,7 +211,9 @@ void worker(Serve* s) {
             s->work.pop_front();
         }
         const crystal_request& r = s->req[w.first];
-        if (s->pinned_source) {
+        if (s->ring_off[w.first] != InputRing::kNone) {
+            if (r.size) memcpy(s->ring_mem.host + s->ring_off[w.first], s->src + r.src_offset, r.size);
+        } else if (s->pinned_source) {
             crystal_task_bind_input(w.second, s->src + r.src_offset, r.size);
         } else if (r.size) {
             memcpy(crystal_task_host_in(w.second), s->src + r.src_offset, r.size);
@@ -142,6 +222,7 @@ void worker(Serve* s) {
         const int st = crystal_task_submit(w.second, r.kind, s->params_for(r.kind), on_done, &s->tickets[w.first]);
         if (st != CRYSTAL_OK) {
             crystal_task_release(w.second);
+            if (s->ring_off[w.first] != InputRing::kNone) s->ring.give_back(s->ring_seq[w.first]);
             s->finish(w.first, st);
         }
     }
@@ -180,6 +261,14 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
                   : (cfg && cfg->bypass_ns) ? cfg->bypass_ns : kDefaultBypassNs;
     if (threads > 64) threads = 64;
     memset(res, 0, sizeof(crystal_request_result) * n);
+    s.ring_off.assign(n, InputRing::kNone);
+    s.ring_seq.assign(n, 0);
+    if (cfg && cfg->ring_bytes) {
+        const int rs = crystal::reserve_pool_pair(ctx, crystal::align_up(cfg->ring_bytes, 256), &s.ring_mem);
+        if (rs != CRYSTAL_OK) return rs;
+        s.ring.init(s.ring_mem.bytes);
+        s.ring_max = cfg->ring_max_request ? cfg->ring_max_request : kDefaultRingMaxRequest;
+    }
     s.tickets.resize(n);
     for (uint32_t i = 0; i < n; ++i) s.tickets[i] = Ticket{&s, i};
     std::vector<std::thread> pool;
@@ -194,8 +283,24 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
         const crystal_request& r = req[i];
         const uint64_t scratch = crystal_scratch_bytes(r.kind, r.size, r.out_size, s.params_for(r.kind));
         crystal_task* t = nullptr;
-        const int st = crystal_task_create_ex(ctx, r.size, r.out_size, scratch,
-                                              s.pinned_source ? CRYSTAL_TASK_EXTERNAL_INPUT : 0u, &t);
+        int st = CRYSTAL_EAGAIN;
+        if (s.ring.enabled() && r.size <= s.ring_max) {
+            uint64_t seq = 0;
+            const uint64_t off = s.ring.take(r.size, &seq);
+            if (off != InputRing::kNone) {
+                st = crystal::task_create_borrowed(ctx, s.ring_mem.host + off, s.ring_mem.dev + off, r.size,
+                                                   r.out_size, scratch, &t);
+                if (st == CRYSTAL_OK) {
+                    s.ring_off[i] = off;
+                    s.ring_seq[i] = seq;
+                } else {
+                    s.ring.give_back(seq);
+                }
+            }
+        }
+        // not in the ring (too large, the ring full, or the pools): buffers of its own
+        if (!t) st = crystal_task_create_ex(ctx, r.size, r.out_size, scratch,
+                                            s.pinned_source ? CRYSTAL_TASK_EXTERNAL_INPUT : 0u, &t);
         if (st == CRYSTAL_OK) {
             ++admitted;
             res[i].admit_ns = mono_ns() - s.t0;
@@ -289,6 +394,7 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
     }
     s.cv_work.notify_all();
     for (auto& th : pool) th.join();
+    crystal::release_pool_pair(ctx, s.ring_mem);
     if (wall_ns) *wall_ns = s.last_done;
     int worst = CRYSTAL_OK;
     for (uint32_t i = 0; i < n; ++i)

@@ -210,11 +210,14 @@ def assign_capture(req, every: int = 1) -> int:
 def serve_trace(req, source, *, device_pool_bytes: int, host_pool_bytes: int, streams: int = 8,
                 batch_jobs: int = 8, copy_threads: int = 4, device: int = 0, capture_bytes: int = 0,
                 graphs: bool = True, direct=None, sliding=None, source_pinned: bool = False,
-                arrival_order: bool = False, bypass_ns: int = 0):
+                arrival_order: bool = False, bypass_ns: int = 0, ring_bytes: int = 0,
+                ring_max_request: int = 0):
     """Run a trace through crystal_serve on a fresh context sized to the pools.
     With ``source_pinned`` the source is page-locked for the run and jobs read
     their input from it directly; ``arrival_order`` / ``bypass_ns`` set the
-    admission policy.  Returns (status, results, wall_ns, capture)."""
+    admission policy; ``ring_bytes`` / ``ring_max_request`` stage small
+    requests through an input ring.  Returns (status, results, wall_ns,
+    capture)."""
     max_in = int(req["size"].max()) if len(req) else 1
     max_out = int(req["out_size"].max()) if len(req) else 16
     ctx = C.Context(max_in_bytes=max(max_in, 1), max_out_bytes=max(max_out, 16),
@@ -227,7 +230,8 @@ def serve_trace(req, source, *, device_pool_bytes: int, host_pool_bytes: int, st
     try:
         st, res, wall = ctx.serve(source, req, direct=direct, sliding=sliding, capture=capture,
                                   copy_threads=copy_threads, source_pinned=source_pinned,
-                                  arrival_order=arrival_order, bypass_ns=bypass_ns)
+                                  arrival_order=arrival_order, bypass_ns=bypass_ns, ring_bytes=ring_bytes,
+                                  ring_max_request=ring_max_request)
     finally:
         ctx.shutdown()
         if source_pinned:

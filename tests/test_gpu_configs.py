@@ -230,8 +230,9 @@ def config5(C, oracle_mod):
     return src, req, big, want
 
 
-@pytest.mark.parametrize("pinned", [True, False], ids=["pinned_source", "staged"])
-def test_config5_served_lognormal_with_capped_requests(C, config5, pinned):
+@pytest.mark.parametrize("pinned,ring", [(True, 0), (False, 0), (True, 64 << 20)],
+                         ids=["pinned_source", "staged", "pinned_ring"])
+def test_config5_served_lognormal_with_capped_requests(C, config5, pinned, ring):
     from paper_1005_1695_b300 import streams as S
 
     src, req, big, want = config5
@@ -241,8 +242,11 @@ def test_config5_served_lognormal_with_capped_requests(C, config5, pinned):
     pool = 96 << 20
     assert C.scratch_bytes(SLIDING, 64 << 20, int(req["out_size"][big[1]])) + (64 << 20) + \
         int(req["out_size"][big[1]]) + (64 << 20) > pool
-    st, res, wall, capture = S.serve_trace(req, src, device_pool_bytes=pool, host_pool_bytes=pool, streams=8,
-                                           batch_jobs=8, copy_threads=4, capture_bytes=cap, source_pinned=pinned)
+    # with the 64 MiB input ring (requests up to 256 KiB) the pool holds the
+    # ring beside the capped requests' buffers
+    st, res, wall, capture = S.serve_trace(req, src, device_pool_bytes=pool + ring, host_pool_bytes=pool + ring,
+                                           streams=8, batch_jobs=8, copy_threads=4, capture_bytes=cap,
+                                           source_pinned=pinned, ring_bytes=ring)
     assert st == C.CRYSTAL_OK and (res["status"] == 0).all()
     assert (res["admit_ns"] >= req["arrival_ns"]).all() and (res["done_ns"] >= res["submit_ns"]).all()
     mix = {}

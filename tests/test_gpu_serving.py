@@ -31,18 +31,21 @@ def _outputs(req, res, capture):
     return outs
 
 
-@pytest.mark.parametrize("pinned", [False, True], ids=["staged", "pinned_source"])
-def test_served_mix_bit_exact_alone_equals_mix(C, oracle_mod, pinned):
+@pytest.mark.parametrize("pinned,ring", [(False, 0), (True, 0), (True, 2 << 20), (False, 2 << 20)],
+                         ids=["staged", "pinned_source", "pinned_ring", "staged_ring"])
+def test_served_mix_bit_exact_alone_equals_mix(C, oracle_mod, pinned, ring):
     from paper_1005_1695_b300 import inputs
     from paper_1005_1695_b300 import streams as S
 
     src = inputs.arena(3, 64 << 20, out=C.page_aligned(64 << 20))
     req, cap = S.make_trace(3, 240, 4000.0, src.nbytes, median=96 << 10, sigma=1.5, cap=4 << 20,
                             capture_every=1)
-    # a device pool far smaller than the trace's total bytes: admission has to wait
+    # a device pool far smaller than the trace's total bytes: admission has to
+    # wait; the 2 MiB input ring (requests up to 256 KiB) wraps many times and
+    # is full at times, so some small requests get buffers of their own
     st, res, wall, capture = S.serve_trace(req, src, device_pool_bytes=24 << 20, host_pool_bytes=24 << 20,
                                            streams=4, batch_jobs=4, copy_threads=4, capture_bytes=cap,
-                                           source_pinned=pinned)
+                                           source_pinned=pinned, ring_bytes=ring)
     assert st == C.CRYSTAL_OK
     assert (res["status"] == 0).all()
     assert (res["done_ns"] >= res["submit_ns"]).all() and (res["submit_ns"] >= res["admit_ns"]).all()
@@ -119,3 +122,75 @@ def test_admission_past_a_blocked_large_request(C, oracle_mod, arrival_order):
         got = capture[off:off + int(res["used_bytes"][i])].tobytes()
         assert ost == 0 and same_result(k, n, got, want), f"request {i}: " + first_difference(k, n, got, want)
 
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned_source", "staged"])
+def test_input_ring_merges_small_requests(C, oracle_mod, pinned):
+    """64 requests of 40-200 KiB waiting at once, read from scattered offsets
+    of the source: through the input ring, requests admitted one after another
+    sit side by side in pinned and device memory, and each batch copies its
+    ring inputs in one transfer.  Without the ring every request (read in
+    place) is its own transfer.  Every output is bit-exact either way."""
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    src = inputs.arena(8, 32 << 20, out=C.page_aligned(32 << 20))
+    req, _ = S.make_trace(8, 64, 1000.0, src.nbytes, median=96 << 10, sigma=0.4, cap=200 << 10, p_sliding=0.25)
+    req["arrival_ns"] = 0
+    req["size"] = np.maximum(req["size"], 40 << 10)
+    req["src_offset"] = np.minimum(req["src_offset"], src.nbytes - req["size"])
+    S.set_out_sizes(req)
+    cap = S.assign_capture(req)
+    if pinned:
+        C.host_register(src)
+    copies = {}
+    try:
+        for ring in (0, 32 << 20):
+            ctx = C.Context(max_in_bytes=256 << 10, max_out_bytes=1 << 20, device_pool_bytes=128 << 20,
+                            host_pool_bytes=128 << 20, n_streams=2, max_batch_jobs=16,
+                            max_batch_bytes=32 << 20, flags=C.CRYSTAL_FLAG_GRAPHS)
+            capture = np.zeros(cap, dtype=np.uint8)
+            try:
+                st, res, _ = ctx.serve(src, req, capture=capture, copy_threads=4, source_pinned=pinned,
+                                       ring_bytes=ring)
+                copies[ring] = int(ctx.stats().copies_dma)
+            finally:
+                ctx.shutdown()
+            assert st == C.CRYSTAL_OK and (res["status"] == 0).all()
+            for i in range(len(req)):
+                k, n, o = int(req["kind"][i]), int(req["size"][i]), int(req["src_offset"][i])
+                ost, want = oracle_mod.task(k, src[o:o + n], int(req["out_size"][i]))
+                off = int(req["capture_offset"][i])
+                got = capture[off:off + int(res["used_bytes"][i])].tobytes()
+                assert ost == 0 and same_result(k, n, got, want), \
+                    f"ring {ring}, request {i}: " + first_difference(k, n, got, want)
+    finally:
+        if pinned:
+            C.host_unregister(src)
+    sliding = int(np.isin(req["kind"], list(C.SLIDING_KINDS)).sum())
+    if pinned:
+        assert copies[0] >= len(req)  # every input in place is its own transfer
+    # ring inputs merge: fewer input transfers than requests (outputs of the
+    # sliding requests are copied back on their own at most)
+    assert copies[32 << 20] - sliding < len(req) // 2, copies
+
+
+def test_input_ring_larger_than_the_pools_is_refused(C):
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    src = inputs.arena(9, 4 << 20)
+    req, _ = S.make_trace(9, 8, 1000.0, src.nbytes, median=16 << 10, cap=64 << 10, p_sliding=0.0)
+    ctx = C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 16, device_pool_bytes=16 << 20,
+                    host_pool_bytes=16 << 20, n_streams=1)
+    try:
+        before = ctx.stats()
+        st, res, _ = ctx.serve(src, req, ring_bytes=64 << 20)
+        assert st in (C.CRYSTAL_EAGAIN, C.CRYSTAL_ENOMEM)
+        st, res, _ = ctx.serve(src, req, ring_bytes=1 << 20)
+        assert st == C.CRYSTAL_OK and (res["status"] == 0).all()
+        after = ctx.stats()  # the ring and every job's buffers are back in the pools
+        assert after.device_pool_used == before.device_pool_used
+        assert after.host_pool_used == before.host_pool_used
+    finally:
+        ctx.shutdown()

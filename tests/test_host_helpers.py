@@ -64,7 +64,7 @@ def test_geometry_and_stream_structs_match_header(C):
 
     assert ctypes.sizeof(C.crystal_geometry) == 24
     assert ctypes.sizeof(C.crystal_stream_config) == 32
-    assert ctypes.sizeof(C.crystal_serve_config) == 48
+    assert ctypes.sizeof(C.crystal_serve_config) == 64
     g = C.geometry(seg_threads=64, win_registers=64)
     assert g.as_dict()["seg_threads"] == 64 and g.reserved == 0
 
@@ -82,10 +82,11 @@ def test_ctypes_layouts_match_the_c_compiler(C, tmp_path):
 #include <stddef.h>
 #include "crystal.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(crystal_config), sizeof(crystal_hash_params),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(crystal_config), sizeof(crystal_hash_params),
          sizeof(crystal_stats), sizeof(crystal_unit), sizeof(crystal_batch), sizeof(crystal_request),
          sizeof(crystal_request_result), sizeof(crystal_serve_config), sizeof(crystal_stream_config),
-         sizeof(crystal_geometry), offsetof(crystal_serve_config, bypass_ns));
+         sizeof(crystal_geometry), offsetof(crystal_serve_config, bypass_ns),
+         offsetof(crystal_serve_config, ring_max_request));
   return 0;
 }
 ''')
@@ -95,5 +96,6 @@ int main(void) {
     want = [ctypes.sizeof(C.crystal_config), ctypes.sizeof(C.crystal_hash_params), ctypes.sizeof(C.crystal_stats),
             C.UNIT_DTYPE.itemsize, C.BATCH_HEADER_BYTES, C.REQUEST_DTYPE.itemsize, C.RESULT_DTYPE.itemsize,
             ctypes.sizeof(C.crystal_serve_config), ctypes.sizeof(C.crystal_stream_config),
-            ctypes.sizeof(C.crystal_geometry), C.crystal_serve_config.bypass_ns.offset]
+            ctypes.sizeof(C.crystal_geometry), C.crystal_serve_config.bypass_ns.offset,
+            C.crystal_serve_config.ring_max_request.offset]
     assert got == want
