@@ -4,9 +4,11 @@ Picks, by measuring the workload itself, two levels of the runtime's
 settings:
 
 1. the pipeline shape: the number of streams the master thread interleaves
-   batches over (the pipeline depth of Section 4.2 / Figure 4), and how many
+   batches over (the pipeline depth of Section 4.2 / Figure 4), how many
    outstanding jobs and bytes it packs into one batch (one descriptor upload
-   and one persistent-kernel chain or graph replay);
+   and one persistent-kernel chain or graph replay), and up to which size
+   units are copied into an input ring so that neighbours' copies merge into
+   one transfer (0: none; every unit read in place);
 2. for each batch size class (the mean input size of a batch's jobs: under
    64 KiB, 64 KiB to 1 MiB, 1 MiB and up) the kernels' launch geometry:
    threads per CTA and CTAs per SM of the segment-digest kernel, CTAs per SM
@@ -43,15 +45,24 @@ GEOMETRY_KNOBS = (
 )
 
 
+# Bytes of the input ring when a setting uses one.
+RING_BYTES = 256 << 20
+
+
 @dataclass
 class Setting:
     streams: int
     batch_jobs: int
     batch_bytes: int
     geometry: Dict[int, Dict[str, int]] = field(default_factory=dict)  # size class -> geometry fields
+    ring_max: int = 0  # units up to this size go through the input ring (0: no ring)
+
+    def serve_kw(self) -> Dict[str, int]:
+        return {"ring_bytes": RING_BYTES if self.ring_max else 0, "ring_max_request": self.ring_max}
 
     def as_dict(self) -> Dict:
-        d = {"streams": self.streams, "batch_jobs": self.batch_jobs, "batch_bytes": self.batch_bytes}
+        d = {"streams": self.streams, "batch_jobs": self.batch_jobs, "batch_bytes": self.batch_bytes,
+             "ring_max": self.ring_max}
         if self.geometry:
             d["geometry"] = {C.SIZE_CLASS_NAMES[k]: v for k, v in sorted(self.geometry.items())}
         return d
@@ -68,8 +79,9 @@ def _context(req: np.ndarray, setting: Setting, device_pool_bytes: int, device: 
     max_in = int(req["size"].max())
     max_out = int(req["out_size"].max())
     host_pool = int(req["out_size"].astype(np.int64).sum()) + len(req) * 768 + (64 << 20)
+    host_pool = min(host_pool, 2 << 30) + setting.serve_kw()["ring_bytes"]
     ctx = C.Context(max_in_bytes=max_in, max_out_bytes=max_out, device_pool_bytes=device_pool_bytes,
-                    host_pool_bytes=min(host_pool, 2 << 30), n_streams=setting.streams, device=device,
+                    host_pool_bytes=host_pool, n_streams=setting.streams, device=device,
                     max_batch_jobs=setting.batch_jobs, max_batch_bytes=setting.batch_bytes, flags=flags)
     for cls, g in setting.geometry.items():
         ctx.set_geometry(cls, C.geometry(**g))
@@ -83,19 +95,21 @@ def run_batch(req: np.ndarray, source: np.ndarray, setting: Setting, *, device_p
     read their inputs in place).  Returns (status, results, wall_ns)."""
     ctx = _context(req, setting, device_pool_bytes, device, flags)
     try:
-        return ctx.serve(source, req, copy_threads=submit_threads, source_pinned=True, capture=capture)
+        return ctx.serve(source, req, copy_threads=submit_threads, source_pinned=True, capture=capture,
+                         **setting.serve_kw())
     finally:
         ctx.shutdown()
 
 
 def tune(req_sample: np.ndarray, source: np.ndarray, *, device_pool_bytes: int, device: int = 0,
          streams: Sequence[int] = (4, 8, 16), batch_jobs: Sequence[int] = (8, 32, 128),
-         batch_bytes: Sequence[int] = (32 << 20, 128 << 20), repeats: int = 2, flags: int = C.CRYSTAL_FLAG_GRAPHS):
+         batch_bytes: Sequence[int] = (32 << 20, 128 << 20), ring_max: Sequence[int] = (0,), repeats: int = 2,
+         flags: int = C.CRYSTAL_FLAG_GRAPHS):
     """Measure every pipeline shape on ``req_sample``; return (best, table)."""
     total = float(req_sample["size"].sum())
     table: List[Dict] = []
-    for s, j, b in itertools.product(streams, batch_jobs, batch_bytes):
-        setting = Setting(s, j, b)
+    for s, j, b, r in itertools.product(streams, batch_jobs, batch_bytes, ring_max):
+        setting = Setting(s, j, b, ring_max=r)
         walls = []
         for _ in range(repeats):
             st, res, wall = run_batch(req_sample, source, setting, device_pool_bytes=device_pool_bytes,
@@ -104,7 +118,7 @@ def tune(req_sample: np.ndarray, source: np.ndarray, *, device_pool_bytes: int, 
             walls.append(wall)
         table.append({**setting.as_dict(), "GB_per_s": round(total / (min(walls) / 1e9) / 1e9, 3)})
     best = max(table, key=lambda r: r["GB_per_s"])
-    return Setting(best["streams"], best["batch_jobs"], best["batch_bytes"]), table
+    return Setting(best["streams"], best["batch_jobs"], best["batch_bytes"], ring_max=best["ring_max"]), table
 
 
 def tune_geometry(req_sample: np.ndarray, source: np.ndarray, setting: Setting, *, device_pool_bytes: int,
@@ -116,8 +130,9 @@ def tune_geometry(req_sample: np.ndarray, source: np.ndarray, setting: Setting, 
     only if it is faster by more than ``margin``.  Returns (setting with the
     chosen geometry, table)."""
     classes = size_classes(req_sample["size"])
-    ctx = _context(req_sample, Setting(setting.streams, setting.batch_jobs, setting.batch_bytes), device_pool_bytes,
-                   device, flags)
+    ctx = _context(req_sample, Setting(setting.streams, setting.batch_jobs, setting.batch_bytes,
+                                       ring_max=setting.ring_max), device_pool_bytes, device, flags)
+    kw = setting.serve_kw()
     table: List[Dict] = []
     chosen: Dict[int, Dict[str, int]] = {}
     try:
@@ -129,10 +144,10 @@ def tune_geometry(req_sample: np.ndarray, source: np.ndarray, setting: Setting, 
 
             def measure(g: Dict[str, int]) -> float:
                 ctx.set_geometry(cls, C.geometry(**g))
-                C.check(ctx.serve(source, sub, copy_threads=2, source_pinned=True)[0], "crystal_serve")  # capture
+                C.check(ctx.serve(source, sub, copy_threads=2, source_pinned=True, **kw)[0], "crystal_serve")  # capture
                 walls = []
                 for _ in range(repeats):
-                    st, res, wall = ctx.serve(source, sub, copy_threads=2, source_pinned=True)
+                    st, res, wall = ctx.serve(source, sub, copy_threads=2, source_pinned=True, **kw)
                     C.check(st, "crystal_serve")
                     walls.append(wall)
                 gbs = total / (min(walls) / 1e9) / 1e9
@@ -154,4 +169,4 @@ def tune_geometry(req_sample: np.ndarray, source: np.ndarray, setting: Setting, 
             chosen[cls] = ctx.get_geometry(cls).as_dict()
     finally:
         ctx.shutdown()
-    return Setting(setting.streams, setting.batch_jobs, setting.batch_bytes, chosen), table
+    return Setting(setting.streams, setting.batch_jobs, setting.batch_bytes, chosen, ring_max=setting.ring_max), table

@@ -33,15 +33,17 @@ def test_batched_uneven_autotuned_bit_exact(C, oracle_mod):
     C.host_register(src)
     try:
         best, table = A.tune(req[:400], src, device_pool_bytes=512 << 20, streams=(2, 8), batch_jobs=(4, 64),
-                             batch_bytes=(32 << 20,), repeats=1)
-        assert len(table) == 4 and best.streams in (2, 8)
+                             batch_bytes=(32 << 20,), ring_max=(0, 256 << 10), repeats=1)
+        assert len(table) == 8 and best.streams in (2, 8) and best.ring_max in (0, 256 << 10)
         best, gtable = A.tune_geometry(req[:400], src, best, device_pool_bytes=512 << 20, repeats=1,
                                        knobs=(("seg_threads", (128, 64)), ("win_ctas_per_sm", (0, 2))))
         assert set(best.geometry) <= {0, 1, 2} and len(best.geometry) >= 2 and len(gtable) >= 2 * len(best.geometry)
         import numpy as np
 
+        # the whole batch with the units up to 256 KiB going through the input ring
+        best.ring_max = 256 << 10
         capture = np.zeros(cap, dtype=np.uint8)
-        st, res, wall = A.run_batch(req, src, best, device_pool_bytes=256 << 20, capture=capture)
+        st, res, wall = A.run_batch(req, src, best, device_pool_bytes=512 << 20, capture=capture)
     finally:
         C.host_unregister(src)
     assert st == C.CRYSTAL_OK and (res["status"] == 0).all()

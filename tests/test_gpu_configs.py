@@ -190,7 +190,7 @@ def test_config4_uneven_full_size_range_every_unit(C, oracle_mod):
     C.host_register(src)
     try:
         best, table = A.tune(req[:300], src, device_pool_bytes=1 << 30, streams=(4, 8), batch_jobs=(8, 32),
-                             batch_bytes=(64 << 20,), repeats=1)
+                             batch_bytes=(64 << 20,), ring_max=(0, 256 << 10), repeats=1)
         capture = np.zeros(cap, dtype=np.uint8)
         st, res, wall = A.run_batch(req, src, best, device_pool_bytes=1 << 30, capture=capture)
     finally:
