@@ -34,6 +34,7 @@
 
 #include "crystal.h"
 #include "crystal_internal.h"
+#include "input_ring.h"
 
 namespace {
 
@@ -50,65 +51,6 @@ uint64_t mono_ns() {
     clock_gettime(CLOCK_MONOTONIC, &ts);
     return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
 }
-
-// Input ring: slots of 256-byte-aligned sizes handed out in admission order
-// (after the newest slot, wrapping to the start when the end is reached) and
-// reclaimed in the same order: a finished slot is reused once every older
-// slot has finished too.  Thread-safe (admission takes, completion frees).
-class InputRing {
-  public:
-    static constexpr uint64_t kNone = UINT64_MAX;
-    void init(uint64_t bytes) { bytes_ = bytes; }
-    bool enabled() const { return bytes_ != 0; }
-    // A slot for `size` bytes: its offset, and its ticket in *seq; kNone when
-    // the ring has no room.
-    uint64_t take(uint64_t size, uint64_t* seq) {
-        const uint64_t b = crystal::align_up(size ? size : 1, 256);
-        std::lock_guard<std::mutex> lk(mu_);
-        uint64_t off = kNone;
-        if (live_.empty()) {
-            if (b <= bytes_) off = 0;
-        } else {
-            const uint64_t first = live_.front().off;
-            const uint64_t end = live_.back().off + live_.back().len;
-            if (live_.back().off >= first) {  // live slots run from first up to end
-                if (end + b <= bytes_) off = end;
-                else if (b <= first) off = 0;
-            } else if (end + b <= first) {    // wrapped: the gap is [end, first)
-                off = end;
-            }
-        }
-        if (off == kNone) return kNone;
-        live_.push_back(Slot{off, b, false});
-        *seq = front_seq_ + live_.size() - 1;
-        return off;
-    }
-    // The slot's job finished (or was never submitted): reclaim it and every
-    // finished slot behind it.
-    void give_back(uint64_t seq) {
-        std::lock_guard<std::mutex> lk(mu_);
-        if (seq < front_seq_ || seq - front_seq_ >= live_.size()) return;
-        if (seq - front_seq_ == live_.size() - 1 && live_.size() > 1) {
-            live_.pop_back();  // the newest slot: its room is free at once
-            return;
-        }
-        live_[seq - front_seq_].done = true;
-        while (!live_.empty() && live_.front().done) {
-            live_.pop_front();
-            ++front_seq_;
-        }
-    }
-
-  private:
-    struct Slot {
-        uint64_t off, len;
-        bool done;
-    };
-    std::mutex mu_;
-    std::deque<Slot> live_;  // slots in use, oldest first
-    uint64_t front_seq_ = 0; // ticket of live_.front()
-    uint64_t bytes_ = 0;
-};
 
 struct Serve;
 
@@ -130,8 +72,8 @@ struct Serve {
     uint64_t bypass_ns = 0;  // how long the oldest waiting request may be passed
     std::vector<Ticket> tickets;
     // input ring (small requests): the pools' blocks, the size limit, and per
-    // request its slot (offset, ticket) or InputRing::kNone
-    InputRing ring;
+    // request its slot (offset, ticket) or crystal::InputRing::kNone
+    crystal::InputRing ring;
     crystal::PoolPair ring_mem;
     uint64_t ring_max = 0;
     std::vector<uint64_t> ring_off, ring_seq;
@@ -196,7 +138,7 @@ void on_done(crystal_task* t, int status, void* user) {
         used <= s->capture_bytes - r.capture_offset)
         memcpy(s->capture + r.capture_offset, out, used);
     crystal_task_release(t);  // buffers back to the pools now (room for the next admission); handle later
-    if (s->ring_off[i] != InputRing::kNone) s->ring.give_back(s->ring_seq[i]);
+    if (s->ring_off[i] != crystal::InputRing::kNone) s->ring.give_back(s->ring_seq[i]);
     s->finish(i, status);
 }
 
@@ -211,7 +153,7 @@ void worker(Serve* s) {
             s->work.pop_front();
         }
         const crystal_request& r = s->req[w.first];
-        if (s->ring_off[w.first] != InputRing::kNone) {
+        if (s->ring_off[w.first] != crystal::InputRing::kNone) {
             if (r.size) memcpy(s->ring_mem.host + s->ring_off[w.first], s->src + r.src_offset, r.size);
         } else if (s->pinned_source) {
             crystal_task_bind_input(w.second, s->src + r.src_offset, r.size);
@@ -222,7 +164,7 @@ void worker(Serve* s) {
         const int st = crystal_task_submit(w.second, r.kind, s->params_for(r.kind), on_done, &s->tickets[w.first]);
         if (st != CRYSTAL_OK) {
             crystal_task_release(w.second);
-            if (s->ring_off[w.first] != InputRing::kNone) s->ring.give_back(s->ring_seq[w.first]);
+            if (s->ring_off[w.first] != crystal::InputRing::kNone) s->ring.give_back(s->ring_seq[w.first]);
             s->finish(w.first, st);
         }
     }
@@ -261,7 +203,7 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
                   : (cfg && cfg->bypass_ns) ? cfg->bypass_ns : kDefaultBypassNs;
     if (threads > 64) threads = 64;
     memset(res, 0, sizeof(crystal_request_result) * n);
-    s.ring_off.assign(n, InputRing::kNone);
+    s.ring_off.assign(n, crystal::InputRing::kNone);
     s.ring_seq.assign(n, 0);
     if (cfg && cfg->ring_bytes) {
         const int rs = crystal::reserve_pool_pair(ctx, crystal::align_up(cfg->ring_bytes, 256), &s.ring_mem);
@@ -287,7 +229,7 @@ int crystal_serve(crystal_ctx* ctx, const void* source, uint64_t source_bytes, c
         if (s.ring.enabled() && r.size <= s.ring_max) {
             uint64_t seq = 0;
             const uint64_t off = s.ring.take(r.size, &seq);
-            if (off != InputRing::kNone) {
+            if (off != crystal::InputRing::kNone) {
                 st = crystal::task_create_borrowed(ctx, s.ring_mem.host + off, s.ring_mem.dev + off, r.size,
                                                    r.out_size, scratch, &t);
                 if (st == CRYSTAL_OK) {
