@@ -62,8 +62,8 @@ INT_LANES_PER_SM = 128  # 4 schedulers x one 32-lane instruction per clock
 # DRAM bytes (read + write) of the window kernel per 1 MiB sliding unit, from one
 # ncu capture of 160 units (traffic grows with the units processed), valid only
 # for the kernel sources it was taken on (checked by hash; otherwise null).
-WINDOW_TRAFFIC_PER_UNIT = (168.245760e6 + 14.485248e6) / 160
-WINDOW_TRAFFIC_SOURCES = "3c7f11974f75cdc9"
+WINDOW_TRAFFIC_PER_UNIT = (168.128512e6 + 14.240768e6) / 160
+WINDOW_TRAFFIC_SOURCES = "36822ebde71ff91b"
 
 
 def _kernel_sources_hash() -> str:
@@ -708,27 +708,31 @@ def record_config3(args, local, link):
     from paper_1005_1695_b300 import streams as S
 
     U, N = args.c3_units, 4 << 20
+    US = max(U, args.c3_staged_units)
     # units are 4 MiB windows at seeded offsets of a 2 GiB pageable arena
     arena_bytes = 2 << 30
     arena = _arena_pageable(args.seed + 3, arena_bytes)
-    offs = (np.arange(U, dtype=np.int64) * 7919 * 4096 + 13 * np.arange(U)) % (arena_bytes - N)
+    offs = (np.arange(US, dtype=np.int64) * 7919 * 4096 + 13 * np.arange(US)) % (arena_bytes - N)
     unit = lambda i: arena[int(offs[i]):int(offs[i]) + N]
     p = C.params(segment_bytes=4096)
     h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
     memcpy1 = host_memcpy_rate(torch, arena)
-    sample = list(range(0, U, max(1, U // 8)))
-    rec = {"workload": f"pipelined direct hashing, {U} units x 4 MiB, S=4 KiB, 8 streams x 8 jobs per batch",
+    rec = {"workload": f"pipelined direct hashing of 4 MiB units, S=4 KiB, 8 streams x 8 jobs per batch: the "
+                       f"staging ring over the configuration's {US} units, the other forms over {U}",
            "host_link_h2d_gbs": h2d}
     checks = Checks()
-    modes = [("pooled", U), ("pooled_staged", U), ("no_overlap", U), ("per_job_malloc", min(U, args.malloc_units))]
+    # the staging ring needs no memory per unit, so it runs the whole stream;
+    # the resident forms hold every unit in pinned memory at once
+    modes = [("pooled", U), ("pooled_staged", US), ("no_overlap", U), ("per_job_malloc", min(U, args.malloc_units))]
     for mode, n in modes:
+        sample = sorted(set(range(0, n, max(1, n // 8))) | {n - 1})
         r = S.run_stream(mode, unit, n, N, C.CRYSTAL_KIND_MD5_DIRECT, p, 16, streams=8, batch_jobs=8,
                          depth=args.ring_jobs if mode == "pooled_staged" else args.depth,
-                         copy_threads=args.stage_threads, device=local, keep=[i for i in sample if i < n])
+                         copy_threads=args.stage_threads, device=local, keep=sample)
         assert all(st == 0 for st in r.statuses), (mode, set(r.statuses))
         rec[mode] = {"units": n, "GB_per_s": round(r.gbs, 3), "frac_of_link": round(r.gbs / h2d, 4)}
-        for i in sample:
-            if i < n and mode in ("pooled", "pooled_staged"):
+        if mode in ("pooled", "pooled_staged"):
+            for i in sample:
                 checks.add(C.CRYSTAL_KIND_MD5_DIRECT, unit(i), 16, r.outputs[i], {"seg_bytes": 4096})
     bound = min(memcpy1 * args.stage_threads, h2d)
     rec["pooled_staged"].update({"copy_threads": args.stage_threads, "ring_jobs": args.ring_jobs,
@@ -1404,6 +1408,8 @@ def main():
     ap.add_argument("--configs", type=int, default=1,
                     help="add the records of configurations 1, 3, 4 and 5 to the default line (rank 0)")
     ap.add_argument("--c3-units", type=int, default=512)
+    ap.add_argument("--c3-staged-units", type=int, default=4096,
+                    help="units of the staging-ring form in the configuration-3 record")
     ap.add_argument("--ring-jobs", type=int, default=48, help="staging ring of the pageable-source form")
     ap.add_argument("--stage-threads", type=int, default=16, help="copy threads of the staging ring")
     ap.add_argument("--c4-units", type=int, default=5000)

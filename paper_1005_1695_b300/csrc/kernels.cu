@@ -231,6 +231,61 @@ __device__ __forceinline__ uint32_t tile_windows(const uint32_t* sw, uint32_t de
     return mine;
 }
 
+// Hit mask of a lane's eight windows past the unit's last full window
+// (rel0 + 4 j + 20 > lim) cleared, ORed over the four lanes of its group and
+// moved to lane g (the layout of tile_windows).
+__device__ __forceinline__ uint32_t gather_group_mask(uint32_t m, uint32_t rel0, uint32_t lim) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t sub = lane & 3;
+    const int32_t room = (int32_t)lim - (int32_t)(rel0 + 20);
+    const uint32_t valid = room < 0 ? 0u : min(8u, (uint32_t)room / 4 + 1);
+    m &= valid ? (0x11111111u >> (4 * (8 - valid))) << sub : 0u;
+    m |= __shfl_xor_sync(0xffffffffu, m, 1);
+    m |= __shfl_xor_sync(0xffffffffu, m, 2);
+    return __shfl_sync(0xffffffffu, m, (lane & 7) * 4);
+}
+
+// SHA-1 form of tile_windows20 (same lanes and windows).  SHA-1 reads its
+// message words big-endian, so the staged words are byte-swapped once each
+// and shifted into place from the high end (one swap per window instead of
+// five), and the boundary test compares the big-endian first digest word
+// against the byte-swapped mask and target: (bswap(x) & m) == t exactly when
+// (x & bswap(m)) == bswap(t).
+__device__ __forceinline__ uint32_t tile_windows20_sha1(const uint32_t* s, uint32_t sh, uint32_t rel0, uint32_t lim,
+                                                        uint32_t mask, uint32_t target, uint32_t one) {
+    const uint32_t sub = threadIdx.x & 3;
+    const uint32_t bmask = sha1::bswap(mask), btarget = sha1::bswap(target);
+    uint32_t M[5];  // big-endian message words 0..4 of the current window
+    uint32_t raw = sha1::bswap(s[0]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const uint32_t nxt = sha1::bswap(s[k + 1]);
+        M[k] = __funnelshift_l(nxt, raw, sh);
+        raw = nxt;
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t W[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) W[k] = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) W[k] = M[k];
+        W[5] = 0x80000000u;
+        W[15] = 8u * 20;
+        const uint32_t A = sha1::first_word_one_block(W, one);
+        m |= (uint32_t)((A & bmask) == btarget) << (sub + 4 * j);
+        if (j < 7) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) M[k] = M[k + 1];
+            const uint32_t nxt = sha1::bswap(s[j + 6]);
+            M[4] = __funnelshift_l(nxt, raw, sh);
+            raw = nxt;
+        }
+    }
+    return gather_group_mask(m, rel0, lim);
+}
+
 // The tile with the common 20-byte window.  Lane (g, s) = (lane / 4, lane % 4)
 // of a warp hashes the windows at offsets 32 g + s + 4 j, j = 0..7, of the
 // warp's 256: consecutive windows of a thread are one word apart, so they
@@ -249,6 +304,7 @@ __device__ __forceinline__ uint32_t tile_windows20(const uint32_t* sw, uint32_t 
     const uint32_t p = rel0 + delta;
     const uint32_t* s = sw + (p >> 2);
     const uint32_t sh = (p & 3) * 8;
+    if constexpr (H::kWords == 5) return tile_windows20_sha1(s, sh, rel0, lim, mask, target, one);
     uint32_t M[5];  // message words 0..4 of the current window
     uint32_t raw = s[0];
 #pragma unroll
@@ -277,14 +333,8 @@ __device__ __forceinline__ uint32_t tile_windows20(const uint32_t* sw, uint32_t 
             raw = nxt;
         }
     }
-    // windows past the unit's last full window (rel0 + 4 j + 20 > lim) do not
-    // count: this lane's first `valid` windows fit, bits s + 4 j of the mask
-    const int32_t room = (int32_t)lim - (int32_t)(rel0 + 20);
-    const uint32_t valid = room < 0 ? 0u : min(8u, (uint32_t)room / 4 + 1);
-    m &= valid ? (0x11111111u >> (4 * (8 - valid))) << sub : 0u;
-    m |= __shfl_xor_sync(0xffffffffu, m, 1);
-    m |= __shfl_xor_sync(0xffffffffu, m, 2);
-    return __shfl_sync(0xffffffffu, m, (lane & 7) * 4);
+    // windows past the unit's last full window do not count
+    return gather_group_mask(m, rel0, lim);
 }
 
 // What every thread of a CTA needs to know about one tile, worked out once by
