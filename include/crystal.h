@@ -458,7 +458,8 @@ int crystal_launch_batch(const crystal_batch* batch_dev, void* stream);
  * bind the job's input to them) and submit it; with ring_bytes > 0, requests
  * of at most ring_max_request bytes are instead copied into an input ring
  * (ring_bytes of pinned host pool and ring_bytes of device pool, reserved for
- * the call; EAGAIN / ENOMEM if the pools cannot hold it) in admission order,
+ * the call; EAGAIN / ENOMEM if the pools cannot hold it, EINVAL for a context
+ * without pools, CRYSTAL_FLAG_NO_POOL) in admission order,
  * so neighbouring requests' copies merge into one DMA transfer -- a request
  * that finds the ring full gets buffers of its own as before; the master thread
  * batches whatever is outstanding (continuous batching).  On completion the
