@@ -852,12 +852,13 @@ def record_config5(args, local, link):
                           "input ring (merged transfers)" if args.input_ring else "no input ring"),
            "rates_per_s": {}}
     checks = Checks()
+    ctx.prepare_graphs()
     C.host_register(src)
 
     def median_run(req, capture_bytes, **kw):
-        # the host side of serving (admission, staging threads, the master)
-        # shares the machine's cores with other work: each rate runs three times
-        # and the run with the median throughput is reported, all three listed
+        # near saturation a run either keeps up with the arrivals or drains a
+        # backlog after the last one: each rate runs several times and the
+        # run with the median throughput is reported, all of them listed
         runs = []
         for _ in range(args.c5_repeats):
             capture = np.zeros(capture_bytes, dtype=np.uint8)
@@ -1078,6 +1079,7 @@ def run_serving(args, ws, rank, local):
                     flags=C.CRYSTAL_FLAG_GRAPHS)
     out = {}
     checks = Checks()
+    ctx.prepare_graphs()
     pinned = args.source == "pinned"
     if pinned:
         C.host_register(src)
@@ -1393,7 +1395,7 @@ def main():
     ap.add_argument("--pool-bytes", type=int, default=8 << 30)
     ap.add_argument("--copy-threads", type=int, default=4,
                     help="serving: threads that bind or stage each admitted request and submit it")
-    ap.add_argument("--c5-repeats", type=int, default=3)
+    ap.add_argument("--c5-repeats", type=int, default=5)
     ap.add_argument("--input-ring", type=int, default=256 << 20,
                     help="served requests: bytes of the input ring for small requests (0: none)")
     ap.add_argument("--ring-max", type=int, default=256 << 10,

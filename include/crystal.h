@@ -267,6 +267,18 @@ typedef struct crystal_geometry {
  * the class's captured graphs are dropped and re-captured on next use. */
 int crystal_set_geometry(crystal_ctx* ctx, int size_class, const crystal_geometry* g);
 
+/* With CRYSTAL_FLAG_GRAPHS each stream slot replays one captured graph per
+ * batch size class and kind mix, captured the first time a batch of that
+ * shape lands on that slot -- a few hundred microseconds of master-thread time
+ * inside whatever stream meets it first.  crystal_prepare_graphs captures
+ * every graph not captured yet now, on the calling thread, so that a stream
+ * that follows pays none of it (a set-up step like the pools of crystal_init;
+ * crystal_set_geometry drops the graphs of the classes it changes, so call it
+ * again after that).  The context must be idle (no outstanding or running
+ * job): EINVAL otherwise; CRYSTAL_OK with nothing done without
+ * CRYSTAL_FLAG_GRAPHS; EDEVICE if a capture fails. */
+int crystal_prepare_graphs(crystal_ctx* ctx);
+
 /* The geometry class size_class (0..2) runs with, resolved (threads per CTA
  * and CTAs per SM as launched, register budget 32 or 64), written to *out.
  * EINVAL for NULL or a bad class. */
@@ -285,6 +297,7 @@ typedef struct crystal_stats {
     uint64_t create_ns;          /* time spent inside crystal_task_create[_ex] (all threads) */
     uint64_t create_calls;       /* calls of crystal_task_create[_ex] */
     uint64_t create_eagain;      /* of which returned CRYSTAL_EAGAIN (pool full) */
+    uint64_t graph_captures;     /* batch graphs captured and instantiated (CRYSTAL_FLAG_GRAPHS) */
 } crystal_stats;
 int crystal_get_stats(crystal_ctx* ctx, crystal_stats* out);
 

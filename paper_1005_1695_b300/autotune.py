@@ -85,6 +85,9 @@ def _context(req: np.ndarray, setting: Setting, device_pool_bytes: int, device: 
                     max_batch_jobs=setting.batch_jobs, max_batch_bytes=setting.batch_bytes, flags=flags)
     for cls, g in setting.geometry.items():
         ctx.set_geometry(cls, C.geometry(**g))
+    # graphs captured before the measured run, not by its first batches (a
+    # setting with more streams has more slots to capture)
+    ctx.prepare_graphs()
     return ctx
 
 

@@ -86,7 +86,7 @@ class crystal_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "jobs_completed", "batches_launched", "device_pool_bytes", "device_pool_used",
         "host_pool_bytes", "host_pool_used", "jobs_outstanding", "jobs_running", "copies_dma",
-        "master_issue_ns", "master_complete_ns", "create_ns", "create_calls", "create_eagain")]
+        "master_issue_ns", "master_complete_ns", "create_ns", "create_calls", "create_eagain", "graph_captures")]
 
 
 UNIT_DTYPE = np.dtype([
@@ -195,6 +195,7 @@ def load() -> ctypes.CDLL:
         "crystal_task_wait_many": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.c_int64]),
         "crystal_task_timing_many": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, _vp]),
         "crystal_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(crystal_stats)]),
+        "crystal_prepare_graphs": (ctypes.c_int, [_vp]),
         "crystal_out_bytes": (_u64, [ctypes.c_int, _u64, ctypes.POINTER(crystal_hash_params)]),
         "crystal_sliding_out_bytes": (_u64, [_u64, _u64]),
         "crystal_out_bytes_for_chunks": (_u64, [ctypes.c_int, _u64, _u64]),
@@ -457,6 +458,11 @@ class Context:
         c = crystal_config()
         check(load().crystal_get_config(self.handle, ctypes.byref(c)), "crystal_get_config")
         return c
+
+    def prepare_graphs(self) -> None:
+        """crystal_prepare_graphs: capture every stream slot's batch graphs
+        now (the context must be idle)."""
+        check(load().crystal_prepare_graphs(self.handle), "crystal_prepare_graphs")
 
     def stats(self) -> crystal_stats:
         s = crystal_stats()

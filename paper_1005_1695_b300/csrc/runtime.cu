@@ -169,6 +169,7 @@ struct crystal_ctx {
     std::atomic<uint64_t> copies_dma{0};
     std::atomic<uint64_t> issue_ns{0}, complete_ns{0};  // master thread time issuing / completing batches
     std::atomic<uint64_t> create_ns{0}, create_calls{0}, create_eagain{0};  // crystal_task_create_ex
+    std::atomic<uint64_t> graph_captures{0};
     uint64_t n_running_jobs = 0;
 };
 
@@ -366,6 +367,7 @@ int capture_graph(crystal_ctx* c, Slot& s, int cls, int variant) {
     }
     e = cudaGraphInstantiate(&s.graph[cls][variant], g, 0);
     cudaGraphDestroy(g);
+    if (e == cudaSuccess) c->graph_captures.fetch_add(1, std::memory_order_relaxed);
     return e == cudaSuccess ? CRYSTAL_OK : CRYSTAL_EDEVICE;
 }
 
@@ -1352,7 +1354,32 @@ int crystal_get_stats(crystal_ctx* c, crystal_stats* out) {
     out->create_ns = c->create_ns.load();
     out->create_calls = c->create_calls.load();
     out->create_eagain = c->create_eagain.load();
+    out->graph_captures = c->graph_captures.load();
     return CRYSTAL_OK;
+}
+
+int crystal_prepare_graphs(crystal_ctx* c) {
+    if (!c) return CRYSTAL_EINVAL;
+    if (!(c->cfg.flags & CRYSTAL_FLAG_GRAPHS)) return CRYSTAL_OK;
+    int prev = 0;
+    const bool restore = cudaGetDevice(&prev) == cudaSuccess && prev != c->device;
+    if (restore) cudaSetDevice(c->device);
+    int r = CRYSTAL_OK;
+    {
+        // idle: the master issues nothing while no job is outstanding, so the
+        // slots' streams and graphs are this thread's for the duration
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!c->outstanding.empty() || c->n_running_jobs || c->stop) {
+            r = CRYSTAL_EINVAL;
+        } else {
+            for (Slot& s : c->slots)
+                for (int cls = 0; cls < CRYSTAL_SIZE_CLASSES && r == CRYSTAL_OK; ++cls)
+                    for (int variant = 1; variant < 4 && r == CRYSTAL_OK; ++variant)
+                        if (!s.graph[cls][variant]) r = capture_graph(c, s, cls, variant);
+        }
+    }
+    if (restore) cudaSetDevice(prev);
+    return r;
 }
 
 }  // extern "C"

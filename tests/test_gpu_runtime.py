@@ -95,6 +95,35 @@ def test_runtime_modes_bit_exact(C, oracle_mod, flags):
         assert after.device_pool_used == used0 and after.host_pool_used == 0
 
 
+def test_prepared_graphs_are_replayed_not_captured(C, oracle_mod):
+    """crystal_prepare_graphs captures every stream slot's graph for every
+    batch size class and kind mix up front; a mixed stream afterwards
+    captures nothing and stays bit-exact.  Without graphs it does nothing."""
+    jobs = _jobs(C)
+    want = _want(oracle_mod, jobs)
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=256 << 20,
+                   host_pool_bytes=128 << 20, n_streams=3, flags=C.CRYSTAL_FLAG_GRAPHS, max_batch_jobs=8) as ctx:
+        assert ctx.stats().graph_captures == 0
+        ctx.prepare_graphs()
+        n = ctx.stats().graph_captures
+        assert n == 3 * 2 * C.CRYSTAL_SIZE_CLASSES * 3  # slots x size classes x kind mixes
+        ctx.prepare_graphs()  # nothing left to capture
+        assert ctx.stats().graph_captures == n
+        tasks = _submit_all(C, ctx, jobs)
+        _check(C, tasks, jobs, want)
+        assert ctx.stats().graph_captures == n
+        for t in tasks:
+            t.release()
+        # a geometry change drops that class's graphs; preparing again recaptures them
+        ctx.set_geometry(1, C.geometry(seg_threads=64))
+        ctx.prepare_graphs()
+        assert ctx.stats().graph_captures == n + 3 * 2 * 3
+    with C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 16, device_pool_bytes=64 << 20,
+                   host_pool_bytes=64 << 20, n_streams=2) as ctx:
+        ctx.prepare_graphs()
+        assert ctx.stats().graph_captures == 0
+
+
 def test_resubmit_reuses_buffers(C, oracle_mod):
     jobs = _jobs(C, count=6, seed=11)
     want = _want(oracle_mod, jobs)
