@@ -13,6 +13,7 @@
 // persistent-kernel chain however many jobs it holds; with
 // CRYSTAL_FLAG_GRAPHS that chain is a captured CUDA graph.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string.h>
 #include <time.h>
@@ -68,6 +69,18 @@ struct Slot {
 };
 
 thread_local const crystal_ctx* tl_callback_ctx = nullptr;
+
+// NVTX ranges (header-only NVTX 3) around the master thread's work -- issuing
+// a batch, completing one, capturing a graph -- so that a timeline tool
+// (Nsight Systems, or ncu's NVTX filters) shows the runtime's stages beside
+// the copies and kernels; without a tool attached each range costs a few
+// nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace
 
@@ -353,6 +366,7 @@ int batch_sequence(crystal_ctx* c, Slot& s, bool direct, bool sliding, const Lau
 
 // Capture batch_sequence of one slot as a graph.
 int capture_graph(crystal_ctx* c, Slot& s, int cls, int variant) {
+    NvtxRange range("crystal: capture batch graph");
     const bool direct = variant & 1, sliding = variant & 2;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CRYSTAL_EDEVICE;
@@ -435,6 +449,7 @@ bool dma(const Run& r, cudaMemcpyKind kind, cudaStream_t st) {
 
 // Issue copy-in, kernels and copy-out of the slot's jobs on its stream.
 int issue(crystal_ctx* c, Slot& s) {
+    NvtxRange range("crystal: issue batch");
     cudaStream_t st = s.stream;
     uint32_t nd = 0, ns = 0;
     build_descriptor(c, s, &nd, &ns);
@@ -530,6 +545,7 @@ void destroy_released(crystal_ctx* c, const std::vector<crystal_task*>& released
 // of jobs released from their callbacks.  Called by the master thread
 // without the lock held.
 void finish_slot(crystal_ctx* c, Slot& s, int issue_status) {
+    NvtxRange range("crystal: complete batch");
     const uint64_t t = now_ns();
     const uint32_t dev_status = s.h_desc ? s.h_desc->status : 0;
     std::vector<crystal_task*> jobs;
