@@ -194,3 +194,29 @@ def test_input_ring_larger_than_the_pools_is_refused(C):
         assert after.host_pool_used == before.host_pool_used
     finally:
         ctx.shutdown()
+
+
+def test_served_mixed_hashes_through_the_ring(C, oracle_mod):
+    """MD5 and SHA-1, direct and sliding, served together with small requests
+    through a 4 MiB input ring (so batches mix kinds, ring slots and buffers
+    of their own): every output bit-exact against the oracle."""
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    src = inputs.arena(12, 48 << 20, out=C.page_aligned(48 << 20))
+    req, _ = S.make_trace(12, 200, 5000.0, src.nbytes, median=96 << 10, sigma=1.2, cap=2 << 20, p_sliding=0.4)
+    sha = np.arange(len(req)) % 2 == 1
+    req["kind"] = np.where(sha, np.where(np.isin(req["kind"], list(C.SLIDING_KINDS)), C.CRYSTAL_KIND_SHA1_SLIDING,
+                                         C.CRYSTAL_KIND_SHA1_DIRECT), req["kind"])
+    S.set_out_sizes(req)
+    cap = S.assign_capture(req)
+    st, res, wall, capture = S.serve_trace(req, src, device_pool_bytes=96 << 20, host_pool_bytes=96 << 20,
+                                           streams=4, batch_jobs=8, copy_threads=4, capture_bytes=cap,
+                                           source_pinned=True, ring_bytes=4 << 20)
+    assert st == C.CRYSTAL_OK and (res["status"] == 0).all()
+    for i in range(len(req)):
+        k, n, o = int(req["kind"][i]), int(req["size"][i]), int(req["src_offset"][i])
+        ost, want = oracle_mod.task(k, src[o:o + n], int(req["out_size"][i]))
+        off = int(req["capture_offset"][i])
+        got = capture[off:off + int(res["used_bytes"][i])].tobytes()
+        assert ost == 0 and same_result(k, n, got, want), f"request {i} (kind {k}): " + first_difference(k, n, got, want)
