@@ -76,6 +76,16 @@ def _kernel_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def _mean_ci(xs) -> dict:
+    """Mean and 95% confidence half-width (normal approximation) of per-step
+    times, with their spread: the paper's reporting (means over repeated runs
+    with 95% intervals, Section 5)."""
+    a = np.asarray(xs, dtype=np.float64)
+    half = 1.96 * float(a.std(ddof=1)) / float(np.sqrt(len(a))) if len(a) > 1 else 0.0
+    return {"mean": round(float(a.mean()), 4), "ci95": round(half, 4), "min": round(float(a.min()), 4),
+            "max": round(float(a.max()), 4), "n": int(len(a))}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -461,6 +471,10 @@ def run_ours(args, ws, rank, local):
         e2e_wall = slowest(time.perf_counter() - t0)
         for tm in stamps:
             lat.extend(((tm[:, 2] - tm[:, 0]).astype(np.float64) / 1e6).tolist())
+        # time between consecutive steps' last completions (steps overlap, so
+        # this spacing, not a step's own span, is its share of the wall time)
+        done = np.array([float(tm[:, 2].max()) for tm in stamps]) / 1e6
+        e2e_step_ms = np.diff(done).tolist()
         launches = launches_value + C.kernel_launches() - launches1
         e2e_value = aggregate_gbs(ws, total_bytes, args.steps, e2e_wall)
         # results of the units the CPU baseline leg will also hash (checked there)
@@ -509,7 +523,8 @@ def run_ours(args, ws, rank, local):
         "value_basis": "hashed GB/s with the inputs resident in HBM (the kernel chain through the C ABI); the "
                        "host-to-digests figure of the metric is e2e.value",
         "device_resident_gbs": round(value, 3), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4),
+        "step_ms_stats": _mean_ci(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"sliding-window {args.hash.upper()}, {U} units x {N // 1024} KiB, w=20, "
                                "mask=target=0x1FFF, chunk direct hash S=4 KiB",
@@ -542,6 +557,7 @@ def run_ours(args, ws, rank, local):
         "e2e": None if e2e_value is None else {
             "value": round(e2e_value, 3), "unit": "GB/s", "h2d_bytes_per_step": total_bytes * ws,
             "d2h_bytes_per_step": U * out_size * ws, "ms_per_step": round(e2e_wall * 1e3 / args.steps, 3),
+            "step_spacing_ms_stats": _mean_ci(e2e_step_ms) if len(e2e_step_ms) > 1 else None,
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                            "p99": round(float(np.percentile(lat, 99)), 3)},
             "roofline_gbs": round(e2e_bound, 2), "frac": round(e2e_value / ws / e2e_bound, 4),
