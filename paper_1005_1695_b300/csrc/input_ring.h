@@ -25,6 +25,7 @@ class InputRing {
     // A slot for `size` bytes: its offset, and its ticket in *seq; kNone when
     // the ring has no room.
     uint64_t take(uint64_t size, uint64_t* seq) {
+        if (size > bytes_) return kNone;  // also keeps the rounding below from wrapping
         const uint64_t b = ((size ? size : 1) + 255) & ~(uint64_t)255;
         std::lock_guard<std::mutex> lk(mu_);
         uint64_t off = kNone;

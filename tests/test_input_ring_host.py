@@ -146,6 +146,11 @@ def test_ring_reclaims_everything_and_grants_when_empty(driver):
     assert lines[9] == "0" and lines[10] == "none"  # larger than the ring: never
 
 
+def test_ring_refuses_sizes_that_would_wrap(driver):
+    lines = run(driver, 1 << 20, [("t", (1 << 64) - 1), ("t", (1 << 64) - 200), ("n", 0), ("t", 100)])
+    assert lines[:3] == ["none", "none", "0"] and lines[3] == "0 0"
+
+
 def test_ring_wraps_and_waits_for_the_oldest(driver):
     R = 4096
     ops = [("t", 1024), ("t", 1024), ("t", 1024), ("t", 1024),  # full: seqs 0-3 at 0,1024,2048,3072
