@@ -1411,8 +1411,9 @@ def main():
     ap.add_argument("--max-requests", type=int, default=20000)
     ap.add_argument("--arena-bytes", type=int, default=1 << 30)
     ap.add_argument("--pool-bytes", type=int, default=8 << 30)
-    ap.add_argument("--copy-threads", type=int, default=4,
-                    help="serving: threads that bind or stage each admitted request and submit it")
+    ap.add_argument("--copy-threads", type=int, default=0,
+                    help="serving: threads that bind or stage each admitted request and submit it "
+                         "(0: 4 for a page-locked source, 8 for a pageable one, whose bytes they copy)")
     ap.add_argument("--c5-repeats", type=int, default=5)
     ap.add_argument("--input-ring", type=int, default=256 << 20,
                     help="served requests: bytes of the input ring for small requests (0: none)")
@@ -1436,6 +1437,8 @@ def main():
     ap.add_argument("--c4-plain-units", type=int, default=300)
     ap.add_argument("--c5-rates", default="10000,50000")
     args = ap.parse_args()
+    if not args.copy_threads:
+        args.copy_threads = 8 if args.source == "pageable" else 4
     ws, rank, local = _dist()
     cores = len(os.sched_getaffinity(0))
     params = dict(window=20, mask=0x1FFF, target=0x1FFF, chunk_seg_bytes=4096)
