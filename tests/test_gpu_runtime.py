@@ -124,6 +124,67 @@ def test_prepared_graphs_are_replayed_not_captured(C, oracle_mod):
         assert ctx.stats().graph_captures == 0
 
 
+def test_application_threads_share_one_context(C, oracle_mod):
+    """Eight application threads create, fill, submit, wait for and release
+    jobs on one context at the same time (some waiting job by job, some with
+    wait_many), over many rounds with a small pool, so creation meets EAGAIN
+    while other threads free room: every output bit-exact, the pools whole at
+    the end."""
+    jobs = _jobs(C, count=24, seed=21)
+    want = _want(oracle_mod, jobs)
+    errors = []
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=8 << 20,
+                   host_pool_bytes=8 << 20, n_streams=4, max_batch_jobs=8, flags=C.CRYSTAL_FLAG_GRAPHS) as ctx:
+        used0 = ctx.stats().device_pool_used
+
+        def worker(k):
+            held = []
+
+            def drain():
+                if k % 2 and held:
+                    ctx.wait_many([t for _, t in held], 60 * SEC)
+                for i, t in held:
+                    kind, data = jobs[i][0], jobs[i][1]
+                    st = t.wait(60 * SEC)
+                    assert st == (C.CRYSTAL_OK if want[i][0] == 0 else C.CRYSTAL_EOVERFLOW), (k, i, st)
+                    assert same_result(kind, len(data), t.output(), want[i][1]), (k, i)
+                    assert t.release() == C.CRYSTAL_OK
+                held.clear()
+
+            try:
+                for r in range(6):
+                    for i in [i for i in range(len(jobs)) if (i + k + r) % 8 == 0]:
+                        kind, data, osz, p = jobs[i]
+                        for attempt in range(20000):  # bounded: ~10 s of retries at most
+                            try:
+                                t = ctx.task_create(len(data), osz)
+                                break
+                            except C.CrystalError as e:
+                                # pool full: finish this thread's own jobs (never
+                                # hold buffers while waiting for room), then retry
+                                assert e.status == C.CRYSTAL_EAGAIN, e
+                                drain()
+                                threading.Event().wait(0.0005)
+                        else:
+                            raise AssertionError("no room for a job after 20,000 tries")
+                        t.h_in[:] = data
+                        assert t.submit(kind, p) == C.CRYSTAL_OK
+                        held.append((i, t))
+                    drain()
+            except Exception as e:  # reported on the main thread
+                errors.append(e)
+
+        threads = [threading.Thread(target=worker, args=(k,)) for k in range(8)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        assert not errors, errors[0]
+        s = ctx.stats()
+        assert s.device_pool_used == used0 and s.host_pool_used == 0
+        assert s.jobs_completed == 6 * len(jobs)
+
+
 def test_resubmit_reuses_buffers(C, oracle_mod):
     jobs = _jobs(C, count=6, seed=11)
     want = _want(oracle_mod, jobs)
