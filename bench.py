@@ -856,9 +856,10 @@ def record_config5(args, local, link):
     src = inputs.arena(args.seed + 5, arena_bytes, out=C.page_aligned(arena_bytes))
     pool = args.pool_bytes
     h2d = max(link["h2d_single_gbs"], link["h2d_multi_gbs"])
-    # the host pool holds outputs only (inputs are read in place from the arena)
+    # the host pool holds outputs and the input ring (inputs are read in place
+    # from the arena), and the staged inputs of the pageable-source runs
     ctx = C.Context(max_in_bytes=64 << 20, max_out_bytes=C.sliding_out_bytes(64 << 20, 4 * 8192 + 64),
-                    device_pool_bytes=pool, host_pool_bytes=1 << 30, n_streams=args.streams, device=local,
+                    device_pool_bytes=pool, host_pool_bytes=4 << 30, n_streams=args.streams, device=local,
                     max_batch_jobs=args.serve_batch_jobs, max_batch_bytes=32 << 20, flags=C.CRYSTAL_FLAG_GRAPHS)
     ring = dict(ring_bytes=args.input_ring, ring_max_request=args.ring_max)
     rec = {"workload": "open-loop Poisson requests, lognormal sizes (median 256 KiB, sigma 1.5, cap 64 MiB), "
@@ -870,8 +871,9 @@ def record_config5(args, local, link):
     checks = Checks()
     ctx.prepare_graphs()
     C.host_register(src)
+    registered = True
 
-    def median_run(req, capture_bytes, **kw):
+    def median_run(req, capture_bytes, pinned=True, threads=args.copy_threads, **kw):
         # near saturation a run either keeps up with the arrivals or drains a
         # backlog after the last one: each rate runs several times and the
         # run with the median throughput is reported, all of them listed
@@ -879,8 +881,8 @@ def record_config5(args, local, link):
         for _ in range(args.c5_repeats):
             capture = np.zeros(capture_bytes, dtype=np.uint8)
             s0 = ctx.stats()
-            st, res, wall = ctx.serve(src, req, capture=capture, copy_threads=args.copy_threads,
-                                      source_pinned=True, **kw)
+            st, res, wall = ctx.serve(src, req, capture=capture, copy_threads=threads,
+                                      source_pinned=pinned, **kw)
             C.check(st, "crystal_serve")
             runs.append((wall, res, capture, int(ctx.stats().copies_dma - s0.copies_dma)))
         order = sorted(runs, key=lambda r: r[0])
@@ -924,9 +926,30 @@ def record_config5(args, local, link):
                 o, nb, off = int(req["src_offset"][i]), int(req["size"][i]), int(req["capture_offset"][i])
                 checks.add(int(req["kind"][i]), src[o:o + nb], int(req["out_size"][i]),
                            capture[off:off + int(res["used_bytes"][i])])
+            if rate == max(args.c5_rates):
+                last = (rate, n, req, cap, total, span, res, capture, sample)
+        # the other source mode: the same highest-rate requests from pageable
+        # memory, every request's bytes copied by the staging threads (8)
+        rate, n, req, cap, total, span, res, capture, sample = last
+        C.host_unregister(src)
+        registered = False
+        (wp, resp, capp, copiesp), wallsp = median_run(req, cap, pinned=False, threads=8, **ring)
+        latp = S.latency_ms(req, resp)
+        same = all(capp[int(req["capture_offset"][i]):int(req["capture_offset"][i]) + int(resp["used_bytes"][i])]
+                   .tobytes() == capture[int(req["capture_offset"][i]):int(req["capture_offset"][i])
+                                         + int(res["used_bytes"][i])].tobytes() for i in sample)
+        gbs = total / (wp / 1e9) / GB
+        rec["pageable_source"] = {
+            "rate_per_s": int(rate), "requests": n, "copy_threads": 8, "GB_per_s": round(gbs, 3),
+            "frac_of_link": round(gbs / h2d, 4),
+            "latency_ms": {"p50": round(float(np.percentile(latp, 50)), 3),
+                           "p99": round(float(np.percentile(latp, 99)), 3)},
+            "runs_GB_per_s": [round(total / (w / 1e9) / GB, 3) for w in wallsp], "dma_copies": copiesp,
+            "sample_outputs_equal_page_locked_run": bool(same)}
     finally:
         ctx.shutdown()
-        C.host_unregister(src)
+        if registered:
+            C.host_unregister(src)
     return rec, checks
 
 
