@@ -924,17 +924,23 @@ int crystal_task_create(crystal_ctx* c, uint64_t in_size, uint64_t out_size, cry
 namespace {
 int create_job(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes, uint32_t flags,
                crystal_task** out, uint8_t* borrowed_h_in = nullptr, uint8_t* borrowed_d_in = nullptr);
-}
 
-int crystal_task_create_ex(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes,
-                           uint32_t flags, crystal_task** out) {
-    if (!c) return CRYSTAL_EINVAL;
+// create_job with the creation counters of crystal_stats
+int counted_create(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes, uint32_t flags,
+                   crystal_task** out, uint8_t* borrowed_h_in = nullptr, uint8_t* borrowed_d_in = nullptr) {
     const uint64_t t0 = now_ns();
-    const int st = create_job(c, in_size, out_size, scratch_bytes, flags, out);
+    const int st = create_job(c, in_size, out_size, scratch_bytes, flags, out, borrowed_h_in, borrowed_d_in);
     c->create_ns.fetch_add(now_ns() - t0, std::memory_order_relaxed);
     c->create_calls.fetch_add(1, std::memory_order_relaxed);
     if (st == CRYSTAL_EAGAIN) c->create_eagain.fetch_add(1, std::memory_order_relaxed);
     return st;
+}
+}  // namespace
+
+int crystal_task_create_ex(crystal_ctx* c, uint64_t in_size, uint64_t out_size, uint64_t scratch_bytes,
+                           uint32_t flags, crystal_task** out) {
+    if (!c) return CRYSTAL_EINVAL;
+    return counted_create(c, in_size, out_size, scratch_bytes, flags, out);
 }
 
 }  // extern "C"
@@ -1426,12 +1432,7 @@ void release_pool_pair(crystal_ctx* c, const PoolPair& p) {
 int task_create_borrowed(crystal_ctx* c, uint8_t* h_in, uint8_t* d_in, uint64_t in_size, uint64_t out_size,
                          uint64_t scratch_bytes, crystal_task** out) {
     if (!c || !h_in || !d_in) return CRYSTAL_EINVAL;
-    const uint64_t t0 = now_ns();
-    const int st = create_job(c, in_size, out_size, scratch_bytes, 0, out, h_in, d_in);
-    c->create_ns.fetch_add(now_ns() - t0, std::memory_order_relaxed);
-    c->create_calls.fetch_add(1, std::memory_order_relaxed);
-    if (st == CRYSTAL_EAGAIN) c->create_eagain.fetch_add(1, std::memory_order_relaxed);
-    return st;
+    return counted_create(c, in_size, out_size, scratch_bytes, 0, out, h_in, d_in);
 }
 
 }  // namespace crystal
