@@ -1,5 +1,8 @@
 """Job streams in every form the runtime offers (pooled / staged / no overlap /
 per-job allocation / plain), bit-exact against the CPU oracle."""
+import concurrent.futures as cf
+import os
+
 import numpy as np
 import pytest
 
@@ -20,26 +23,37 @@ def C():
     return crystal
 
 
-@pytest.mark.parametrize("mode", ["pooled", "pooled_staged", "no_overlap", "per_job_malloc", "plain"])
-@pytest.mark.parametrize("kind", [1, 2], ids=["direct", "sliding"])
+MODE_KINDS = [(m, k) for m in ("pooled", "pooled_staged", "no_overlap", "per_job_malloc", "plain") for k in (1, 2)] + \
+    [(m, k) for m in ("pooled", "pooled_staged") for k in (3, 4)]
+
+
+@pytest.mark.parametrize("mode,kind", MODE_KINDS,
+                         ids=[f"{m}-{['', 'direct', 'sliding', 'sha1_direct', 'sha1_sliding'][k]}" for m, k in MODE_KINDS])
 def test_stream_modes_bit_exact(C, oracle_mod, mode, kind):
     from paper_1005_1695_b300 import inputs
     from paper_1005_1695_b300 import streams as S
 
     n_units, n = 40, 300_017
-    p = C.params(mask=0x3FF, target=0x3FF) if kind == 2 else C.params(segment_bytes=4096)
-    out_size = 16 if kind == 1 else C.sliding_out_bytes(n, n // 256)
+    sliding = kind in (2, 4)
+    p = C.params(mask=0x3FF, target=0x3FF) if sliding else C.params(segment_bytes=4096)
+    out_size = C.sliding_out_bytes(n, n // 256, kind) if sliding else C.digest_size(kind)
 
     def unit(i):
-        return inputs.dedup_unit(5, i, n) if kind == 2 else inputs.uniform_unit(5, i, n)
+        return inputs.dedup_unit(5, i, n) if sliding else inputs.uniform_unit(5, i, n)
 
     r = S.run_stream(mode, unit, n_units, n, kind, p, out_size, streams=3, batch_jobs=4, depth=6,
                      keep=range(n_units))
     assert r.statuses == [C.CRYSTAL_OK] * n_units
     assert len(r.latencies_ms) == n_units and min(r.latencies_ms) >= 0
-    for i in range(0, n_units, 3):
-        st, want = oracle_mod.task(kind, unit(i), out_size, seg_bytes=p.segment_bytes, window=p.window_bytes,
-                                   mask=p.mask, target=p.target, chunk_seg_bytes=p.chunk_segment_bytes)
+    checked = list(range(0, n_units, 3))
+
+    def oracle(i):
+        return oracle_mod.task(kind, unit(i), out_size, seg_bytes=p.segment_bytes, window=p.window_bytes,
+                               mask=p.mask, target=p.target, chunk_seg_bytes=p.chunk_segment_bytes)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        wants = list(ex.map(oracle, checked))
+    for i, (st, want) in zip(checked, wants):
         assert st == 0
         got = r.outputs[i]
         assert same_result(kind, n, got, want), f"{mode} unit {i}: " + first_difference(kind, n, got, want)
