@@ -962,7 +962,9 @@ def record_overhead(args, local, link):
 
 def record_streamlen(args, local, link):
     return {"metric": "GB/s per stream length, 1 MiB direct-hash jobs (Figure 8's shape)",
-            "stream_lengths": measure_streamlen(local, args.seed, (1, 2, 4, 10), 3)}, Checks()
+            "stream_lengths": measure_streamlen(local, args.seed, (1, 2, 4, 10), 3),
+            "stream_lengths_sha1": measure_streamlen(local, args.seed, (1, 2, 4, 10), 3,
+                                                     kind=3)}, Checks()
 
 
 def run_config_records(args, local, link):
@@ -1284,10 +1286,11 @@ def run_overhead(args, ws, rank, local):
                       "paper_context": "slightly under 70 us per job on a 9800 GX2 host (Section 5.1)"}))
 
 
-def measure_streamlen(local: int, seed: int, lengths, reps: int) -> dict:
-    """Streams of 1..10 jobs of 1 MiB (direct hashing, Figure 8's shape): the
-    plain form against no-overlap and pooled + overlap, per stream length
-    (median of ``reps`` streams each)."""
+def measure_streamlen(local: int, seed: int, lengths, reps: int, kind: int = 1) -> dict:
+    """Streams of 1..10 jobs of 1 MiB (direct hashing, Figure 8's shape; the
+    paper's runs hash with SHA-1, kind 3): the plain form against no-overlap
+    and pooled + overlap, per stream length (median of ``reps`` streams
+    each)."""
     import torch
 
     from paper_1005_1695_b300 import crystal as C
@@ -1303,7 +1306,7 @@ def measure_streamlen(local: int, seed: int, lengths, reps: int) -> dict:
     for L in lengths:
         row = {}
         for mode in ("plain", "no_overlap", "pooled"):
-            runs = [S.run_stream(mode, lambda i: data[i], L, N, C.CRYSTAL_KIND_MD5_DIRECT, p, 16, streams=8,
+            runs = [S.run_stream(mode, lambda i: data[i], L, N, kind, p, C.digest_size(kind), streams=8,
                                  batch_jobs=8, depth=24, device=local).seconds for _ in range(reps)]
             row[mode] = round(L * N / float(np.median(runs)) / GB, 3)
         row["speedup_pooled_vs_plain"] = round(row["pooled"] / row["plain"], 2)
@@ -1314,6 +1317,8 @@ def measure_streamlen(local: int, seed: int, lengths, reps: int) -> dict:
 def run_streamlen(args, ws, rank, local):
     print(json.dumps({"metric": "GB/s per stream length, 1 MiB direct-hash jobs", "unit": "GB/s",
                       "stream_lengths": measure_streamlen(local, args.seed, range(1, 11), max(3, args.steps)),
+                      "stream_lengths_sha1": measure_streamlen(local, args.seed, range(1, 11), max(3, args.steps),
+                                                               kind=3),
                       "data": "synthetic"}))
 
 
