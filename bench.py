@@ -974,7 +974,7 @@ def run_config_records(args, local, link):
     for name, fn in (("config1_plain", record_config1), ("config3_pipelined", record_config3),
                      ("config4_batched", record_config4), ("config5_served", record_config5),
                      ("sha1_sliding", record_sha1), ("overhead_per_job", record_overhead),
-                     ("stream_length", record_streamlen)):
+                     ("stream_length", record_streamlen), ("stream_of_10_by_size", record_sizes)):
         t0 = time.perf_counter()
         rec, checks = fn(args, local, link)
         rec["wall_s"] = round(time.perf_counter() - t0, 1)
@@ -1314,6 +1314,48 @@ def measure_streamlen(local: int, seed: int, lengths, reps: int, kind: int = 1) 
     return out
 
 
+def measure_sizes(local: int, seed: int, sizes, jobs: int, reps: int, kind: int = 3) -> dict:
+    """Streams of ``jobs`` direct-hash jobs per data size (Figure 7's shape:
+    the paper's stream of 10 SHA-1 jobs over block sizes): the plain form
+    (allocation per job, one job at a time), buffer reuse alone (pooled, no
+    overlap) and reuse with overlap (pooled, 8 streams), median of ``reps``."""
+    import torch
+
+    from paper_1005_1695_b300 import crystal as C
+    from paper_1005_1695_b300 import inputs
+    from paper_1005_1695_b300 import streams as S
+
+    torch.cuda.set_device(local)
+    C.load()
+    p = C.params()
+    out = {}
+    for N in sizes:
+        data = [inputs.uniform_unit(seed, i, N) for i in range(jobs)]
+        row = {}
+        for mode in ("plain", "no_overlap", "pooled"):
+            runs = [S.run_stream(mode, lambda i: data[i], jobs, N, kind, p, C.digest_size(kind), streams=8,
+                                 batch_jobs=8, depth=24, device=local).seconds for _ in range(reps)]
+            row[mode] = round(jobs * N / float(np.median(runs)) / GB, 3)
+        row["speedup_reuse"] = round(row["no_overlap"] / row["plain"], 2)
+        row["speedup_reuse_overlap"] = round(row["pooled"] / row["plain"], 2)
+        out[str(N)] = row
+    return out
+
+
+def record_sizes(args, local, link):
+    return {"metric": "GB/s per data size, streams of 10 SHA-1 direct-hash jobs (Figure 7's shape)",
+            "sizes": measure_sizes(local, args.seed, (64 << 10, 256 << 10, 1 << 20, 4 << 20, 16 << 20), 10, 3),
+            "paper_context": "reuse alone > 6x (small blocks) and > 1.6x (large); with overlap up to 8x and "
+                             ">= 3x, on a 9800 GX2 (Section 5.2)"}, Checks()
+
+
+def run_sizes(args, ws, rank, local):
+    print(json.dumps({"metric": "GB/s per data size, streams of 10 SHA-1 direct-hash jobs", "unit": "GB/s",
+                      "sizes": measure_sizes(local, args.seed, (16 << 10, 64 << 10, 256 << 10, 1 << 20, 4 << 20,
+                                                                16 << 20, 64 << 20), 10, max(3, args.steps)),
+                      "data": "synthetic"}))
+
+
 def run_streamlen(args, ws, rank, local):
     print(json.dumps({"metric": "GB/s per stream length, 1 MiB direct-hash jobs", "unit": "GB/s",
                       "stream_lengths": measure_streamlen(local, args.seed, range(1, 11), max(3, args.steps)),
@@ -1430,7 +1472,7 @@ def main():
     ap.add_argument("--hash", default="md5", choices=["md5", "sha1"],
                     help="hash of the sliding workload (the headline is MD5)")
     ap.add_argument("--workload", default="sliding", choices=["sliding", "direct", "plain", "pipelined", "serving", "batched", "overhead",
-                             "streamlen"])
+                             "streamlen", "sizes"])
     ap.add_argument("--sizes", default="4096,65536,1048576,16777216,67108864")
     ap.add_argument("--tune-units", type=int, default=4000)
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000")
@@ -1499,8 +1541,8 @@ def main():
     if args.workload == "serving":
         run_serving(args, ws, rank, local)
         return
-    if args.workload in ("overhead", "streamlen"):
-        {"overhead": run_overhead, "streamlen": run_streamlen}[args.workload](args, ws, rank, local)
+    if args.workload in ("overhead", "streamlen", "sizes"):
+        {"overhead": run_overhead, "streamlen": run_streamlen, "sizes": run_sizes}[args.workload](args, ws, rank, local)
         return
     if args.workload == "batched":
         if args.units == 256:
