@@ -185,6 +185,44 @@ def test_application_threads_share_one_context(C, oracle_mod):
         assert s.jobs_completed == 6 * len(jobs)
 
 
+def test_graph_preparation_and_geometry_refused_while_busy(C, oracle_mod):
+    """While a job is running (its callback is held open, so the master has
+    not retired it), crystal_prepare_graphs and crystal_set_geometry refuse
+    with EINVAL and change nothing; once the job is retired both succeed, and
+    the job's output is exact."""
+    jobs = _jobs(C, count=1, seed=31)
+    want = _want(oracle_mod, jobs)
+    entered, gate = threading.Event(), threading.Event()
+
+    @C.crystal_callback
+    def cb(handle, status, user):
+        entered.set()
+        gate.wait(20)  # bounded: the test sets it at once
+
+    with C.Context(max_in_bytes=2 << 20, max_out_bytes=1 << 20, device_pool_bytes=64 << 20,
+                   host_pool_bytes=64 << 20, n_streams=2, flags=C.CRYSTAL_FLAG_GRAPHS) as ctx:
+        kind, data, osz, p = jobs[0]
+        t = ctx.task_create(len(data), osz)
+        t.h_in[:] = data
+        assert t.submit(kind, p, cb) == C.CRYSTAL_OK
+        assert entered.wait(30)
+        try:
+            captures = ctx.stats().graph_captures
+            L = C.load()
+            assert L.crystal_prepare_graphs(ctx.handle) == C.CRYSTAL_EINVAL
+            g = C.geometry(seg_threads=64)
+            assert L.crystal_set_geometry(ctx.handle, 0, ctypes.byref(g)) == C.CRYSTAL_EINVAL
+            assert ctx.stats().graph_captures == captures
+        finally:
+            gate.set()
+        assert t.wait(30 * SEC) == (C.CRYSTAL_OK if want[0][0] == 0 else C.CRYSTAL_EOVERFLOW)
+        assert same_result(kind, len(data), t.output(), want[0][1])
+        assert t.release() == C.CRYSTAL_OK
+        ctx.set_geometry(0, C.geometry(seg_threads=64))
+        ctx.prepare_graphs()
+        assert ctx.stats().graph_captures > captures
+
+
 def test_resubmit_reuses_buffers(C, oracle_mod):
     jobs = _jobs(C, count=6, seed=11)
     want = _want(oracle_mod, jobs)
