@@ -677,3 +677,57 @@ def test_adjacent_inputs_merge_into_one_copy_in_any_order(C, oracle_mod):
         assert s.batches_launched == 1 and s.copies_dma - before == 1
         for t, d in zip(tasks, data):
             assert t.output()[:16] == oracle_mod.direct(d, 4096)
+
+
+def test_alu_probe_kinds_work_and_arguments(C):
+    """crystal_alu_probe: every kind launches and reports its work (windows
+    for the two window kinds, instructions for the chains), the work grows
+    with the iterations, and bad arguments are refused (EINVAL)."""
+    import torch
+
+    sink = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for kind in range(7):
+        w1 = C.alu_probe(kind, 2, 1, sink)
+        w4 = C.alu_probe(kind, 2, 4, sink)
+        assert w1 > 0 and w4 == 4 * w1, kind
+        if kind in (0, 1):  # eight windows per thread per iteration
+            assert w1 == sms * 2 * 256 * 8
+    torch.cuda.synchronize()
+    L = C.load()
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.crystal_alu_probe(7, 2, 1, 0, sink.data_ptr(), s, None) == C.CRYSTAL_EINVAL
+    assert L.crystal_alu_probe(0, 0, 1, 0, sink.data_ptr(), s, None) == C.CRYSTAL_EINVAL
+    assert L.crystal_alu_probe(0, 65, 1, 0, sink.data_ptr(), s, None) == C.CRYSTAL_EINVAL
+    assert L.crystal_alu_probe(0, 2, 0, 0, sink.data_ptr(), s, None) == C.CRYSTAL_EINVAL
+    assert L.crystal_alu_probe(0, 2, 1, 0, None, s, None) == C.CRYSTAL_EINVAL
+
+
+def test_get_config_reports_the_context(C):
+    with C.Context(max_in_bytes=3 << 20, max_out_bytes=5 << 10, device_pool_bytes=48 << 20,
+                   host_pool_bytes=40 << 20, n_streams=3, max_batch_jobs=12, flags=C.CRYSTAL_FLAG_GRAPHS) as ctx:
+        cfg = ctx.config()
+        assert (cfg.max_in_bytes, cfg.max_out_bytes) == (3 << 20, 5 << 10)
+        assert (cfg.device_pool_bytes, cfg.host_pool_bytes) == (48 << 20, 40 << 20)
+        assert cfg.n_streams == 3 and cfg.max_batch_jobs == 12 and cfg.flags == C.CRYSTAL_FLAG_GRAPHS
+    with C.Context(max_in_bytes=1 << 20, max_out_bytes=1 << 10, device_pool_bytes=16 << 20,
+                   host_pool_bytes=16 << 20, n_streams=4, max_batch_jobs=12,
+                   flags=C.CRYSTAL_FLAG_NO_BATCH) as ctx:
+        assert ctx.config().max_batch_jobs == 1  # one job per launch
+
+
+def test_direct_job_moves_the_bytes(C):
+    """crystal_direct_job (the overhead experiment's baseline): copy in, an
+    empty kernel, copy out.  With the output read back from the input's
+    device buffer, the bytes come back unchanged."""
+    import torch
+
+    n = 300_001
+    h_in = torch.randint(0, 256, (n,), dtype=torch.uint8).pin_memory()
+    h_out = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    d = torch.empty(n, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    L = C.load()
+    assert L.crystal_direct_job(h_in.data_ptr(), d.data_ptr(), n, h_out.data_ptr(), d.data_ptr(), n,
+                                s.cuda_stream) == C.CRYSTAL_OK
+    assert torch.equal(h_in, h_out)
