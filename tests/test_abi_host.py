@@ -318,3 +318,42 @@ def test_arena_top_blocks_aligned_for_any_size(C):
         assert L.crystal_arena_alloc_at(h, 777, 2, ctypes.byref(off)) == 0
         assert off.value % 256 == 0
     L.crystal_arena_destroy(h)
+
+
+def test_entry_points_refuse_missing_arguments_on_the_host(C):
+    """Every entry point that takes a context, job or batch refuses a NULL one
+    (and the other missing arguments each documents) with CRYSTAL_EINVAL
+    before any device call, so these run without a GPU."""
+    L = C.load()
+    EINVAL = C.CRYSTAL_EINVAL
+    h = ctypes.c_void_p()
+    assert L.crystal_init(None, ctypes.byref(h)) == EINVAL
+    cfg = C.crystal_config()
+    L.crystal_config_default(ctypes.byref(cfg))
+    assert L.crystal_init(ctypes.byref(cfg), None) == EINVAL
+    assert L.crystal_shutdown(None) == EINVAL
+    for name in ("crystal_task_poll", "crystal_task_release", "crystal_prepare_graphs"):
+        assert getattr(L, name)(None) == EINVAL, name
+    assert L.crystal_task_wait(None, 0) == EINVAL
+    assert L.crystal_task_wait_many(None, 1, 0) == EINVAL
+    assert L.crystal_task_wait_many(None, 0, 0) == C.CRYSTAL_OK  # nothing to wait for
+    assert L.crystal_task_resize(None, 0, 0) == EINVAL
+    assert L.crystal_task_bind_input(None, None, 0) == EINVAL
+    assert L.crystal_task_timing(None, None, None, None) == EINVAL
+    assert L.crystal_task_set_priority(None, 1) == EINVAL
+    assert L.crystal_task_submit(None, C.CRYSTAL_KIND_MD5_DIRECT, None, C.crystal_callback(), None) == EINVAL
+    assert L.crystal_get_stats(None, None) == EINVAL
+    assert L.crystal_get_config(None, None) == EINVAL
+    assert L.crystal_set_geometry(None, 0, None) == EINVAL
+    res = np.zeros(1, dtype=C.RESULT_DTYPE)
+    assert L.crystal_serve(None, None, 0, None, 0, None, res.ctypes.data, None) == EINVAL
+    assert L.crystal_stream_staged(None, None, None, 0, None, None, 0, res.ctypes.data, None) == EINVAL
+    for name in ("crystal_launch_direct", "crystal_launch_direct_segments", "crystal_launch_direct_outer",
+                 "crystal_launch_sliding", "crystal_launch_sliding_windows", "crystal_launch_sliding_chunks",
+                 "crystal_launch_sliding_digests", "crystal_launch_batch"):
+        assert getattr(L, name)(None, None) == EINVAL, name
+    assert L.crystal_alu_probe(0, 2, 1, 0, None, None, None) == EINVAL   # no sink
+    assert L.crystal_alu_probe(0, 0, 1, 0, 16, None, None) == EINVAL     # no CTAs
+    assert L.crystal_alu_probe(0, 2, 0, 0, 16, None, None) == EINVAL     # no iterations
+    assert L.crystal_md5_direct_noalloc(None, 4096, 1, 4096, None, None) == EINVAL
+    assert L.crystal_md5_direct_noalloc(None, 4096, 0, 4096, None, None) == C.CRYSTAL_OK  # no units
