@@ -229,9 +229,10 @@ def load() -> ctypes.CDLL:
 
 
 def check(status: int, what: str = "") -> int:
+    """``status`` if it is not an error, else raise CrystalError (a
+    RuntimeError carrying the status)."""
     if status < 0:
-        msg = load().crystal_strerror(status).decode()
-        raise RuntimeError(f"{what}: {msg} ({status})")
+        raise CrystalError(status, what)
     return status
 
 
