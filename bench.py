@@ -234,21 +234,23 @@ def measure_link(torch, dev, total: int, n_streams: int = 8, chunk: int = 8 << 2
 
 def measure_int_pipes(torch, dev, C, ctas_per_sm: int = 16) -> dict:
     """The integer-pipe microbenchmarks of the library (crystal_alu_probe), on
-    register data only, each timed with CUDA events on its stream (best of 3
+    register data only, each timed with CUDA events on its stream (best of 5
     after a warm-up launch): the 20-byte window hash of MD5 and of SHA-1 as the
     window kernel computes it (windows/s), and single-instruction chains on
     one pipe (LOP3, funnel shift, three-input add, IMAD) or two (LOP3 and IMAD
-    alternately: the dual-issue rate), in instructions/s."""
+    alternately: the dual-issue rate), in instructions/s.  Every launch runs
+    for milliseconds (the chains 2,000 iterations), so that launch latency and
+    the clock's ramp do not lower a peak."""
     sink = torch.zeros(4, dtype=torch.int32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     iters = {"md5_windows": 400, "sha1_windows": 150}
     out = {}
     for name, kind in C.PROBE_KINDS.items():
-        it = iters.get(name, 200)
+        it = iters.get(name, 2000)
         with torch.cuda.stream(stream):
             C.alu_probe(kind, ctas_per_sm, max(1, it // 10), sink, stream)
             best = None
-            for _ in range(3):
+            for _ in range(5):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 work = C.alu_probe(kind, ctas_per_sm, it, sink, stream)
